@@ -1,0 +1,71 @@
+"""Paper-printed FP16 facts and sanity pins of the synthetic-input generators."""
+import os
+
+import numpy as np
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_paper_fp16_examples():
+    # Sec. 2.1 prints three FP16 facts; numpy's IEEE binary16 reproduces them.
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "fp16_examples.txt"))
+            if l.strip() and not l.startswith("#")]
+    for op, a, b, expect in rows:
+        if op == "sub":
+            got = np.float16(a) - np.float16(b)
+        elif op == "mul":
+            with np.errstate(over="ignore"):
+                got = np.float16(a) * np.float16(b)
+        else:
+            got = np.finfo(np.float16).max
+        assert float(got) == float(expect)
+    # A 16-bit detector count does not fit in FP16 (65535 > 65504).
+    with np.errstate(over="ignore"):
+        assert np.isinf(np.float16(65535.0))
+
+
+def test_disk_line_integral_is_chord_length():
+    th = np.array([0.0, 0.7, 2.0])
+    p = synth.ellipse_sinogram([(0.0, 0.0, 5.0, 5.0, 0.3, 2.0)], th, 21, 10.0)
+    t = np.arange(21) - 10.0
+    ref = np.where(np.abs(t) < 5, 2 * 2.0 * np.sqrt(np.maximum(25 - t ** 2, 0)), 0)
+    assert np.max(np.abs(p - ref[None])) < 1e-12
+
+
+def test_ellipse_integral_conserves_area():
+    th = synth.uniform_theta(7)
+    ell = [(15.0, -20.0, 900.0, 400.0, 0.4, 1.0)]
+    p = synth.ellipse_sinogram(ell, th, 4001, 2000.0)  # unit-spaced samples
+    # the integral over s of every projection is the area pi A B (midpoint rule)
+    area = np.pi * 900.0 * 400.0
+    assert np.max(np.abs(p.sum(axis=1) - area)) < 1e-4 * area
+
+
+def test_rasterized_area():
+    img = synth.rasterize_ellipses([(0.0, 0.0, 20.0, 10.0, 0.5, 1.0)], 64, supersample=8)
+    assert abs(img.sum() - np.pi * 200.0) / (np.pi * 200.0) < 0.01
+
+
+def test_porous_solid_fraction_and_bounds():
+    rng = np.random.default_rng(0)
+    s = synth.porous_spheres(rng, 1024, 128)
+    x0, y0, z0, r, rho = s.T
+    assert np.all((r >= 3) & (r <= 40)) and np.all((rho >= 0.2) & (rho <= 1.0))
+    assert np.all(np.hypot(x0, y0) + r <= 0.45 * 1024 + 1e-9)
+    frac = (4 / 3 * np.pi * r ** 3).sum() / (np.pi * (0.45 * 1024) ** 2 * 128)
+    assert 0.4 <= frac < 0.41
+
+
+def test_frames_statistics_and_seed():
+    p = np.zeros((50, 2, 40))
+    p[:, :, 10:30] = 1.0
+    raw, dark, flat, mu = synth.frames_from_line_integrals(p, np.random.default_rng(1), 4e4, 10, 10)
+    assert raw.dtype == np.uint16 and raw.shape == p.shape
+    assert abs(mu - 2.0) < 1e-15
+    assert abs(dark.mean() - 100) < 1.0
+    assert abs(flat.mean() - 40100) < 20
+    assert abs(raw[:, :, 15].mean() - (4e4 * np.exp(-2) + 100)) < 10
+    raw2, *_ = synth.frames_from_line_integrals(p, np.random.default_rng(1), 4e4, 10, 10)
+    assert np.array_equal(raw, raw2)
