@@ -1,0 +1,229 @@
+/*
+ * tcp.h -- C ABI of the GB300 (sm_103a) chunked parallel-beam FBP library.
+ *
+ * The operations follow the problem statement of Nikitin, "TomocuPy: efficient
+ * GPU-based tomographic reconstruction with asynchronous data processing"
+ * (arXiv 2209.08450):
+ *   Sec. 2.2  dark-flat field correction and negative logarithm (tcp_normalize),
+ *             one-dimensional Shepp-Logan / Parzen filtering of each detector
+ *             row in Fourier space with padding (tcp_filter), and backprojection
+ *             by direct discretisation of the line integral with linear
+ *             interpolation, the method called LineRec in Sec. 3
+ *             (tcp_backproject);
+ *   Sec. 2.3  asynchronous chunk processing with host-device copies overlapped
+ *             with GPU computation (tcp_fbp);
+ *   Sec. 2.1  16-bit storage with wider arithmetic where 16 bits would lose
+ *             accuracy (every call accepts FP16/BF16 storage and accumulates in
+ *             FP32).
+ * tcp_project, the adjoint Radon projector, is not in the paper; it is the exact
+ * transpose of tcp_backproject.
+ *
+ * Geometry (pixel units):
+ *   projections  raw[theta][z][j]   uint16, projection-major as acquired
+ *   sinograms    sino[z][theta][j]  detector pixel j has its centre at j
+ *   volume       vol[z][iy][ix]     voxel centre (x, y) = (ix - n/2, iy - n/2)
+ *   ray coordinate  s = x cos(theta) + y sin(theta) + center
+ *   interpolation   q(s) = (1-w) q[floor(s)] + w q[floor(s)+1], w = s - floor(s),
+ *                   q[j] = 0 outside [0, ndet)
+ *
+ * Conventions shared by every call:
+ *   - Buffers are described by tcp_tensor: a pointer, a dtype, up to 4 dims and
+ *     element strides.  The innermost stride (the detector or x axis) must be 1.
+ *     The caller allocates and frees every input and output buffer; the library
+ *     never frees caller memory.
+ *   - Device-compute calls are asynchronous on the caller's CUDA stream `stream`
+ *     (a cudaStream_t; NULL means the legacy default stream).  Arguments are
+ *     checked on the host before anything is launched; a rejected call launches
+ *     nothing and returns a non-zero tcp_status.  Errors of kernels already
+ *     queued surface at a later call or through tcp_device_check.
+ *   - The library never synchronises the device inside a compute call, except
+ *     where a call says so (first use of an angle set or filter, see below).
+ *   - Angle arrays `theta` are HOST pointers to FP64 radians.  On first use of
+ *     an angle set the library builds its FP64 cos/sin table, allocates device
+ *     memory for it and copies it synchronously; later calls with the same
+ *     contents reuse the cached table.  The same holds for filter responses
+ *     (keyed by padded length, filter, angle count and centre).  Make the first
+ *     call outside CUDA-graph capture.
+ *   - Scratch memory that a call needs (a few tables) is taken from the CUDA
+ *     stream-ordered allocator on `stream` and released on it.
+ *   - No call aborts or throws across the ABI; failures return a tcp_status and
+ *     record a message retrievable with tcp_last_error (thread-local).
+ */
+#ifndef TCP_H_
+#define TCP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TCP_VERSION 1
+
+typedef enum {
+  TCP_OK = 0,
+  TCP_ERR_ARG = 1,          /* null pointer, unknown enum, non-finite scalar */
+  TCP_ERR_SHAPE = 2,        /* inconsistent, empty-with-data or unsupported sizes */
+  TCP_ERR_DTYPE = 3,        /* dtype not accepted by this argument */
+  TCP_ERR_ALIGN = 4,        /* innermost stride not 1 or a required alignment */
+  TCP_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  TCP_ERR_OOM = 6,          /* device or host allocation failed */
+  TCP_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  TCP_ERR_DEVICE_CHECK = 8, /* a kernel recorded an index violation (checked mode) */
+  TCP_ERR_UNSUPPORTED = 9,  /* valid request outside what this build implements */
+  TCP_ERR_ALIAS = 10        /* input and output overlap where they must not */
+} tcp_status;
+
+typedef enum { TCP_U16 = 0, TCP_F16 = 1, TCP_BF16 = 2, TCP_F32 = 3 } tcp_dtype;
+
+/* Filters of Sec. 2.2 ("Shepp-Logan, Parzen or other").  Every ramp is the
+ * band-limited Ram-Lak response on the padded period; SHEPP multiplies it by
+ * sin(pi nu)/(pi nu), PARZEN by (1 - 2|nu|)^3, NONE applies no filter (only the
+ * pi/N_theta weight and the centre shift). */
+typedef enum {
+  TCP_FILTER_SHEPP = 0,
+  TCP_FILTER_PARZEN = 1,
+  TCP_FILTER_RAMP = 2,
+  TCP_FILTER_NONE = 3
+} tcp_filter_kind;
+
+/* Padding of each row before the filter FFT (Sec. 2.2 pads to FFT-friendly
+ * sizes; Sec. 3 pads to suppress artefacts from objects wider than the field
+ * of view).  The padded length is the next power of two >= 2*ndet. */
+typedef enum { TCP_PAD_EDGE = 0, TCP_PAD_ZERO = 1 } tcp_pad_mode;
+
+typedef struct {
+  void* data;         /* device pointer unless the call says host */
+  int32_t dtype;      /* tcp_dtype */
+  int32_t ndim;       /* 1..4 */
+  int64_t shape[4];   /* outermost first */
+  int64_t stride[4];  /* in elements; stride[ndim-1] must be 1 */
+} tcp_tensor;
+
+/* ---------------------------------------------------------------- status -- */
+
+const char* tcp_status_string(tcp_status s);
+/* Message of the last failing call on this host thread ("" if none). */
+const char* tcp_last_error(void);
+int tcp_version(void);
+
+/* Reads and clears the device error word that kernels set in checked mode
+ * (and on bounded-wait timeouts).  Synchronises `stream`.  *word receives the
+ * raw bits (0 = clean).  Returns TCP_ERR_DEVICE_CHECK if bits were set. */
+tcp_status tcp_device_check(void* stream, uint32_t* word);
+
+/* Turn per-access index checks on (1) or off (0) for later launches. */
+tcp_status tcp_set_checked(int32_t on);
+
+/* Free every cached angle table and filter response (synchronises device). */
+tcp_status tcp_cache_clear(void);
+
+/* ------------------------------------------------------------- normalise -- */
+
+/* Mean over frames of uint16 frames[f][z][j] -> FP32 mean[z][j]
+ * (Sec. 2.2 dark-flat field correction; the paper does not say how frames are
+ * reduced, the arithmetic mean is used).  frames: U16, ndim 3.  mean: F32,
+ * ndim 2, shape [nz][ndet].  nf >= 1. */
+tcp_status tcp_frame_mean(const tcp_tensor* frames, tcp_tensor* mean, void* stream);
+
+/* Dark/flat correction and negative logarithm (Sec. 2.2), computed in FP32:
+ *   r = (raw - dark) / (flat - dark);  r <- 1e-6 if r is not finite or r <= 1e-6;
+ *   sino[z][theta][j] = -ln(r).
+ * raw:  U16 [ntheta][nz][ndet] (any outer strides; a z-chunk of a larger stack
+ *       is a view with the full stack's strides).
+ * dark, flat: F32 [nz][ndet] pre-averaged means, or U16 frames [nf][nz][ndet]
+ *       (then averaged on the device in stream-ordered scratch).
+ * sino: F32, F16 or BF16 [nz][ntheta][ndet]; must not overlap raw.
+ * The transposition from projection-major to sinogram-major is part of the
+ * call. */
+tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                         tcp_tensor* sino, void* stream);
+
+/* ---------------------------------------------------------------- filter -- */
+
+/* One-dimensional FBP filter of every detector row, in place (Sec. 2.2).
+ * Per row: pad to npad = next power of two >= 2*ndet (L = (npad-ndet)/2 on the
+ * left, edge-replicated), FFT, multiply bin k by
+ *   H(k) * pi/ntheta * exp(2 pi i (k/npad) (center - ndet/2))
+ * (Hermitian: the Nyquist bin takes the real part), inverse FFT, crop
+ * [L, L+ndet).  The phase factor moves the rotation axis from `center` to
+ * ndet/2, so the filtered stack is backprojected with center = ndet/2.
+ * Passing center = ndet/2 applies no shift.  sino: F32/F16/BF16
+ * [nz][ntheta][ndet] or [rows][ndet] (then ntheta = rows), FFT math in FP32
+ * with FP64-derived twiddles and responses.  ndet <= 4096 (npad <= 8192). */
+tcp_status tcp_filter(tcp_tensor* sino, int32_t filter, double center, void* stream);
+
+/* tcp_filter with an explicit padding mode (TCP_PAD_EDGE or TCP_PAD_ZERO) and
+ * an explicit angle count for the pi/ntheta weight (ntheta <= 0: take it from
+ * the sinogram shape). */
+tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
+                         int64_t ntheta, void* stream);
+
+/* ----------------------------------------------------------- backproject -- */
+
+/* LineRec backprojection (Sec. 2.2, Sec. 3): for every voxel,
+ *   vol[z][iy][ix] = sum over theta of q_{z,theta}(s(x, y, theta)),
+ * linear interpolation, zero outside the detector.  The FBP weight pi/ntheta
+ * belongs to tcp_filter, so this is the plain sum (the transpose of
+ * tcp_project).  Output is overwritten, not accumulated.
+ * sino:  F32/F16/BF16 [nz][ntheta][ndet]; theta: HOST FP64 [ntheta];
+ * vol:   F32/F16/BF16 [nz][n][n] (n is taken from vol), accumulation in FP32.
+ * The ray coordinate is formed from an FP64 origin per 32x32 voxel tile and
+ * FP32 in-tile offsets (|error| < 1e-5 px). */
+tcp_status tcp_backproject(const tcp_tensor* sino, const double* theta, double center,
+                           tcp_tensor* vol, void* stream);
+
+/* Adjoint Radon projector (not in the paper): the exact transpose of
+ * tcp_backproject with the same interpolation weights,
+ *   sino[z][theta][j] = sum over voxels of vol * (weight of j in q(s)).
+ * vol: F32/F16/BF16 [nz][n][n]; theta: HOST FP64 [ntheta];
+ * sino: F32/F16/BF16 [nz][ntheta][ndet] (ndet from sino), overwritten.
+ * A gather per (theta, j): no atomics, deterministic. */
+tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center,
+                       tcp_tensor* sino, void* stream);
+
+/* Backprojector launch configuration.  k_slices: slices per thread block
+ * (1, 2, 4, 8 or 16); theta_stage: angles staged in shared memory per step
+ * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4). */
+typedef struct {
+  int32_t k_slices;
+  int32_t theta_stage;
+  int32_t rows_per_thread;
+  int32_t reserved;
+} tcp_bp_config;
+
+/* Fix the backprojector configuration for later calls (NULL: automatic). */
+tcp_status tcp_set_backproject_config(const tcp_bp_config* cfg);
+/* Configuration the next call with this shape and dtype pair would use. */
+tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n,
+                                      int32_t sino_dtype, int32_t vol_dtype, tcp_bp_config* cfg);
+
+/* ------------------------------------------------------------- pipeline -- */
+
+typedef struct {
+  int32_t chunk_nz;     /* slices per chunk (default 16 when <= 0) */
+  int32_t sino_dtype;   /* storage of the intermediate sinogram chunk */
+  int32_t filter;       /* tcp_filter_kind */
+  int32_t pad_mode;     /* tcp_pad_mode */
+  int32_t n_buffers;    /* device ring depth, 2 or 3 (default 2) */
+  int32_t reserved[3];
+} tcp_fbp_opts;
+
+/* Chunked FBP (Sec. 2.3): for each chunk of chunk_nz slices, copy the raw
+ * z-slab in, normalise, filter (axis moved to ndet/2) and backproject into
+ * vol[z0:z1].  raw may be a HOST buffer (page-locked for overlap) or a device
+ * buffer; vol likewise.  Host inputs are copied on an internal copy stream into
+ * a ring of device buffers while the previous chunk computes on `stream`; host
+ * outputs are copied back on a third stream.  dark/flat: U16 frames or F32
+ * means, on the device or the host.  Returns after queueing the work; the
+ * result is complete when `stream` is.  Device buffers of the ring are taken
+ * from the stream-ordered allocator. */
+tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                   const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCP_H_ */

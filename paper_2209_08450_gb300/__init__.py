@@ -1,0 +1,170 @@
+"""GB300-native chunked parallel-beam filtered backprojection.
+
+Python face of libtcp (include/tcp.h), following Nikitin, "TomocuPy: efficient
+GPU-based tomographic reconstruction with asynchronous data processing"
+(arXiv 2209.08450): dark/flat normalisation with -log (Sec. 2.2), Fourier
+ramp filtering of detector rows (Sec. 2.2), LineRec backprojection (Sec. 2.2
+and Sec. 3), the adjoint projector, chunked asynchronous FBP (Sec. 2.3) and
+16-bit storage with FP32 accumulation (Sec. 2.1).
+
+Every function marshals arguments and calls one C-ABI entry point; the
+computation is in the library's CUDA kernels.  Tensors live on the GPU
+(torch); angles are radians.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import TcpError, load  # noqa: F401
+
+__all__ = ["frame_mean", "normalize", "filter_", "backproject", "project", "device_check",
+           "set_checked", "cache_clear", "set_backproject_config", "get_backproject_config",
+           "TcpError", "load", "padded_length"]
+
+
+def _as_u16(t: torch.Tensor) -> torch.Tensor:
+    if t.dtype == torch.int16 or (hasattr(torch, "uint16") and t.dtype == torch.uint16):
+        return t
+    raise TypeError("raw/dark/flat frames must be uint16 (or int16 holding the same bits)")
+
+
+def padded_length(ndet: int) -> int:
+    n = 1
+    while n < 2 * ndet:
+        n *= 2
+    return n
+
+
+def frame_mean(frames: torch.Tensor, stream=None) -> torch.Tensor:
+    """FP32 mean over frames of uint16 frames[f][z][j] (dark or flat)."""
+    frames = _as_u16(frames)
+    out = torch.empty(frames.shape[1:], dtype=torch.float32, device=frames.device)
+    a, b = _lib.desc(frames, _lib.U16), _lib.desc(out)
+    _lib.call("tcp_frame_mean", _lib.ref(a), _lib.ref(b), _lib.stream_ptr(stream))
+    return out
+
+
+def normalize(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, out: torch.Tensor | None = None,
+              dtype=torch.float32, stream=None) -> torch.Tensor:
+    """raw uint16 [theta][z][j] -> sinogram [z][theta][j] = -ln((raw-dark)/(flat-dark)).
+
+    dark/flat are uint16 frames [nf][z][j] or FP32 means [z][j]."""
+    raw = _as_u16(raw)
+    nt, nz, nd = raw.shape
+    if out is None:
+        out = torch.empty((nz, nt, nd), dtype=_lib.DTYPES[dtype], device=raw.device)
+
+    def dd(x):
+        return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
+
+    r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
+    _lib.call("tcp_normalize", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.stream_ptr(stream))
+    return out
+
+
+def filter_(sino: torch.Tensor, center: float, filter: str = "shepp", pad: str = "edge",
+            ntheta: int | None = None, stream=None) -> torch.Tensor:
+    """In-place FBP filter of every detector row; moves the axis from `center` to ndet/2."""
+    d = _lib.desc(sino)
+    _lib.call("tcp_filter_ex", _lib.ref(d), _lib.FILTERS[filter], float(center), _lib.PADS[pad],
+              int(ntheta or 0), _lib.stream_ptr(stream))
+    return sino
+
+
+def backproject(sino: torch.Tensor, theta, center: float, n: int | None = None,
+                out: torch.Tensor | None = None, dtype=None, stream=None) -> torch.Tensor:
+    """LineRec backprojection sino[z][theta][j] -> vol[z][n][n] (sum over angles)."""
+    th = _lib.theta_array(theta)
+    nz, nt, nd = sino.shape
+    if out is None:
+        n = nd if n is None else n
+        out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype or sino.dtype], device=sino.device)
+    a, b = _lib.desc(sino), _lib.desc(out)
+    _lib.call("tcp_backproject", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
+              _lib.stream_ptr(stream))
+    return out
+
+
+def project(vol: torch.Tensor, theta, center: float, ndet: int | None = None,
+            out: torch.Tensor | None = None, dtype=None, stream=None) -> torch.Tensor:
+    """Adjoint projector vol[z][n][n] -> sino[z][theta][ndet]."""
+    th = _lib.theta_array(theta)
+    nz, n, _ = vol.shape
+    if out is None:
+        ndet = n if ndet is None else ndet
+        out = torch.empty((nz, th.shape[0], ndet), dtype=_lib.DTYPES[dtype or vol.dtype], device=vol.device)
+    a, b = _lib.desc(vol), _lib.desc(out)
+    _lib.call("tcp_project", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
+              _lib.stream_ptr(stream))
+    return out
+
+
+def device_check(stream=None) -> int:
+    """Read and clear the device error word (synchronises the stream); raises if set."""
+    w = ctypes.c_uint32(0)
+    _lib.call("tcp_device_check", _lib.stream_ptr(stream), ctypes.byref(w))
+    return w.value
+
+
+def set_checked(on: bool) -> None:
+    _lib.call("tcp_set_checked", int(bool(on)))
+
+
+def cache_clear() -> None:
+    _lib.call("tcp_cache_clear")
+
+
+def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, rows_per_thread: int = 4) -> None:
+    if k_slices is None:
+        _lib.load().tcp_set_backproject_config(None)
+        return
+    c = _lib.BpConfig(k_slices, theta_stage, rows_per_thread, 0)
+    _lib.call("tcp_set_backproject_config", ctypes.byref(c))
+
+
+def get_backproject_config(nz, ntheta, ndet, n, sino_dtype=torch.float32, vol_dtype=torch.float32) -> tuple:
+    c = _lib.BpConfig()
+    _lib.call("tcp_get_backproject_config", nz, ntheta, ndet, n, _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype]],
+              _lib._TORCH_DTYPE[_lib.DTYPES[vol_dtype]], ctypes.byref(c))
+    return (c.k_slices, c.theta_stage, c.rows_per_thread)
+
+
+def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center: float,
+        out: torch.Tensor | None = None, dtype=torch.float32, n: int | None = None, chunk_nz: int = 16,
+        filter: str = "shepp", pad: str = "edge", sino_dtype=None, n_buffers: int = 2,
+        stream=None) -> torch.Tensor:
+    """Chunked FBP (normalise -> filter -> backproject per z-slab, Sec. 2.3).
+
+    raw uint16 [theta][z][j] and the output may be CUDA tensors or host tensors
+    (page-locked host memory lets the slab copies overlap compute).  dark/flat
+    are uint16 frames [nf][z][j] or FP32 means [z][j].  The volume is
+    reconstructed about the filtered axis ndet/2 with the `center` shift folded
+    into the filter.  Returns `out` once the work is queued on the stream."""
+    raw = _as_u16(raw)
+    nt, nz, nd = raw.shape
+    if out is None:
+        n = nd if n is None else n
+        out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype], device=raw.device,
+                          pin_memory=raw.device.type == "cpu")
+    th = _lib.theta_array(theta)
+
+    def dd(x):
+        return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
+
+    opts = _lib.FbpOpts()
+    opts.chunk_nz = chunk_nz
+    opts.sino_dtype = _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype or out.dtype]]
+    opts.filter = _lib.FILTERS[filter]
+    opts.pad_mode = _lib.PADS[pad]
+    opts.n_buffers = n_buffers
+    r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
+    _lib.call("tcp_fbp", _lib.ref(r), _lib.ref(d), _lib.ref(f), th.ctypes.data_as(ctypes.c_void_p), float(center),
+              _lib.ref(o), ctypes.byref(opts), _lib.stream_ptr(stream))
+    return out
+
+
+__all__.append("fbp")

@@ -1,0 +1,519 @@
+// C-ABI entry points of libtcp: argument checks, views, cached device tables
+// (FP64 angle tables, FP64-derived filter responses and twiddles) and error
+// reporting.  Every compute step runs in the CUDA kernels of this library.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "tcp_internal.cuh"
+
+namespace tcp {
+
+// ------------------------------------------------------------ error state --
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+tcp_status fail(tcp_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+tcp_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TCP_ERR_OOM : TCP_ERR_CUDA;
+}
+
+__device__ uint32_t g_error_word;
+
+static std::mutex g_mu;
+static std::unordered_map<int, uint32_t*> g_err_ptr;
+
+uint32_t* device_error_word() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_err_ptr.find(dev);
+  if (it != g_err_ptr.end()) return it->second;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
+  g_err_ptr[dev] = reinterpret_cast<uint32_t*>(p);
+  return reinterpret_cast<uint32_t*>(p);
+}
+
+static bool g_checked = [] {
+  const char* e = getenv("TCP_CHECKED");
+  return e && e[0] == '1';
+}();
+bool checked_mode() { return g_checked; }
+
+// ------------------------------------------------------------------ caches --
+
+static uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+struct TrigEntry {
+  std::vector<double> theta;
+  double2* dev = nullptr;
+};
+static std::unordered_map<uint64_t, std::vector<TrigEntry>> g_trig;  // key: hash ^ device
+
+tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out) {
+  int dev = 0;
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
+  const uint64_t key = fnv1a(theta, sizeof(double) * (size_t)n) ^ ((uint64_t)(dev + 1) * 0x9e3779b97f4a7c15ull) ^
+                       (uint64_t)n;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& bucket = g_trig[key];
+  for (auto& e : bucket)
+    if ((int64_t)e.theta.size() == n && std::memcmp(e.theta.data(), theta, sizeof(double) * (size_t)n) == 0) {
+      out->dev = e.dev;
+      out->n = n;
+      return TCP_OK;
+    }
+  std::vector<double2> h((size_t)std::max<int64_t>(n, 1));
+  for (int64_t i = 0; i < n; ++i) h[(size_t)i] = make_double2(std::cos(theta[i]), std::sin(theta[i]));
+  TrigEntry e;
+  e.theta.assign(theta, theta + n);
+  TCP_CUDA_TRY(cudaMalloc(&e.dev, h.size() * sizeof(double2)));
+  cudaError_t err = cudaMemcpy(e.dev, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(e.dev);
+    return cuda_fail(err, "upload angle table");
+  }
+  bucket.push_back(e);
+  out->dev = e.dev;
+  out->n = n;
+  return TCP_OK;
+}
+
+int64_t padded_length(int64_t ndet) {
+  int64_t n = 1;
+  while (n < 2 * ndet) n *= 2;
+  return n;
+}
+
+// In-place iterative radix-2 FFT in FP64 (host), forward: X_k = sum x_m e^{-2 pi i km/N}.
+static void fft64(std::vector<std::complex<double>>& x) {
+  const size_t N = x.size();
+  for (size_t i = 1, j = 0; i < N; ++i) {
+    size_t bit = N >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(x[i], x[j]);
+  }
+  for (size_t len = 2; len <= N; len <<= 1) {
+    for (size_t i = 0; i < N; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)len;
+        const std::complex<double> w(std::cos(ang), std::sin(ang));
+        const std::complex<double> u = x[i + k], v = x[i + k + len / 2] * w;
+        x[i + k] = u + v;
+        x[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+// Band-limited ramp on the padded period: DFT of the spatial Ram-Lak kernel
+// h[0] = 1/4, h[m] = -1/(pi^2 m^2) for odd m, 0 for even m != 0, truncated to
+// -N/2 <= m < N/2.  The window multiplies it: Shepp-Logan sin(pi nu)/(pi nu),
+// Parzen (1 - 2 nu)^3.
+static std::vector<double> filter_response(int64_t npad, int32_t filter) {
+  std::vector<double> H((size_t)npad / 2 + 1, 1.0);
+  if (filter == TCP_FILTER_NONE) return H;
+  std::vector<std::complex<double>> h((size_t)npad, 0.0);
+  h[0] = 0.25;
+  for (int64_t m = 1; m < npad / 2; m += 2) {
+    const double v = -1.0 / (M_PI * M_PI * (double)m * (double)m);
+    h[(size_t)m] = v;
+    h[(size_t)(npad - m)] = v;
+  }
+  fft64(h);
+  for (int64_t k = 0; k <= npad / 2; ++k) {
+    const double nu = (double)k / (double)npad;
+    double w = 1.0;
+    if (filter == TCP_FILTER_SHEPP) w = k == 0 ? 1.0 : std::sin(M_PI * nu) / (M_PI * nu);
+    else if (filter == TCP_FILTER_PARZEN) w = std::pow(1.0 - 2.0 * nu, 3);
+    H[(size_t)k] = h[(size_t)k].real() * w;
+  }
+  return H;
+}
+
+struct FiltKey {
+  int dev;
+  int64_t npad, ndet, ntheta;
+  int32_t filter;
+  double center;
+  bool operator==(const FiltKey& o) const {
+    return dev == o.dev && npad == o.npad && ndet == o.ndet && ntheta == o.ntheta && filter == o.filter &&
+           std::memcmp(&center, &o.center, sizeof(double)) == 0;
+  }
+};
+struct FiltKeyHash {
+  size_t operator()(const FiltKey& k) const { return (size_t)fnv1a(&k, sizeof(FiltKey)); }
+};
+static std::unordered_map<FiltKey, float2*, FiltKeyHash> g_resp;
+static std::unordered_map<uint64_t, float2*> g_tw;  // (dev << 32) | npad
+
+tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double center, FilterTable* out) {
+  int dev = 0;
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t npad = padded_length(ndet);
+  FiltKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.dev = dev;
+  key.npad = npad;
+  key.ndet = ndet;
+  key.ntheta = ntheta;
+  key.filter = filter;
+  key.center = center;
+  std::lock_guard<std::mutex> lk(g_mu);
+  out->npad = (int)npad;
+  const uint64_t twkey = ((uint64_t)(uint32_t)dev << 32) | (uint64_t)npad;
+  auto tit = g_tw.find(twkey);
+  if (tit == g_tw.end()) {
+    std::vector<float2> tw((size_t)npad);
+    for (int64_t m = 0; m < npad; ++m) {
+      const double ang = -2.0 * M_PI * (double)m / (double)npad;
+      tw[(size_t)m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    float2* d = nullptr;
+    TCP_CUDA_TRY(cudaMalloc(&d, tw.size() * sizeof(float2)));
+    cudaError_t e = cudaMemcpy(d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "upload twiddles");
+    }
+    tit = g_tw.emplace(twkey, d).first;
+  }
+  out->twiddle = tit->second;
+  auto rit = g_resp.find(key);
+  if (rit == g_resp.end()) {
+    const std::vector<double> H = filter_response(npad, filter);
+    const double shift = center - 0.5 * (double)ndet;
+    const double scale = M_PI / (double)ntheta / (double)npad;
+    std::vector<float2> F(H.size());
+    for (int64_t k = 0; k <= npad / 2; ++k) {
+      const double ph = 2.0 * M_PI * ((double)k / (double)npad) * shift;
+      double re = H[(size_t)k] * scale * std::cos(ph), im = H[(size_t)k] * scale * std::sin(ph);
+      if (k == npad / 2) im = 0.0;  // Hermitian Nyquist bin: real part only
+      F[(size_t)k] = make_float2((float)re, (float)im);
+    }
+    float2* d = nullptr;
+    TCP_CUDA_TRY(cudaMalloc(&d, F.size() * sizeof(float2)));
+    cudaError_t e = cudaMemcpy(d, F.data(), F.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "upload filter response");
+    }
+    rit = g_resp.emplace(key, d).first;
+  }
+  out->response = rit->second;
+  return TCP_OK;
+}
+
+static tcp_status cache_clear() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  TCP_CUDA_TRY(cudaDeviceSynchronize());
+  for (auto& kv : g_trig)
+    for (auto& e : kv.second) cudaFree(e.dev);
+  g_trig.clear();
+  for (auto& kv : g_resp) cudaFree(kv.second);
+  g_resp.clear();
+  for (auto& kv : g_tw) cudaFree(kv.second);
+  g_tw.clear();
+  return TCP_OK;
+}
+
+// --------------------------------------------------------- argument checks --
+
+static int dtype_size(int dt) {
+  switch (dt) {
+    case TCP_U16: case TCP_F16: case TCP_BF16: return 2;
+    case TCP_F32: return 4;
+  }
+  return 0;
+}
+
+static tcp_status check_tensor(const tcp_tensor* t, const char* name, int ndim_lo, int ndim_hi) {
+  if (!t) return fail(TCP_ERR_ARG, std::string(name) + ": null tensor");
+  if (t->ndim < ndim_lo || t->ndim > ndim_hi)
+    return fail(TCP_ERR_SHAPE, std::string(name) + ": wrong number of dimensions");
+  if (dtype_size(t->dtype) == 0) return fail(TCP_ERR_DTYPE, std::string(name) + ": unknown dtype");
+  int64_t numel = 1;
+  for (int i = 0; i < t->ndim; ++i) {
+    if (t->shape[i] < 0) return fail(TCP_ERR_SHAPE, std::string(name) + ": negative extent");
+    if (t->shape[i] > (int64_t)INT32_MAX) return fail(TCP_ERR_SHAPE, std::string(name) + ": extent too large");
+    numel *= t->shape[i];
+  }
+  if (numel > 0) {
+    if (!t->data) return fail(TCP_ERR_ARG, std::string(name) + ": null data");
+    if (t->shape[t->ndim - 1] > 1 && t->stride[t->ndim - 1] != 1)
+      return fail(TCP_ERR_ALIGN, std::string(name) + ": innermost stride must be 1");
+    if ((uintptr_t)t->data % dtype_size(t->dtype) != 0)
+      return fail(TCP_ERR_ALIGN, std::string(name) + ": data not aligned to its dtype");
+  }
+  return TCP_OK;
+}
+
+// View of a 2- or 3-d tensor as [d0][d1][d2].
+static View3 view3(const tcp_tensor* t) {
+  View3 v;
+  v.p = t->data;
+  v.dtype = t->dtype;
+  if (t->ndim == 3) {
+    v.d0 = t->shape[0];
+    v.d1 = t->shape[1];
+    v.d2 = t->shape[2];
+    v.s0 = t->stride[0];
+    v.s1 = t->stride[1];
+  } else if (t->ndim == 2) {
+    v.d0 = 1;
+    v.d1 = t->shape[0];
+    v.d2 = t->shape[1];
+    v.s0 = 0;
+    v.s1 = t->stride[0];
+  } else {
+    v.d0 = 1;
+    v.d1 = 1;
+    v.d2 = t->shape[0];
+    v.s0 = 0;
+    v.s1 = 0;
+  }
+  return v;
+}
+
+static int64_t numel(const tcp_tensor* t) {
+  int64_t n = 1;
+  for (int i = 0; i < t->ndim; ++i) n *= t->shape[i];
+  return n;
+}
+
+// Byte range [lo, hi) covered by a tensor.
+static void extent(const tcp_tensor* t, uintptr_t* lo, uintptr_t* hi) {
+  int64_t last = 0;
+  for (int i = 0; i < t->ndim; ++i) last += (t->shape[i] - 1) * t->stride[i];
+  *lo = (uintptr_t)t->data;
+  *hi = (uintptr_t)t->data + (uintptr_t)(last + 1) * dtype_size(t->dtype);
+}
+static bool overlap(const tcp_tensor* a, const tcp_tensor* b) {
+  if (numel(a) == 0 || numel(b) == 0) return false;
+  uintptr_t al, ah, bl, bh;
+  extent(a, &al, &ah);
+  extent(b, &bl, &bh);
+  return al < bh && bl < ah;
+}
+
+static bool is_float(int dt) { return dt == TCP_F32 || dt == TCP_F16 || dt == TCP_BF16; }
+
+static tcp_bp_config g_bp_override{0, 0, 0, 0};
+
+}  // namespace tcp
+
+using namespace tcp;
+
+extern "C" {
+
+const char* tcp_status_string(tcp_status s) {
+  switch (s) {
+    case TCP_OK: return "ok";
+    case TCP_ERR_ARG: return "invalid argument";
+    case TCP_ERR_SHAPE: return "invalid shape";
+    case TCP_ERR_DTYPE: return "invalid dtype";
+    case TCP_ERR_ALIGN: return "invalid stride or alignment";
+    case TCP_ERR_CUDA: return "CUDA error";
+    case TCP_ERR_OOM: return "out of memory";
+    case TCP_ERR_TIMEOUT: return "device wait timed out";
+    case TCP_ERR_DEVICE_CHECK: return "device index check failed";
+    case TCP_ERR_UNSUPPORTED: return "unsupported";
+    case TCP_ERR_ALIAS: return "overlapping input and output";
+  }
+  return "unknown status";
+}
+
+const char* tcp_last_error(void) { return g_last_error.c_str(); }
+
+int tcp_version(void) { return TCP_VERSION; }
+
+tcp_status tcp_set_checked(int32_t on) {
+  g_checked = on != 0;
+  return TCP_OK;
+}
+
+tcp_status tcp_cache_clear(void) { return cache_clear(); }
+
+tcp_status tcp_device_check(void* stream, uint32_t* word) {
+  uint32_t* p = device_error_word();
+  if (!p) return fail(TCP_ERR_CUDA, "device error word unavailable");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t h = 0;
+  TCP_CUDA_TRY(cudaMemcpyAsync(&h, p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TCP_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(uint32_t), st));
+  TCP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (word) *word = h;
+  if (h) return fail(TCP_ERR_DEVICE_CHECK, "device error word set: " + std::to_string(h));
+  return TCP_OK;
+}
+
+tcp_status tcp_frame_mean(const tcp_tensor* frames, tcp_tensor* mean, void* stream) {
+  tcp_status s;
+  if ((s = check_tensor(frames, "frames", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(mean, "mean", 2, 2)) != TCP_OK) return s;
+  if (frames->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "frames must be U16");
+  if (mean->dtype != TCP_F32) return fail(TCP_ERR_DTYPE, "mean must be F32");
+  if (mean->shape[0] != frames->shape[1] || mean->shape[1] != frames->shape[2])
+    return fail(TCP_ERR_SHAPE, "mean must be [nz][ndet] of frames [nf][nz][ndet]");
+  if (frames->shape[0] < 1 && numel(mean) > 0) return fail(TCP_ERR_SHAPE, "need at least one frame");
+  return launch_frame_mean(view3(frames), view3(mean), reinterpret_cast<cudaStream_t>(stream));
+}
+
+tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat, tcp_tensor* sino,
+                         void* stream) {
+  tcp_status s;
+  if ((s = check_tensor(raw, "raw", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(dark, "dark", 2, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(flat, "flat", 2, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+  if (raw->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "raw must be U16");
+  if (!is_float(sino->dtype)) return fail(TCP_ERR_DTYPE, "sino must be F32, F16 or BF16");
+  const int64_t nt = raw->shape[0], nz = raw->shape[1], nd = raw->shape[2];
+  if (sino->shape[0] != nz || sino->shape[1] != nt || sino->shape[2] != nd)
+    return fail(TCP_ERR_SHAPE, "sino must be [nz][ntheta][ndet] of raw [ntheta][nz][ndet]");
+  for (const tcp_tensor* df : {dark, flat}) {
+    if (df->ndim == 2) {
+      if (df->dtype != TCP_F32) return fail(TCP_ERR_DTYPE, "2-d dark/flat must be F32 means");
+      if (df->shape[0] != nz || df->shape[1] != nd) return fail(TCP_ERR_SHAPE, "dark/flat means must be [nz][ndet]");
+    } else {
+      if (df->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "3-d dark/flat must be U16 frames");
+      if (df->shape[1] != nz || df->shape[2] != nd) return fail(TCP_ERR_SHAPE, "dark/flat frames must be [nf][nz][ndet]");
+      if (df->shape[0] < 1 && nz * nd > 0) return fail(TCP_ERR_SHAPE, "dark/flat need at least one frame");
+    }
+  }
+  if (overlap(raw, sino)) return fail(TCP_ERR_ALIAS, "raw and sino overlap");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (numel(sino) == 0) return TCP_OK;
+  float* scratch = nullptr;
+  View3 dv = view3(dark), fv = view3(flat);
+  const bool need = dark->ndim == 3 || flat->ndim == 3;
+  if (need) {
+    TCP_CUDA_TRY(cudaMallocAsync((void**)&scratch, sizeof(float) * 2 * (size_t)(nz * nd), st));
+    View3 m;
+    m.dtype = TCP_F32;
+    m.d0 = 1;
+    m.d1 = nz;
+    m.d2 = nd;
+    m.s0 = 0;
+    m.s1 = nd;
+    if (dark->ndim == 3) {
+      m.p = scratch;
+      if ((s = launch_frame_mean(dv, m, st)) != TCP_OK) { cudaFreeAsync(scratch, st); return s; }
+      dv = m;
+    }
+    if (flat->ndim == 3) {
+      m.p = scratch + nz * nd;
+      if ((s = launch_frame_mean(fv, m, st)) != TCP_OK) { cudaFreeAsync(scratch, st); return s; }
+      fv = m;
+    }
+  }
+  s = launch_normalize(view3(raw), dv, fv, view3(sino), st);
+  if (scratch) {
+    cudaError_t e = cudaFreeAsync(scratch, st);
+    if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+  }
+  return s;
+}
+
+tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, int64_t ntheta,
+                         void* stream) {
+  tcp_status s;
+  if ((s = check_tensor(sino, "sino", 2, 3)) != TCP_OK) return s;
+  if (!is_float(sino->dtype)) return fail(TCP_ERR_DTYPE, "sino must be F32, F16 or BF16");
+  if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "unknown filter");
+  if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  View3 v = view3(sino);
+  if (v.d2 > 4096) return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
+  const int64_t nt = ntheta > 0 ? ntheta : v.d1;
+  if (numel(sino) == 0) return TCP_OK;
+  FilterTable ft;
+  if ((s = get_filter_table(v.d2, filter, nt, center, &ft)) != TCP_OK) return s;
+  return launch_filter(v, ft, pad_mode, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tcp_status tcp_filter(tcp_tensor* sino, int32_t filter, double center, void* stream) {
+  return tcp_filter_ex(sino, filter, center, TCP_PAD_EDGE, 0, stream);
+}
+
+tcp_status tcp_set_backproject_config(const tcp_bp_config* cfg) {
+  if (!cfg) {
+    g_bp_override = tcp_bp_config{0, 0, 0, 0};
+    return TCP_OK;
+  }
+  if (!valid_bp_config(*cfg)) return fail(TCP_ERR_UNSUPPORTED, "no backprojector instantiated for this config");
+  g_bp_override = *cfg;
+  return TCP_OK;
+}
+
+tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n, int32_t sdt, int32_t vdt,
+                                      tcp_bp_config* cfg) {
+  if (!cfg) return fail(TCP_ERR_ARG, "null config");
+  *cfg = g_bp_override.k_slices ? g_bp_override : default_bp_config(nz, ntheta, ndet, n, sdt, vdt);
+  return TCP_OK;
+}
+
+tcp_status tcp_backproject(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol,
+                           void* stream) {
+  tcp_status s;
+  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
+  if (!is_float(sino->dtype) || !is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "sino/vol must be F32, F16 or BF16");
+  if (vol->shape[0] != sino->shape[0]) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
+  if (vol->shape[1] != vol->shape[2]) return fail(TCP_ERR_SHAPE, "vol slices must be square [n][n]");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  const int64_t nt = sino->shape[1];
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "theta is null");
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "theta must be finite");
+  if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (numel(vol) == 0) return TCP_OK;
+  if (nt == 0 || sino->shape[2] == 0) {  // no rays: the sum is zero
+    for (int64_t z = 0; z < vol->shape[0]; ++z)
+      TCP_CUDA_TRY(cudaMemset2DAsync((char*)vol->data + z * vol->stride[0] * dtype_size(vol->dtype),
+                                     vol->stride[1] * dtype_size(vol->dtype), 0,
+                                     vol->shape[2] * dtype_size(vol->dtype), vol->shape[1], st));
+    return TCP_OK;
+  }
+  TrigTable trig;
+  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  tcp_bp_config cfg;
+  tcp_get_backproject_config(sino->shape[0], nt, sino->shape[2], vol->shape[1], sino->dtype, vol->dtype, &cfg);
+  return launch_backproject(view3(sino), trig, center, view3(vol), cfg, st);
+}
+
+tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {
+  tcp_status s;
+  if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+  if (!is_float(sino->dtype) || !is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "sino/vol must be F32, F16 or BF16");
+  if (vol->shape[0] != sino->shape[0]) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
+  if (vol->shape[1] != vol->shape[2]) return fail(TCP_ERR_SHAPE, "vol slices must be square [n][n]");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  const int64_t nt = sino->shape[1];
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "theta is null");
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "theta must be finite");
+  if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
+  if (numel(sino) == 0) return TCP_OK;
+  TrigTable trig;
+  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  return launch_project(view3(vol), trig, center, view3(sino), reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Radon projector, the adjoint of the LineRec backprojector (not in the
+// paper; it makes backprojection differentiable and enables least-squares
+// reconstruction):
+//   sino[z][theta][j] = sum over voxels of vol * weight_j(s(voxel, theta)),
+// where weight_j is the linear-interpolation weight that the backprojector
+// gives detector pixel j at that voxel: (1 - w) if floor(s) == j, w if
+// floor(s) + 1 == j, else 0.
+//
+// Gather form, one thread per (theta, j) and K slices: no atomics, a fixed
+// summation order, deterministic.  The thread walks the major axis of the ray
+// (y when |cos| >= |sin|, else x) and visits the <= 3 voxels per step whose
+// ray coordinate can lie in [j - 1, j + 1).  Each candidate's coordinate is
+// recomputed with the backprojector's canonical tile geometry, from a per-call
+// table of FP64 tile origins built by the same function, so the two operators
+// share bit-identical weights.
+#include "tcp_internal.cuh"
+
+namespace tcp {
+namespace {
+
+__global__ void k_origin_table(const double2* trig, int ntheta, int ntx, double half_n, double center,
+                               int2* out) {
+  const int64_t total = (int64_t)ntheta * ntx * ntx;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e / ((int64_t)ntx * ntx));
+    const int rem = (int)(e - (int64_t)t * ntx * ntx);
+    const int gy = rem / ntx, gx = rem - gy * ntx;
+    const TileOrigin o = tile_origin(gx, gy, half_n, center, trig[t]);
+    out[e] = make_int2(o.i0, __float_as_int(o.f0));
+  }
+}
+
+template <class TS> struct WRound {
+  static __device__ __forceinline__ float r(float w) { return w; }
+};
+template <> struct WRound<__half> {
+  static __device__ __forceinline__ float r(float w) { return __half2float(__float2half_rn(w)); }
+};
+template <> struct WRound<__nv_bfloat16> {
+  static __device__ __forceinline__ float r(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
+};
+
+struct PjArgs {
+  const void* vol;
+  int64_t v_z, v_y;
+  int nz, n, ntx;
+  void* sino;
+  int64_t s_z, s_t;
+  int ntheta, ndet;
+  const double2* trig;
+  const int2* orig;
+  double center, half_n;
+};
+
+constexpr int kPjThreads = 128;
+
+template <class TV, class TS, int K>
+__global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
+  const int t = blockIdx.y;
+  const int j = blockIdx.x * kPjThreads + threadIdx.x;
+  const int z0 = blockIdx.z * K;
+  if (j >= a.ndet) return;
+  const double2 cs = a.trig[t];
+  const float c = __double2float_rn(cs.x), s = __double2float_rn(cs.y);
+  const bool ymajor = fabs(cs.x) >= fabs(cs.y);
+  const float inv = 1.0f / (ymajor ? c : s);
+  const float hr = fabsf(inv) + 0.02f;
+  const float hn = (float)a.half_n;
+  const float jc = (float)((double)j - a.center);
+  const int2* orig = a.orig + (int64_t)t * a.ntx * a.ntx;
+  const TV* vol = reinterpret_cast<const TV*>(a.vol);
+
+  float acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.f;
+
+  for (int m = 0; m < a.n; ++m) {
+    const float other = (float)m - hn;
+    const float uc = (jc - other * (ymajor ? s : c)) * inv + hn;
+    const int lo = max(0, (int)ceilf(uc - hr));
+    const int hi = min(a.n - 1, (int)floorf(uc + hr));
+    for (int u = lo; u <= hi; ++u) {
+      const int ix = ymajor ? u : m, iy = ymajor ? m : u;
+      const int2 o = __ldg(orig + (iy >> 5) * a.ntx + (ix >> 5));
+      const float sr = rel_coord(__int_as_float(o.y), c, s, (float)(ix & 31), (float)(iy & 31));
+      const float fl = floorf(sr);
+      const float w = sr - fl;
+      const int i = o.x + (int)fl;
+      float wt = 0.f;
+      if (i == j) wt = WRound<TS>::r(1.f - w);
+      else if (i + 1 == j) wt = WRound<TS>::r(w);
+      if (wt != 0.f) {
+        const TV* p = vol + (int64_t)iy * a.v_y + ix;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (z0 + k < a.nz) acc[k] = __fmaf_rn(wt, Store<TV>::load(p + (int64_t)(z0 + k) * a.v_z), acc[k]);
+      }
+    }
+  }
+  TS* out = reinterpret_cast<TS*>(a.sino);
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (z0 + k < a.nz) Store<TS>::put(out + (int64_t)(z0 + k) * a.s_z + (int64_t)t * a.s_t + j, acc[k]);
+}
+
+template <class TV, class TS>
+void (*pick(int K))(PjArgs) {
+  switch (K) {
+    case 1: return k_project<TV, TS, 1>;
+    case 2: return k_project<TV, TS, 2>;
+    case 4: return k_project<TV, TS, 4>;
+    default: return k_project<TV, TS, 8>;
+  }
+}
+
+template <class TV>
+void (*pick_s(int sdt, int K))(PjArgs) {
+  switch (sdt) {
+    case TCP_F32: return pick<TV, float>(K);
+    case TCP_F16: return pick<TV, __half>(K);
+    case TCP_BF16: return pick<TV, __nv_bfloat16>(K);
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
+                          cudaStream_t st) {
+  const int nz = (int)vol.d0, n = (int)vol.d1, nt = (int)sino.d1, nd = (int)sino.d2;
+  if (nz == 0 || nt == 0 || nd == 0) return TCP_OK;
+  const int K = nz >= 8 ? 8 : (nz >= 4 ? 4 : (nz >= 2 ? 2 : 1));
+  void (*k)(PjArgs) = nullptr;
+  switch (vol.dtype) {
+    case TCP_F32: k = pick_s<float>(sino.dtype, K); break;
+    case TCP_F16: k = pick_s<__half>(sino.dtype, K); break;
+    case TCP_BF16: k = pick_s<__nv_bfloat16>(sino.dtype, K); break;
+  }
+  if (!k) return fail(TCP_ERR_UNSUPPORTED, "project: no kernel for this dtype pair");
+  PjArgs a;
+  a.vol = vol.p;
+  a.v_z = vol.s0;
+  a.v_y = vol.s1;
+  a.nz = nz;
+  a.n = n;
+  a.ntx = (n + kTile - 1) / kTile;
+  a.sino = sino.p;
+  a.s_z = sino.s0;
+  a.s_t = sino.s1;
+  a.ntheta = nt;
+  a.ndet = nd;
+  a.trig = trig.dev;
+  a.center = center;
+  a.half_n = 0.5 * (double)n;
+  int2* orig = nullptr;
+  const size_t bytes = (size_t)nt * a.ntx * a.ntx * sizeof(int2);
+  TCP_CUDA_TRY(cudaMallocAsync((void**)&orig, bytes > 0 ? bytes : 8, st));
+  if (n > 0) {
+    const int64_t total = (int64_t)nt * a.ntx * a.ntx;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    k_origin_table<<<blocks, 256, 0, st>>>(trig.dev, nt, a.ntx, a.half_n, center, orig);
+  }
+  a.orig = orig;
+  dim3 grid((unsigned)((nd + kPjThreads - 1) / kPjThreads), (unsigned)nt, (unsigned)((nz + K - 1) / K));
+  cudaError_t e1 = cudaSuccess;
+  if (grid.y > 65535u || grid.z > 65535u) {
+    cudaFreeAsync(orig, st);
+    return fail(TCP_ERR_SHAPE, "project: too many angles or slice blocks for one launch");
+  }
+  k<<<grid, kPjThreads, 0, st>>>(a);
+  e1 = cudaGetLastError();
+  cudaError_t e2 = cudaFreeAsync(orig, st);
+  if (e1 != cudaSuccess) return cuda_fail(e1, "project kernel launch");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  return TCP_OK;
+}
+
+}  // namespace tcp

@@ -1,0 +1,285 @@
+// Chunked asynchronous FBP (Sec. 2.3 of the TomocuPy paper): the volume is
+// reconstructed by z-slabs ("chunks" of slices).  While chunk k is normalised,
+// filtered and backprojected on the caller's stream, the raw slab of chunk
+// k+1 is copied host->device on a copy stream and the volume slab of chunk
+// k-1 is copied device->host on a third stream, through a ring of device
+// buffers guarded by events.  Device-resident inputs and outputs skip the
+// corresponding copies.  Every compute step is one of the library's kernels.
+#include <cmath>
+#include <vector>
+
+#include "tcp_internal.cuh"
+
+namespace tcp {
+namespace {
+
+enum Where { kDevice, kPinned, kPageable };
+
+Where where(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kPageable;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged: return kDevice;
+    case cudaMemoryTypeHost: return kPinned;
+    default: return kPageable;
+  }
+}
+
+int esize(int dt) { return dt == TCP_F32 ? 4 : 2; }
+
+// Everything created for one call; released in stream order at the end.
+struct Scope {
+  cudaStream_t st;
+  std::vector<void*> dev;
+  std::vector<cudaEvent_t> ev;
+  std::vector<cudaStream_t> streams;
+  tcp_status alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    dev.push_back(*p);
+    return TCP_OK;
+  }
+  tcp_status event(cudaEvent_t* e) {
+    cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (r != cudaSuccess) return cuda_fail(r, "cudaEventCreate");
+    ev.push_back(*e);
+    return TCP_OK;
+  }
+  tcp_status stream(cudaStream_t* s) {
+    cudaError_t r = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+    if (r != cudaSuccess) return cuda_fail(r, "cudaStreamCreate");
+    streams.push_back(*s);
+    return TCP_OK;
+  }
+  ~Scope() {
+    // Join every side stream first, so that buffers are released in stream
+    // order after their last use on any stream (also on error paths).
+    for (cudaStream_t s : streams) {
+      cudaEvent_t j;
+      if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(j, s);
+        cudaStreamWaitEvent(st, j, 0);
+        cudaEventDestroy(j);
+      }
+    }
+    for (void* p : dev) cudaFreeAsync(p, st);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaStream_t s : streams) cudaStreamDestroy(s);
+  }
+};
+
+#define TRY_S(x)                      \
+  do {                                \
+    tcp_status s_ = (x);              \
+    if (s_ != TCP_OK) return s_;      \
+  } while (0)
+
+// Bring dark/flat (U16 frames or F32 means, host or device) to FP32 means on
+// the device, laid out [nz][nd].
+tcp_status device_means(const tcp_tensor* t, int64_t nz, int64_t nd, Scope& sc, View3* out) {
+  const Where w = where(t->data);
+  View3 v;
+  v.dtype = t->dtype;
+  if (t->ndim == 3) {
+    v.d0 = t->shape[0]; v.d1 = t->shape[1]; v.d2 = t->shape[2];
+    v.s0 = t->stride[0]; v.s1 = t->stride[1];
+  } else {
+    v.d0 = 1; v.d1 = t->shape[0]; v.d2 = t->shape[1];
+    v.s0 = 0; v.s1 = t->stride[0];
+  }
+  v.p = t->data;
+  if (w != kDevice) {  // upload packed
+    const int es = esize(t->dtype == TCP_U16 ? TCP_F16 : TCP_F32);
+    const size_t bytes = (size_t)v.d0 * v.d1 * v.d2 * es;
+    void* d = nullptr;
+    TRY_S(sc.alloc(&d, bytes));
+    for (int64_t f = 0; f < v.d0; ++f)
+      TCP_CUDA_TRY(cudaMemcpy2DAsync((char*)d + (size_t)f * v.d1 * v.d2 * es, (size_t)v.d2 * es,
+                                     (const char*)v.p + (size_t)f * v.s0 * es, (size_t)v.s1 * es,
+                                     (size_t)v.d2 * es, (size_t)v.d1, cudaMemcpyHostToDevice, sc.st));
+    v.p = d;
+    v.s0 = v.d1 * v.d2;
+    v.s1 = v.d2;
+  }
+  if (t->ndim == 3) {
+    void* m = nullptr;
+    TRY_S(sc.alloc(&m, sizeof(float) * (size_t)(nz * nd)));
+    View3 mv;
+    mv.p = m; mv.dtype = TCP_F32; mv.d0 = 1; mv.d1 = nz; mv.d2 = nd; mv.s0 = 0; mv.s1 = nd;
+    TRY_S(launch_frame_mean(v, mv, sc.st));
+    v = mv;
+  }
+  *out = v;
+  return TCP_OK;
+}
+
+}  // namespace
+}  // namespace tcp
+
+using namespace tcp;
+
+extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                              const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
+                              void* stream) {
+  if (!raw || !dark || !flat || !vol) return fail(TCP_ERR_ARG, "fbp: null tensor");
+  if (raw->ndim != 3 || raw->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "fbp: raw must be U16 [ntheta][nz][ndet]");
+  if (vol->ndim != 3 || (vol->dtype != TCP_F32 && vol->dtype != TCP_F16 && vol->dtype != TCP_BF16))
+    return fail(TCP_ERR_DTYPE, "fbp: vol must be F32/F16/BF16 [nz][n][n]");
+  const int64_t nt = raw->shape[0], nz = raw->shape[1], nd = raw->shape[2], n = vol->shape[1];
+  if (vol->shape[0] != nz || vol->shape[2] != n) return fail(TCP_ERR_SHAPE, "fbp: vol must be [nz][n][n]");
+  if (raw->stride[2] != 1 || vol->stride[2] != 1) return fail(TCP_ERR_ALIGN, "fbp: innermost stride must be 1");
+  for (const tcp_tensor* df : {dark, flat}) {
+    const bool ok = (df->ndim == 2 && df->dtype == TCP_F32 && df->shape[0] == nz && df->shape[1] == nd) ||
+                    (df->ndim == 3 && df->dtype == TCP_U16 && df->shape[0] >= 1 && df->shape[1] == nz &&
+                     df->shape[2] == nd);
+    if (!ok) return fail(TCP_ERR_SHAPE, "fbp: dark/flat must be F32 [nz][ndet] or U16 [nf][nz][ndet]");
+  }
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "fbp: center must be finite");
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "fbp: theta is null");
+  if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "fbp: ndet > 4096");
+  tcp_fbp_opts o{};
+  if (opts) o = *opts;
+  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : 16;
+  const int sdt = (o.sino_dtype == TCP_F32 || o.sino_dtype == TCP_F16 || o.sino_dtype == TCP_BF16) ? o.sino_dtype
+                                                                                                   : vol->dtype;
+  if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
+  if (o.pad_mode != TCP_PAD_EDGE && o.pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
+  const int B = o.n_buffers == 3 ? 3 : 2;
+  if (nz == 0 || n == 0 || nt == 0 || nd == 0) {
+    if (nz * n * n > 0) return fail(TCP_ERR_SHAPE, "fbp: empty projections for a non-empty volume");
+    return TCP_OK;
+  }
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "fbp: theta must be finite");
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Where wraw = where(raw->data), wvol = where(vol->data);
+  if (wraw != kDevice && raw->stride[1] != nd) return fail(TCP_ERR_ALIGN, "fbp: host raw rows must be packed");
+
+  TrigTable trig;
+  FilterTable ft;
+  tcp_status s;
+  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  if ((s = get_filter_table(nd, o.filter, nt, center, &ft)) != TCP_OK) return s;
+  tcp_bp_config cfg;
+  tcp_get_backproject_config(std::min(chunk, nz), nt, nd, n, sdt, vol->dtype, &cfg);
+
+  Scope sc;
+  sc.st = st;
+  View3 dm, fm;
+  if ((s = device_means(dark, nz, nd, sc, &dm)) != TCP_OK) return s;
+  if ((s = device_means(flat, nz, nd, sc, &fm)) != TCP_OK) return s;
+
+  const int64_t cz = std::min(chunk, nz);
+  void* sino = nullptr;
+  if ((s = sc.alloc(&sino, (size_t)cz * nt * nd * esize(sdt))) != TCP_OK) return s;
+
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t ev_alloc;
+  std::vector<void*> rring(B, nullptr), vring(B, nullptr);
+  std::vector<cudaEvent_t> raw_ready(B), raw_free(B), vol_ready(B), vol_free(B);
+  const bool host_raw = wraw != kDevice, host_vol = wvol != kDevice;
+  if (host_raw) {
+    if ((s = sc.stream(&cin)) != TCP_OK) return s;
+    for (int b = 0; b < B; ++b) {
+      if ((s = sc.alloc(&rring[b], (size_t)nt * cz * nd * 2)) != TCP_OK) return s;
+      if ((s = sc.event(&raw_ready[b])) != TCP_OK) return s;
+      if ((s = sc.event(&raw_free[b])) != TCP_OK) return s;
+    }
+  }
+  if (host_vol) {
+    if ((s = sc.stream(&cout)) != TCP_OK) return s;
+    for (int b = 0; b < B; ++b) {
+      if ((s = sc.alloc(&vring[b], (size_t)cz * n * n * esize(vol->dtype))) != TCP_OK) return s;
+      if ((s = sc.event(&vol_ready[b])) != TCP_OK) return s;
+      if ((s = sc.event(&vol_free[b])) != TCP_OK) return s;
+    }
+  }
+  if ((s = sc.event(&ev_alloc)) != TCP_OK) return s;
+  TCP_CUDA_TRY(cudaEventRecord(ev_alloc, st));
+  if (cin) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, ev_alloc, 0));
+  if (cout) TCP_CUDA_TRY(cudaStreamWaitEvent(cout, ev_alloc, 0));
+
+  const int64_t nchunks = (nz + chunk - 1) / chunk;
+  auto issue_copy_in = [&](int64_t k) -> tcp_status {
+    const int b = (int)(k % B);
+    const int64_t z0 = k * chunk, c = std::min(chunk, nz - z0);
+    if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, raw_free[b], 0));
+    TCP_CUDA_TRY(cudaMemcpy2DAsync(rring[b], (size_t)c * nd * 2,
+                                   (const uint16_t*)raw->data + z0 * raw->stride[1], (size_t)raw->stride[0] * 2,
+                                   (size_t)c * nd * 2, (size_t)nt, cudaMemcpyHostToDevice, cin));
+    TCP_CUDA_TRY(cudaEventRecord(raw_ready[b], cin));
+    return TCP_OK;
+  };
+  if (host_raw)
+    for (int64_t k = 0; k < std::min<int64_t>(B, nchunks); ++k) TRY_S(issue_copy_in(k));
+
+  for (int64_t k = 0; k < nchunks; ++k) {
+    const int b = (int)(k % B);
+    const int64_t z0 = k * chunk, c = std::min(chunk, nz - z0);
+    View3 rv;
+    rv.dtype = TCP_U16;
+    rv.d0 = nt; rv.d1 = c; rv.d2 = nd;
+    if (host_raw) {
+      TCP_CUDA_TRY(cudaStreamWaitEvent(st, raw_ready[b], 0));
+      rv.p = rring[b]; rv.s0 = c * nd; rv.s1 = nd;
+    } else {
+      rv.p = (uint16_t*)raw->data + z0 * raw->stride[1];
+      rv.s0 = raw->stride[0]; rv.s1 = raw->stride[1];
+    }
+    View3 dv = dm, fv = fm;
+    dv.p = (float*)dm.p + z0 * dm.s1; dv.d1 = c;
+    fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
+    View3 sv;
+    sv.p = sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    TRY_S(launch_normalize(rv, dv, fv, sv, st));
+    if (host_raw) {
+      TCP_CUDA_TRY(cudaEventRecord(raw_free[b], st));
+      if (k + B < nchunks) TRY_S(issue_copy_in(k + B));
+    }
+    TRY_S(launch_filter(sv, ft, o.pad_mode, st));
+    View3 vv;
+    vv.dtype = vol->dtype; vv.d0 = c; vv.d1 = n; vv.d2 = n;
+    if (host_vol) {
+      if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(st, vol_free[b], 0));
+      vv.p = vring[b]; vv.s0 = n * n; vv.s1 = n;
+    } else {
+      vv.p = (char*)vol->data + z0 * vol->stride[0] * esize(vol->dtype);
+      vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
+    }
+    TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st));
+    if (host_vol) {
+      const int es = esize(vol->dtype);
+      TCP_CUDA_TRY(cudaEventRecord(vol_ready[b], st));
+      TCP_CUDA_TRY(cudaStreamWaitEvent(cout, vol_ready[b], 0));
+      if (vol->stride[1] == n && vol->stride[0] == n * n) {
+        TCP_CUDA_TRY(cudaMemcpyAsync((char*)vol->data + z0 * n * n * es, vring[b], (size_t)c * n * n * es,
+                                     cudaMemcpyDeviceToHost, cout));
+      } else {
+        for (int64_t z = 0; z < c; ++z)
+          TCP_CUDA_TRY(cudaMemcpy2DAsync((char*)vol->data + ((z0 + z) * vol->stride[0]) * es, (size_t)vol->stride[1] * es,
+                                       (char*)vring[b] + (size_t)z * n * n * es, (size_t)n * es, (size_t)n * es,
+                                       (size_t)n, cudaMemcpyDeviceToHost, cout));
+      }
+      TCP_CUDA_TRY(cudaEventRecord(vol_free[b], cout));
+    }
+  }
+  // Join the side streams so that `stream` completes after every copy.
+  if (cout) {
+    cudaEvent_t done;
+    TRY_S(sc.event(&done));
+    TCP_CUDA_TRY(cudaEventRecord(done, cout));
+    TCP_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+  }
+  if (cin) {
+    cudaEvent_t done;
+    TRY_S(sc.event(&done));
+    TCP_CUDA_TRY(cudaEventRecord(done, cin));
+    TCP_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+  }
+  return TCP_OK;
+}

@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of libtcp.
+// Geometry conventions are those of include/tcp.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <type_traits>
+
+#include "tcp.h"
+
+namespace tcp {
+
+// ------------------------------------------------------------------ errors --
+
+// Device error word: kernels OR bits into it instead of trapping.
+enum : uint32_t {
+  kErrBpWindow = 1u << 0,     // backprojector window index out of range
+  kErrPjCandidate = 1u << 1,  // projector candidate outside the volume
+  kErrFilterIndex = 1u << 2,  // filter shared-memory index out of range
+  kErrTimeout = 1u << 3,      // bounded wait gave up
+  kErrBatchItem = 1u << 4,    // batched work item out of range
+};
+
+uint32_t* device_error_word();  // device address of the word (current device)
+
+void set_error(const std::string& msg);
+tcp_status fail(tcp_status s, const std::string& msg);
+tcp_status cuda_fail(cudaError_t e, const char* what);
+
+#define TCP_CUDA_TRY(expr)                               \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);  \
+  } while (0)
+
+bool checked_mode();
+
+// ----------------------------------------------------------------- dtypes --
+
+template <class T> struct Store;
+template <> struct Store<float> {
+  static __device__ __forceinline__ float load(const float* p) { return __ldg(p); }
+  static __device__ __forceinline__ void put(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+  static __device__ __forceinline__ float load(const __half* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void put(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+  static __device__ __forceinline__ float load(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ------------------------------------------------- canonical ray geometry --
+//
+// The ray coordinate of voxel (ix, iy) at angle theta is
+//   s = (ix - n/2) cos + (iy - n/2) sin + center.
+// It is evaluated as an FP64 origin per aligned 32x32 voxel tile, split into an
+// integer part and an FP32 fraction, plus FP32 in-tile offsets.  Both the
+// backprojector and the projector call exactly these functions (explicit
+// rounding intrinsics, no contraction freedom), so the two operators use
+// bit-identical weights and are exact transposes of each other.
+
+constexpr int kTile = 32;
+
+struct TileOrigin {
+  int i0;    // floor of the tile-origin ray coordinate
+  float f0;  // fractional part in [0, 1]
+  float c;   // cos(theta) rounded to FP32
+  float s;   // sin(theta) rounded to FP32
+};
+
+__device__ __forceinline__ TileOrigin tile_origin(int gx, int gy, double half_n, double center,
+                                                  double2 cs) {
+  const double X0 = __dsub_rn((double)(gx * kTile), half_n);
+  const double Y0 = __dsub_rn((double)(gy * kTile), half_n);
+  const double S0 = __fma_rn(X0, cs.x, __fma_rn(Y0, cs.y, center));
+  const double fl = floor(S0);
+  TileOrigin o;
+  o.i0 = (int)fl;
+  o.f0 = __double2float_rn(__dsub_rn(S0, fl));
+  o.c = __double2float_rn(cs.x);
+  o.s = __double2float_rn(cs.y);
+  return o;
+}
+
+// In-tile ray coordinate relative to i0 for offsets (dx, dy) in [0, 32).
+__device__ __forceinline__ float rel_coord(float f0, float c, float s, float dx, float dy) {
+  return __fmaf_rn(dy, s, __fmaf_rn(dx, c, f0));
+}
+
+// ------------------------------------------------------------- host side --
+
+struct TrigTable {
+  const double2* dev = nullptr;  // (cos, sin) per angle, FP64
+  int64_t n = 0;
+};
+// Cached FP64 cos/sin table for a host angle array (first use uploads it).
+tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out);
+
+struct FilterTable {
+  const float2* response = nullptr;  // npad/2+1 complex factors (incl. 1/npad)
+  const float2* twiddle = nullptr;   // npad twiddles exp(-2 pi i m / npad)
+  int npad = 0;
+};
+tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double center,
+                            FilterTable* out);
+
+int64_t padded_length(int64_t ndet);
+
+// Launchers (argument checks are done by the API layer).
+struct View3 {  // [d0][d1][d2] with element strides s0, s1 (s2 == 1)
+  void* p;
+  int dtype;
+  int64_t d0, d1, d2;
+  int64_t s0, s1;
+};
+
+tcp_status launch_frame_mean(const View3& frames, const View3& mean, cudaStream_t st);
+tcp_status launch_normalize(const View3& raw, const View3& dark, const View3& flat, const View3& sino,
+                            cudaStream_t st);
+tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode, cudaStream_t st);
+tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
+                              const tcp_bp_config& cfg, cudaStream_t st);
+tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
+                          cudaStream_t st);
+
+tcp_bp_config default_bp_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n, int sdt, int vdt);
+bool valid_bp_config(const tcp_bp_config& c);
+
+}  // namespace tcp

@@ -1,0 +1,101 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function include/tcp.h declares, and rejects bad arguments on the host (no
+compute call is made without a GPU)."""
+import ctypes
+
+import pytest
+
+from paper_2209_08450_gb300 import _lib
+from paper_2209_08450_gb300 import build as tcp_build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    tcp_build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _lib.header_functions()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    assert lib.tcp_version() == 1
+    assert lib.tcp_status_string(0) == b"ok"
+    assert lib.tcp_status_string(2) == b"invalid shape"
+
+
+def _t(dtype, shape, ptr=4096):
+    d = _lib.TcpTensor()
+    d.data = ptr
+    d.dtype = dtype
+    d.ndim = len(shape)
+    st = 1
+    for i in reversed(range(len(shape))):
+        d.shape[i] = shape[i]
+        d.stride[i] = st
+        st *= shape[i]
+    return d
+
+
+def _status(lib, name, *args):
+    return getattr(lib, name)(*args)
+
+
+def test_host_side_argument_checks(lib):
+    th = (ctypes.c_double * 4)(0, 0.5, 1.0, 1.5)
+    sino = _t(_lib.F32, (2, 4, 16))
+    vol = _t(_lib.F32, (2, 16, 16), ptr=1 << 20)
+    # null tensor
+    assert _status(lib, "tcp_backproject", None, th, 8.0, ctypes.byref(vol), None) == 1
+    # wrong slice count
+    bad = _t(_lib.F32, (3, 16, 16), ptr=1 << 20)
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, 8.0, ctypes.byref(bad), None) == 2
+    assert b"slice" in lib.tcp_last_error()
+    # non-square volume
+    bad = _t(_lib.F32, (2, 16, 15), ptr=1 << 20)
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, 8.0, ctypes.byref(bad), None) == 2
+    # u16 volume is not a float dtype
+    bad = _t(_lib.U16, (2, 16, 16), ptr=1 << 20)
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, 8.0, ctypes.byref(bad), None) == 3
+    # non-unit innermost stride
+    bad = _t(_lib.F32, (2, 16, 16), ptr=1 << 20)
+    bad.stride[2] = 2
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, 8.0, ctypes.byref(bad), None) == 4
+    # non-finite centre and angle
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, float("nan"), ctypes.byref(vol), None) == 1
+    th_bad = (ctypes.c_double * 4)(0, float("inf"), 1.0, 1.5)
+    assert _status(lib, "tcp_project", ctypes.byref(vol), th_bad, 8.0, ctypes.byref(sino), None) == 1
+    # overlapping input and output
+    alias = _t(_lib.F32, (2, 16, 16), ptr=4096 + 64)
+    assert _status(lib, "tcp_backproject", ctypes.byref(sino), th, 8.0, ctypes.byref(alias), None) == 10
+    # filter: unknown kind, unknown pad, too wide
+    assert _status(lib, "tcp_filter_ex", ctypes.byref(sino), 7, 8.0, 0, 0, None) == 1
+    assert _status(lib, "tcp_filter_ex", ctypes.byref(sino), 0, 8.0, 5, 0, None) == 1
+    wide = _t(_lib.F32, (1, 2, 5000))
+    assert _status(lib, "tcp_filter_ex", ctypes.byref(wide), 0, 8.0, 0, 0, None) == 9
+    # normalize: shapes and dtypes
+    raw = _t(_lib.U16, (4, 2, 16))
+    dark = _t(_lib.F32, (2, 16), ptr=1 << 24)
+    out = _t(_lib.F32, (2, 4, 16), ptr=1 << 26)
+    badout = _t(_lib.F32, (4, 2, 16), ptr=1 << 26)
+    assert _status(lib, "tcp_normalize", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(dark),
+                   ctypes.byref(badout), None) == 2
+    rawf = _t(_lib.F32, (4, 2, 16))
+    assert _status(lib, "tcp_normalize", ctypes.byref(rawf), ctypes.byref(dark), ctypes.byref(dark),
+                   ctypes.byref(out), None) == 3
+    darku = _t(_lib.U16, (2, 16), ptr=1 << 24)
+    assert _status(lib, "tcp_normalize", ctypes.byref(raw), ctypes.byref(darku), ctypes.byref(dark),
+                   ctypes.byref(out), None) == 3
+    # config that is not instantiated
+    c = _lib.BpConfig(3, 16, 4, 0)
+    assert _status(lib, "tcp_set_backproject_config", ctypes.byref(c)) == 9
+
+
+def test_default_config_query(lib):
+    c = _lib.BpConfig()
+    assert lib.tcp_get_backproject_config(64, 2048, 2048, 2048, 3, 3, ctypes.byref(c)) == 0
+    assert c.k_slices in (1, 2, 4, 8, 16) and c.theta_stage in (8, 16, 32)

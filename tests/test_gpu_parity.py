@@ -1,0 +1,300 @@
+"""GPU parity: every CUDA kernel against the FP64 oracle on the same seeded inputs.
+
+Tolerances: relative L2 <= 1e-5 for FP32 storage, <= 5e-3 for FP16/BF16
+storage (FP32 accumulation), per result.  Sizes span several 32x32 tiles and
+leave ragged tails (n, ndet, nz, ntheta not multiples of the tile, the slice
+block or the angle stage).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2209_08450_gb300 as tcp
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+TOL = {torch.float32: 1e-5, torch.float16: 5e-3, torch.bfloat16: 5e-3}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def u16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.uint16).view(np.int16)).to(DEV)
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.fixture(autouse=True)
+def _checked():
+    tcp.set_checked(True)
+    yield
+    tcp.device_check()
+    tcp.set_checked(False)
+
+
+# ------------------------------------------------------------- backproject --
+
+def _bp_case(nz, nt, nd, n, center, seed, uniform=False):
+    rng = np.random.default_rng(seed)
+    q = rng.normal(size=(nz, nt, nd))
+    theta = synth.uniform_theta(nt) if uniform else rng.uniform(-0.3, 2 * np.pi, nt)
+    return q, theta, center
+
+
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (11, 181, 203, 200, 101.37), (3, 64, 96, 96, 48.0), (1, 7, 33, 70, 20.5), (17, 37, 64, 33, 31.9)])
+def test_backproject_fp32(nz, nt, nd, n, center):
+    q, theta, c = _bp_case(nz, nt, nd, n, center, nz * 1000 + nt)
+    got = host(tcp.backproject(to_dev(q), theta, c, n=n))
+    ref = oracle.backproject(q, theta, c, n)
+    assert rel(got, ref) <= 1e-5
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("cfg", [(8, 16, 4), (4, 32, 4), (4, 16, 4), (16, 8, 2), (8, 16, 2), (2, 16, 4),
+                                 (1, 32, 4)])
+def test_backproject_every_config(cfg):
+    q, theta, c = _bp_case(13, 50, 70, 65, 35.2, 7)
+    ref = oracle.backproject(q, theta, c, 65)
+    try:
+        tcp.set_backproject_config(*cfg)
+        got = host(tcp.backproject(to_dev(q), theta, c, n=65))
+    finally:
+        tcp.set_backproject_config(None)
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("sdt", [torch.float16, torch.bfloat16, torch.float32])
+@pytest.mark.parametrize("vdt", [torch.float16, torch.bfloat16, torch.float32])
+def test_backproject_16bit_storage(sdt, vdt):
+    q, theta, c = _bp_case(9, 120, 100, 96, 50.5, 3, uniform=True)
+    qd = to_dev(q, sdt)
+    got = host(tcp.backproject(qd, theta, c, n=96, dtype=vdt))
+    # against the oracle on the stored (rounded) samples and on the exact ones
+    ref_stored = oracle.backproject(host(qd), theta, c, 96)
+    ref_exact = oracle.backproject(q, theta, c, 96)
+    tol = max(TOL[sdt], TOL[vdt])
+    assert rel(got, ref_stored) <= tol
+    assert rel(got, ref_exact) <= tol
+
+
+def test_backproject_special_angles_and_constant():
+    n, nd, nt = 64, 64, 17
+    theta = synth.uniform_theta(nt)
+    got = host(tcp.backproject(torch.full((2, nt, nd), 1.5, device=DEV), theta, nd / 2, n=n))
+    c = np.arange(n) - n / 2
+    X, Y = np.meshgrid(c, c)
+    inside = X ** 2 + Y ** 2 < (nd / 2 - 1.5) ** 2
+    assert np.max(np.abs(got[:, inside] - 1.5 * nt)) < 1e-4
+    q = np.random.default_rng(0).normal(size=(1, 1, nd))
+    b = host(tcp.backproject(to_dev(q), np.array([0.0]), nd / 2, n=n))[0]
+    assert np.max(np.abs(b - np.broadcast_to(q[0], (n, n)))) < 1e-6
+
+
+def test_backproject_edge_cases():
+    th = np.array([0.3, 1.1])
+    # empty slice count
+    out = tcp.backproject(torch.zeros((0, 2, 8), device=DEV), th, 4.0, n=8)
+    assert out.shape == (0, 8, 8)
+    # no angles: zero volume
+    out = tcp.backproject(torch.zeros((2, 0, 8), device=DEV), np.zeros(0), 4.0, n=8)
+    assert torch.count_nonzero(out) == 0
+    # one voxel, one detector pixel
+    q = np.array([[[2.0]]])
+    got = host(tcp.backproject(to_dev(q), np.array([0.0]), 0.0, n=1))
+    assert abs(got[0, 0, 0] - oracle.backproject(q, np.array([0.0]), 0.0, 1)[0, 0, 0]) < 1e-6
+    # non-contiguous (strided) volume output
+    big = torch.zeros((3, 40, 48), device=DEV)
+    view = big[:, 2:34, 5:37]
+    q, theta, c = _bp_case(3, 20, 40, 32, 19.0, 11)
+    tcp.backproject(to_dev(q), theta, c, out=view)
+    assert rel(host(view), oracle.backproject(q, theta, c, 32)) <= 1e-5
+    assert torch.count_nonzero(big[:, :2]) == 0 and torch.count_nonzero(big[:, :, :5]) == 0
+
+
+def test_backproject_large_detector_offsets():
+    # a centre far from ndet/2 and a volume wider than the detector
+    q, theta, c = _bp_case(2, 45, 50, 90, -7.25, 5)
+    got = host(tcp.backproject(to_dev(q), theta, c, n=90))
+    assert rel(got, oracle.backproject(q, theta, c, 90)) <= 1e-5
+
+
+# ----------------------------------------------------------------- project --
+
+@pytest.mark.parametrize("nz,nt,nd,n,center", [(5, 67, 91, 80, 44.6), (9, 30, 40, 64, 33.0), (1, 5, 17, 9, 8.2)])
+def test_project_fp32(nz, nt, nd, n, center):
+    rng = np.random.default_rng(nz + nt)
+    vol = rng.normal(size=(nz, n, n))
+    theta = rng.uniform(0, np.pi, nt)
+    got = host(tcp.project(to_dev(vol), theta, center, ndet=nd))
+    ref = oracle.project(vol, theta, center, nd)
+    assert rel(got, ref) <= 1e-5
+
+
+def test_project_is_exact_transpose_on_gpu():
+    rng = np.random.default_rng(1)
+    nz, n, nt, nd = 4, 100, 73, 111
+    theta = rng.uniform(0, np.pi, nt)
+    x = to_dev(rng.normal(size=(nz, n, n)))
+    y = to_dev(rng.normal(size=(nz, nt, nd)))
+    px = tcp.project(x, theta, 52.3, ndet=nd)
+    bty = tcp.backproject(y, theta, 52.3, n=n)
+    lhs = torch.sum(px.double() * y.double()).item()
+    rhs = torch.sum(x.double() * bty.double()).item()
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_project_16bit(dt):
+    rng = np.random.default_rng(2)
+    vol = rng.uniform(0, 1, size=(3, 64, 64))
+    theta = synth.uniform_theta(48)
+    vd = to_dev(vol, dt)
+    got = host(tcp.project(vd, theta, 32.0, ndet=64, dtype=dt))
+    assert rel(got, oracle.project(host(vd), theta, 32.0, 64)) <= 5e-3
+
+
+# --------------------------------------------------------------- normalize --
+
+@pytest.mark.parametrize("nd", [64, 203])
+@pytest.mark.parametrize("means", [False, True])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float16, torch.bfloat16])
+def test_normalize(nd, means, dt):
+    ds = synth.shepp_logan_dataset(ntheta=33, ndet=nd, nz=5, center=nd / 2, seed=nd)
+    raw, dark, flat = u16(ds.raw), u16(ds.dark), u16(ds.flat)
+    if means:
+        dark, flat = tcp.frame_mean(dark), tcp.frame_mean(flat)
+        assert rel(host(dark), oracle.frame_mean(ds.dark)) < 1e-7
+    got = host(tcp.normalize(raw, dark, flat, dtype=dt))
+    ref = oracle.normalize(ds.raw, oracle.frame_mean(ds.dark), oracle.frame_mean(ds.flat))
+    assert rel(got, ref) <= TOL[dt]
+
+
+def test_normalize_special_values_and_strided_chunk():
+    raw = np.array([10100, 5100, 100, 50, 65535, 2600, 0, 100], np.uint16).reshape(1, 1, 8)
+    raw = np.repeat(raw, 3, axis=1)  # [1][3][8]
+    d = np.full((3, 8), 100.0, np.float32)
+    f = np.full((3, 8), 10100.0, np.float32)
+    f[2] = 100.0  # flat == dark -> clamp
+    got = host(tcp.normalize(u16(raw), to_dev(d), to_dev(f)))
+    ref = oracle.normalize(raw, d.astype(np.float64), f.astype(np.float64))
+    assert np.max(np.abs(got - ref)) < 1e-5
+    # a z-chunk of a larger stack is a strided view
+    ds = synth.shepp_logan_dataset(ntheta=10, ndet=64, nz=8, center=32.0, seed=1)
+    full = u16(ds.raw)
+    dm, fm = tcp.frame_mean(u16(ds.dark)), tcp.frame_mean(u16(ds.flat))
+    got = host(tcp.normalize(full[:, 3:6], dm[3:6], fm[3:6]))
+    ref = oracle.normalize(ds.raw[:, 3:6], oracle.frame_mean(ds.dark)[3:6], oracle.frame_mean(ds.flat)[3:6])
+    assert rel(got, ref) <= 1e-6
+
+
+# ------------------------------------------------------------------ filter --
+
+@pytest.mark.parametrize("nd", [1, 2, 7, 64, 100, 256, 333, 1024, 2048, 2560, 4096])
+def test_filter_shepp_edge(nd):
+    rng = np.random.default_rng(nd)
+    nt = 5
+    q = rng.normal(size=(3, nt, nd))
+    c = nd / 2 + 1.37
+    got = host(tcp.filter_(to_dev(q), c, "shepp"))
+    ref = oracle.filter_sino(q, c, "shepp", "edge")
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["shepp", "parzen", "ramp", "none"])
+@pytest.mark.parametrize("pad", ["edge", "zero"])
+def test_filter_kinds_and_pads(kind, pad):
+    rng = np.random.default_rng(3)
+    q = rng.normal(size=(2, 9, 150)) + 3.0
+    got = host(tcp.filter_(to_dev(q), 71.6, kind, pad))
+    ref = oracle.filter_sino(q, 71.6, kind, pad)
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_filter_16bit(dt):
+    rng = np.random.default_rng(4)
+    q = rng.uniform(0, 2, size=(4, 31, 256))
+    qd = to_dev(q, dt)
+    got = host(tcp.filter_(qd, 128.0, "shepp"))
+    assert rel(got, oracle.filter_sino(host(to_dev(q, dt)), 128.0, "shepp")) <= 5e-3
+
+
+def test_filter_explicit_ntheta_and_2d_rows():
+    rng = np.random.default_rng(5)
+    q = rng.normal(size=(7, 80))
+    got = host(tcp.filter_(to_dev(q), 40.0, "ramp", ntheta=100))
+    assert rel(got, oracle.filter_sino(q[None], 40.0, "ramp", ntheta=100)[0]) <= 1e-5
+
+
+# -------------------------------------------------------------- end to end --
+
+def _fbp_gpu(ds, dt=torch.float32, vdt=None, kind="shepp"):
+    sino = tcp.normalize(u16(ds.raw), u16(ds.dark), u16(ds.flat), dtype=dt)
+    tcp.filter_(sino, ds.center, kind)
+    nd = ds.raw.shape[-1]
+    return tcp.backproject(sino, ds.theta, nd / 2.0, dtype=vdt or dt)
+
+
+def test_fbp_shepp_logan_256_fp32():
+    ds = synth.shepp_logan_dataset()  # 256 angles, 256 x 16, centre 128, I0 4e4
+    got = host(_fbp_gpu(ds))
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    assert rel(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_fbp_shepp_logan_256_16bit(dt):
+    ds = synth.shepp_logan_dataset(nz=6)
+    got = host(_fbp_gpu(ds, dt))
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    assert rel(got, ref) <= 5e-3
+
+
+def test_fbp_ellipsoids_ragged():
+    ds = synth.ellipsoid_dataset(ntheta=150, ndet=173, nz=7, count=20, seed=3)
+    got = host(_fbp_gpu(ds, kind="parzen"))
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "parzen")
+    assert rel(got, ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- pipeline --
+
+@pytest.mark.parametrize("where", ["device", "host"])
+@pytest.mark.parametrize("chunk,nbuf", [(5, 2), (16, 2), (3, 3)])
+def test_fbp_pipeline(where, chunk, nbuf):
+    ds = synth.shepp_logan_dataset(ntheta=120, ndet=96, nz=13, center=47.3, seed=2)
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    if where == "device":
+        raw, dark, flat = u16(ds.raw), u16(ds.dark), u16(ds.flat)
+    else:
+        raw = torch.from_numpy(ds.raw.view(np.int16)).pin_memory()
+        dark = torch.from_numpy(ds.dark.view(np.int16))  # pageable host frames
+        flat = torch.from_numpy(ds.flat.view(np.int16)).pin_memory()
+    out = tcp.fbp(raw, dark, flat, ds.theta, ds.center, chunk_nz=chunk, n_buffers=nbuf)
+    torch.cuda.synchronize()
+    assert out.device.type == ("cuda" if where == "device" else "cpu")
+    assert rel(host(out), ref) <= 1e-5
+
+
+def test_fbp_pipeline_16bit_and_means():
+    ds = synth.shepp_logan_dataset(ntheta=100, ndet=80, nz=9, center=40.0, seed=4)
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    dm, fm = tcp.frame_mean(u16(ds.dark)), tcp.frame_mean(u16(ds.flat))
+    for dt in (torch.float16, torch.bfloat16):
+        out = tcp.fbp(u16(ds.raw), dm, fm, ds.theta, ds.center, dtype=dt, chunk_nz=4)
+        torch.cuda.synchronize()
+        assert rel(host(out), ref) <= 5e-3
