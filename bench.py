@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""FBP throughput at 2048^3 on GB300: GVoxel/s of chunked parallel-beam FBP
+(dark/flat normalisation with -log, Shepp-Logan ramp filter, LineRec
+backprojection) from 2048 uint16 projections of 2048 x 2048 pixels.
+
+One step = one full reconstruction of the 2048^3 volume, every slice chunk
+through normalise+filter and backprojection.  `value` is measured with the
+uint16 projections already in HBM; `e2e` through the same C-ABI call with
+page-locked HOST input and output buffers (host->device copies of the raw
+slabs and device->host copies of the volume inside the timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) each rank reconstructs its own seeded dataset (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FBP GVoxel/s at 2048^3 (FP16 vs FP32, at stated L2 error); % of roofline"
+# Paper, Table 2: LineRec (this method), FP32, N = 2048, 80 s on one A100 incl. I/O.
+PAPER_LINEREC_GVOXS = 2048 ** 3 / 80.0 / 1e9
+DATA = ("synthetic: seeded porous-medium phantom (spheres r = 3-40 px, density 0.2-1.0, 40 % solid in a "
+        "0.45 N cylinder), exact line integrals, Poisson uint16 frames I0 = 3e4 with 20 dark / 20 flat frames")
+
+
+# ----------------------------------------------------------- multi-rank --
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of a scalar over ranks (identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device_index=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device_index is None:
+            dist.barrier()
+        else:
+            dist.barrier(device_ids=[device_index])
+
+
+def slab(nz: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous z-slab [z0, z1) of rank among world (the paper's start/end rows)."""
+    base, extra = divmod(nz, world)
+    z0 = rank * base + min(rank, extra)
+    return z0, z0 + base + (1 if rank < extra else 0)
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- CPU leg --
+
+def oracle_fbp_slices(raw, dark, flat, theta, center, n_threads=None):
+    """FP64 oracle FBP of a few slices (normalise, filter, backproject)."""
+    import oracle
+    p = oracle.normalize(raw, oracle.frame_mean(dark), oracle.frame_mean(flat))
+    q = oracle.filter_sino(p, center, "shepp", "edge")
+    return oracle.backproject(q, theta, raw.shape[-1] / 2.0, raw.shape[-1])
+
+
+def host_sample(n: int, ntheta: int, slices, seed: int = 0):
+    """Host copy of a few slices of the porous workload (torch on the CPU)."""
+    import numpy as np
+    import synth.gpu as sgpu
+    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, ntheta, n, seed=seed, device="cpu",
+                                                            slices=np.asarray(slices))
+    u = lambda t: t.numpy().view(np.uint16)
+    return u(raw), u(dark), u(flat), theta, center
+
+
+def cpu_baseline(n: int, ntheta: int, nslices: int) -> dict:
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    raw, dark, flat, theta, center = host_sample(n, ntheta, list(range(n // 2, n // 2 + nslices)))
+    t0 = time.perf_counter()
+    oracle_fbp_slices(raw, dark, flat, theta, center)
+    dt = time.perf_counter() - t0
+    return {"value": nslices * n * n / dt / 1e9, "unit": "GVoxel/s", "cores": cores, "kind": "oracle",
+            "sample": "%d slices of the %d^3 workload (%d angles): FP64 normalise + numpy-FFT filter + C/OpenMP "
+                      "LineRec backprojection, %.1f s" % (nslices, n, ntheta, dt), "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n, nt = args.size, args.size
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    oracle.build()
+    nsl = args.ref_slices
+    raw, dark, flat, theta, center = host_sample(n, nt, list(range(n // 2, n // 2 + nsl)))
+    for _ in range(args.warmup):
+        oracle_fbp_slices(raw, dark, flat, theta, center)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_fbp_slices(raw, dark, flat, theta, center)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = nsl * n * n / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GVoxel/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": v / PAPER_LINEREC_GVOXS, "dtype": "f64", "data": DATA,
+        "config": {"workload": "%d slices of the %d^3 FBP workload (%d angles) per step" % (nsl, n, nt),
+                   "n": n, "ntheta": nt, "l2": "host run"},
+        "cpu_baseline": {"value": v, "unit": "GVoxel/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d slices per step, FP64 oracle on the host cores" % nsl},
+        "e2e": {"value": v, "unit": "GVoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------- GPU leg --
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--chunk", type=int, default=32)
+    ap.add_argument("--variants", default="f16,bf16")
+    ap.add_argument("--variant-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=4)
+    ap.add_argument("--ref-slices", type=int, default=1)
+    ap.add_argument("--parity-slices", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2209_08450_gb300 as tcp
+    import synth.gpu as sgpu
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n = nt = args.size
+
+    # ---- input: seeded synthetic dataset, resident in HBM (not timed)
+    t_gen = time.perf_counter()
+    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, nt, n, seed=rank, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    nchunks = (n + args.chunk - 1) // args.chunk
+
+    def run_steps(dtype, steps, warmup, out):
+        stream = torch.cuda.current_stream()
+
+        def step():
+            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=args.chunk, stream=stream)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(world, local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world, local)
+        return reduce_max(e0.elapsed_time(e1) / steps, world, dev)
+
+    # ---- headline: FP32 storage and arithmetic
+    vol = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    with ClockSampler(local) as clk:
+        ms = run_steps(torch.float32, args.steps, args.warmup, vol)
+    clocks = clk.summary()
+    value = world * n ** 3 / (ms * 1e-3) / 1e9
+
+    # ---- parity on sampled slices (oracle on the same uint16 frames)
+    def parity(v, zs):
+        import oracle
+        rng = np.random.default_rng(1)
+        errs = []
+        for z in zs:
+            r = raw[:, z:z + 1].cpu().numpy().view(np.uint16)
+            d = dark[:, z:z + 1].cpu().numpy().view(np.uint16)
+            f = flat[:, z:z + 1].cpu().numpy().view(np.uint16)
+            p = oracle.normalize(r, oracle.frame_mean(d), oracle.frame_mean(f))
+            q = oracle.filter_sino(p, center, "shepp")[0]
+            ix, iy = rng.integers(0, n, 2000), rng.integers(0, n, 2000)
+            ref = oracle.backproject_points(q, theta, n / 2.0, n, ix, iy)
+            got = v[z].double().cpu().numpy()[iy, ix]
+            errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        return float(max(errs))
+
+    zs = [int(x) for x in np.linspace(n // 5, 4 * n // 5, args.parity_slices)]
+    par = {"f32": parity(vol, zs)} if rank == 0 else {}
+
+    # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
+    s_chunk = torch.empty((args.chunk, nt, n), dtype=torch.float32, device=dev)
+    v_chunk = vol[:args.chunk]
+    dm, fm = tcp.frame_mean(dark), tcp.frame_mean(flat)
+    z0 = n // 2
+    tcp.normalize_filter(raw[:, z0:z0 + args.chunk], dm[z0:z0 + args.chunk], fm[z0:z0 + args.chunk], center,
+                         out=s_chunk)
+
+    def time_kernel(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    bp_ms = time_kernel(lambda: tcp.backproject(s_chunk, theta, n / 2.0, out=v_chunk))
+    nf_ms = time_kernel(lambda: tcp.normalize_filter(raw[:, z0:z0 + args.chunk], dm[z0:z0 + args.chunk],
+                                                     fm[z0:z0 + args.chunk], center, out=s_chunk))
+    interps = args.chunk * n * n * nt
+    clk_max = 2070.0
+    try:
+        clk_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    bp_peak = sms * 16 * clk_max * 1e6  # FP32: two 128-B shared-memory wavefronts per warp-wide interpolation
+    roofline = {"bound": "alu", "kernel": "k_backproject (LineRec, FP32)", "achieved": interps / (bp_ms * 1e-3) / 1e9,
+                "peak": bp_peak / 1e9, "unit": "Ginterp/s", "frac": interps / (bp_ms * 1e-3) / bp_peak,
+                "traffic": None, "ms_per_launch": bp_ms, "interps_per_launch": interps,
+                "peak_basis": "shared-memory pipe: %d SMs x 16 interp/clk x %.0f MHz (max SM clock)" % (sms, clk_max)}
+    hbm = 6767.4
+    try:
+        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        pass
+    nf_bytes = nt * args.chunk * n * 2 + args.chunk * nt * n * 4
+    secondary = {"normalize_filter": {"bound": "hbm", "achieved": nf_bytes / (nf_ms * 1e-3) / 1e9, "peak": hbm,
+                                      "unit": "GB/s", "frac": nf_bytes / (nf_ms * 1e-3) / 1e9 / hbm,
+                                      "ms_per_launch": nf_ms}}
+    del s_chunk
+
+    # ---- 16-bit storage variants (FP32 accumulation)
+    variants = {}
+    for name in [v for v in args.variants.split(",") if v]:
+        dt = {"f16": torch.float16, "bf16": torch.bfloat16}[name]
+        vv = torch.empty((n, n, n), dtype=dt, device=dev)
+        vms = run_steps(dt, args.variant_steps, 1, vv)
+        variants[name] = {"value": world * n ** 3 / (vms * 1e-3) / 1e9, "ms_per_step": vms,
+                          "speedup_vs_f32": ms / vms}
+        if rank == 0:
+            variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
+        del vv
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        del vol
+        torch.cuda.empty_cache()
+        raw_h = torch.empty(raw.shape, dtype=raw.dtype, pin_memory=True)
+        raw_h.copy_(raw)
+        dark_h = dark.cpu().pin_memory()
+        flat_h = flat.cpu().pin_memory()
+        vol_h = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+        stream = torch.cuda.current_stream()
+
+        def e2e_step():
+            tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=args.chunk, stream=stream)
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world, local)
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / args.steps * 1e3
+        barrier(world, local)
+        ems = reduce_max(max(e0.elapsed_time(e1) / args.steps, wall), world, dev)
+        e2e = {"value": world * n ** 3 / (ems * 1e-3) / 1e9, "unit": "GVoxel/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": raw_h.numel() * 2 + dark_h.numel() * 2 + flat_h.numel() * 2,
+               "d2h_bytes_per_step": vol_h.numel() * 4}
+        if rank == 0:
+            par["f32_e2e"] = parity(vol_h, zs[:1])
+        del raw_h, vol_h
+
+    cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 else None
+    if rank == 0:
+        launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
+        out = {
+            "metric": METRIC, "value": value, "unit": "GVoxel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": "f32", "data": DATA,
+            "config": {"workload": "%d^3 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
+                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (n, nt, n, n, args.chunk),
+                       "n": n, "ntheta": nt, "chunk_nz": args.chunk,
+                       "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw.numel() * 2 / 1e9)},
+            "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f16": 5e-3, "bf16": 5e-3},
+            "variants": variants, "input_generation_s": t_gen,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,19 @@ tcp_status tcp_filter(tcp_tensor* sino, int32_t filter, double center, void* str
 tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
                          int64_t ntheta, void* stream);
 
+/* Normalisation fused with the filter (Sec. 2.2 steps in order, one pass over
+ * HBM): -ln((raw - dark)/(flat - dark)) is computed in FP32 straight into the
+ * padded row in shared memory, filtered as tcp_filter_ex does, and the
+ * filtered sinogram is stored once in its dtype.  16-bit outputs are rounded
+ * after filtering only (rounding the unfiltered sinogram to BF16 loses
+ * accuracy to the ramp's removal of its low-frequency content, Sec. 2.1).
+ * raw: U16 [ntheta][nz][ndet]; dark, flat: F32 means [nz][ndet] or U16 frames
+ * [nf][nz][ndet]; sino: F32/F16/BF16 [nz][ntheta][ndet], must not overlap raw.
+ * ndet <= 4096. */
+tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
+                                void* stream);
+
 /* ----------------------------------------------------------- backproject -- */
 
 /* LineRec backprojection (Sec. 2.2, Sec. 3): for every voxel,
@@ -221,6 +234,61 @@ typedef struct {
 tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
                    const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
                    void* stream);
+
+/* Time every instantiated backprojector configuration on these tensors (the
+ * output is overwritten) and keep the fastest for later calls with the same
+ * shapes and dtypes (an explicit tcp_set_backproject_config still wins).
+ * Synchronises `stream`.  best / best_ms may be NULL. */
+tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta, double center,
+                                    tcp_tensor* vol, void* stream, tcp_bp_config* best, float* best_ms);
+
+/* -------------------------------------------------------------- batching -- */
+
+/* A batch reconstructs many datasets of uneven width and angle count: per
+ * dataset the fused normalise+filter kernel, then ONE persistent
+ * backprojection launch whose blocks pull (dataset, slice block, 32x32 tile)
+ * work units from an atomic counter, longest angle count first.  No block
+ * waits on another.  The run can be captured into a CUDA graph and replayed
+ * (the counter is reset by a memset node inside the graph). */
+typedef struct tcp_batch tcp_batch;
+
+typedef struct {
+  tcp_tensor raw;       /* U16 [ntheta][nz][ndet], device */
+  tcp_tensor dark;      /* U16 frames [nf][nz][ndet] or F32 means [nz][ndet], device */
+  tcp_tensor flat;      /* same forms as dark */
+  tcp_tensor vol;       /* F32/F16/BF16 [nz][n][n], device; one dtype per batch */
+  const double* theta;  /* host FP64 [ntheta]; read during tcp_batch_create only */
+  double center;        /* rotation axis of this dataset */
+  int32_t filter;       /* tcp_filter_kind */
+  int32_t pad_mode;     /* tcp_pad_mode */
+} tcp_batch_item;
+
+typedef struct {
+  int32_t sino_dtype;   /* storage of the filtered sinograms (F16 when opts is NULL) */
+  int32_t autotune;     /* 1: time every backprojector configuration on this batch */
+  int32_t reserved[2];
+} tcp_batch_opts;
+
+/* Validate the items, allocate the batch's device workspaces (one filtered
+ * sinogram per dataset, FP32 means for frame inputs, the work list) with
+ * cudaMalloc, build the angle and filter tables and, with autotune, run the
+ * batch once per configuration on `stream` (synchronising it).  The tensors'
+ * memory must stay valid while the batch is used.  *out is NULL on failure. */
+tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const tcp_batch_opts* opts,
+                            void* stream, tcp_batch** out);
+/* Launch one run on `stream` (asynchronous). */
+tcp_status tcp_batch_run(tcp_batch* b, void* stream);
+/* Capture one run on `stream` (a non-default stream) into the batch's CUDA
+ * graph and instantiate it; nothing executes during capture. */
+tcp_status tcp_batch_capture(tcp_batch* b, void* stream);
+/* Launch the captured graph on `stream`. */
+tcp_status tcp_batch_replay(tcp_batch* b, void* stream);
+/* Chosen configuration, autotune time of the winner (ms, 0 without autotune),
+ * work units and persistent grid size.  Any output may be NULL. */
+tcp_status tcp_batch_info(const tcp_batch* b, tcp_bp_config* cfg, float* tuned_ms, int64_t* work_units,
+                          int32_t* grid_blocks);
+/* Synchronise the device and free the batch (NULL is accepted). */
+tcp_status tcp_batch_destroy(tcp_batch* b);
 
 #ifdef __cplusplus
 }

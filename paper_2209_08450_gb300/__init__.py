@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import TcpError, load  # noqa: F401
 
-__all__ = ["frame_mean", "normalize", "filter_", "backproject", "project", "device_check",
+__all__ = ["frame_mean", "normalize", "normalize_filter", "filter_", "backproject", "project", "device_check",
            "set_checked", "cache_clear", "set_backproject_config", "get_backproject_config",
            "TcpError", "load", "padded_length"]
 
@@ -63,6 +63,26 @@ def normalize(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, out: to
 
     r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
     _lib.call("tcp_normalize", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.stream_ptr(stream))
+    return out
+
+
+def normalize_filter(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, center: float,
+                     filter: str = "shepp", pad: str = "edge", out: torch.Tensor | None = None,
+                     dtype=torch.float32, stream=None) -> torch.Tensor:
+    """Fused normalise + filter: raw uint16 [theta][z][j] -> filtered sinogram
+    [z][theta][j] in `dtype`, -log computed in FP32 in shared memory and the
+    result rounded once (the 16-bit-safe order of the two steps)."""
+    raw = _as_u16(raw)
+    nt, nz, nd = raw.shape
+    if out is None:
+        out = torch.empty((nz, nt, nd), dtype=_lib.DTYPES[dtype], device=raw.device)
+
+    def dd(x):
+        return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
+
+    r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
+    _lib.call("tcp_normalize_filter", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.FILTERS[filter],
+              float(center), _lib.PADS[pad], _lib.stream_ptr(stream))
     return out
 
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "tcp_frame_mean": ([_T, _T, _P], _I32),
     "tcp_normalize": ([_T, _T, _T, _T, _P], _I32),
     "tcp_filter": ([_T, _I32, _D, _P], _I32),
+    "tcp_normalize_filter": ([_T, _T, _T, _T, _I32, _D, _I32, _P], _I32),
     "tcp_filter_ex": ([_T, _I32, _D, _I32, _I64, _P], _I32),
     "tcp_backproject": ([_T, _P, _D, _T, _P], _I32),
     "tcp_project": ([_T, _P, _D, _T, _P], _I32),
@@ -143,3 +144,26 @@ def theta_array(theta) -> np.ndarray:
     if isinstance(theta, torch.Tensor):
         theta = theta.detach().cpu().numpy()
     return np.ascontiguousarray(theta, dtype=np.float64)
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("raw", TcpTensor), ("dark", TcpTensor), ("flat", TcpTensor), ("vol", TcpTensor),
+                ("theta", ctypes.c_void_p), ("center", ctypes.c_double), ("filter", ctypes.c_int32),
+                ("pad_mode", ctypes.c_int32)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("sino_dtype", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+SIGNATURES.update({
+    "tcp_autotune_backproject": ([_T, _P, _D, _T, _P, ctypes.POINTER(BpConfig), ctypes.POINTER(ctypes.c_float)], _I32),
+    "tcp_batch_create": ([ctypes.POINTER(BatchItem), _I32, ctypes.POINTER(BatchOpts), _P,
+                          ctypes.POINTER(ctypes.c_void_p)], _I32),
+    "tcp_batch_run": ([_P, _P], _I32),
+    "tcp_batch_capture": ([_P, _P], _I32),
+    "tcp_batch_replay": ([_P, _P], _I32),
+    "tcp_batch_info": ([_P, ctypes.POINTER(BpConfig), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I64),
+                        ctypes.POINTER(_I32)], _I32),
+    "tcp_batch_destroy": ([_P], _I32),
+})

@@ -134,6 +134,10 @@ static std::vector<double> filter_response(int64_t npad, int32_t filter) {
     h[(size_t)m] = v;
     h[(size_t)(npad - m)] = v;
   }
+  if ((npad / 2) % 2 == 1) {  // m = -npad/2 belongs to the period (odd only when npad == 2)
+    const double m = (double)(npad / 2);
+    h[(size_t)(npad / 2)] = -1.0 / (M_PI * M_PI * m * m);
+  }
   fft64(h);
   for (int64_t k = 0; k <= npad / 2; ++k) {
     const double nu = (double)k / (double)npad;
@@ -314,6 +318,8 @@ static bool is_float(int dt) { return dt == TCP_F32 || dt == TCP_F16 || dt == TC
 
 static tcp_bp_config g_bp_override{0, 0, 0, 0};
 
+tcp_bp_config bp_override() { return g_bp_override; }
+
 }  // namespace tcp
 
 using namespace tcp;
@@ -373,8 +379,34 @@ tcp_status tcp_frame_mean(const tcp_tensor* frames, tcp_tensor* mean, void* stre
   return launch_frame_mean(view3(frames), view3(mean), reinterpret_cast<cudaStream_t>(stream));
 }
 
+static tcp_status normalize_impl(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                 tcp_tensor* sino, const FilterTable* ft, int32_t pad_mode, void* stream);
+
 tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat, tcp_tensor* sino,
                          void* stream) {
+  return normalize_impl(raw, dark, flat, sino, nullptr, TCP_PAD_EDGE, stream);
+}
+
+tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, void* stream) {
+  if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "unknown filter");
+  if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  if (sino && sino->ndim == 3 && sino->shape[2] > 4096)
+    return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
+  FilterTable ft;
+  tcp_status s;
+  if (raw && sino && raw->ndim == 3 && sino->ndim == 3 && numel(sino) > 0 && numel(raw) > 0) {
+    if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+    if ((s = get_filter_table(sino->shape[2], filter, sino->shape[1], center, &ft)) != TCP_OK) return s;
+  } else {
+    ft.npad = 0;
+  }
+  return normalize_impl(raw, dark, flat, sino, &ft, pad_mode, stream);
+}
+
+static tcp_status normalize_impl(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                 tcp_tensor* sino, const FilterTable* ft, int32_t pad_mode, void* stream) {
   tcp_status s;
   if ((s = check_tensor(raw, "raw", 3, 3)) != TCP_OK) return s;
   if ((s = check_tensor(dark, "dark", 2, 3)) != TCP_OK) return s;
@@ -421,7 +453,8 @@ tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tc
       fv = m;
     }
   }
-  s = launch_normalize(view3(raw), dv, fv, view3(sino), st);
+  s = ft ? launch_normalize_filter(view3(raw), dv, fv, view3(sino), *ft, pad_mode, st)
+         : launch_normalize(view3(raw), dv, fv, view3(sino), st);
   if (scratch) {
     cudaError_t e = cudaFreeAsync(scratch, st);
     if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
@@ -463,7 +496,8 @@ tcp_status tcp_set_backproject_config(const tcp_bp_config* cfg) {
 tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n, int32_t sdt, int32_t vdt,
                                       tcp_bp_config* cfg) {
   if (!cfg) return fail(TCP_ERR_ARG, "null config");
-  *cfg = g_bp_override.k_slices ? g_bp_override : default_bp_config(nz, ntheta, ndet, n, sdt, vdt);
+  if (g_bp_override.k_slices) *cfg = g_bp_override;
+  else if (!tuned_bp_config(nz, ntheta, ndet, n, sdt, vdt, cfg)) *cfg = default_bp_config(nz, ntheta, ndet, n, sdt, vdt);
   return TCP_OK;
 }
 

@@ -90,32 +90,26 @@ template <> struct Interp<__nv_bfloat16> {
   }
 };
 
-struct BpArgs {
-  const void* sino;
-  int64_t s_z, s_t;  // sinogram strides (elements)
-  int nz, ntheta, ndet;
-  void* vol;
-  int64_t v_z, v_y;  // volume strides (elements)
-  int n;
-  int ntx;  // tiles along x
-  const double2* trig;
-  double center, half_n;
-  uint32_t* err;
+template <class TS, int K, int T>
+struct BpSmem {
+  Geo geo[T];
+  int wst[T];
+  typename Win<TS>::type win[T * K * kWin];
 };
 
+// One work unit: the aligned 32x32 voxel tile (gx, gy) times slices
+// [z0, z0 + K), summed over every angle.  Ends with a block barrier, so the
+// shared buffers may be reused by the next unit.
 template <class TS, class TV, int K, int T, int R, bool CHECK>
-__global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
+__device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0, BpSmem<TS, K, T>& sm) {
   using WT = typename Win<TS>::type;
   using I = Interp<TS>;
   constexpr int NW = 32 / R;  // warps per block (rows per pass)
   constexpr int NT = 32 * NW;
+  Geo* geo = sm.geo;
+  int* wst = sm.wst;
+  WT* win = sm.win;
 
-  __shared__ Geo geo[T];
-  __shared__ int wst[T];
-  __shared__ WT win[T * K * kWin];
-
-  const int gx = blockIdx.x % a.ntx, gy = blockIdx.x / a.ntx;
-  const int z0 = blockIdx.y * K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const TS* sino = reinterpret_cast<const TS*>(a.sino);
 
@@ -192,16 +186,65 @@ __global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
   }
 }
 
+template <class TS, class TV, int K, int T, int R, bool CHECK>
+__global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
+  __shared__ BpSmem<TS, K, T> sm;
+  bp_tile<TS, TV, K, T, R, CHECK>(a, blockIdx.x % a.ntx, blockIdx.x / a.ntx, blockIdx.y * K, sm);
+}
+
+// Persistent form for batches of datasets with uneven widths and angle
+// counts: a grid sized to the resident capacity pulls work units from one
+// atomic counter.  Unit u belongs to the item with prefix[i] <= u <
+// prefix[i+1]; inside an item, units run over 32x32 tiles fastest, then slice
+// blocks.  No block ever waits on another (the counter is the only shared
+// state), so every launch completes regardless of scheduling.
+template <class TS, class TV, int K, int T, int R, bool CHECK>
+__global__ void __launch_bounds__(32 * (32 / R)) k_backproject_persistent(BpWork w) {
+  __shared__ BpSmem<TS, K, T> sm;
+  __shared__ long long s_unit;
+  __shared__ int s_item;
+  __shared__ BpArgs s_args;
+  const long long total = w.prefix[w.nitems];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long u = (long long)atomicAdd(w.counter, 1ull);
+      int it = 0;
+      if (u < total)
+        while (u >= w.prefix[it + 1]) ++it;
+      s_unit = u;
+      s_item = it;
+    }
+    __syncthreads();
+    const long long u = s_unit;
+    if (u >= total) break;
+    const int it = s_item;
+    if (threadIdx.x == 0) s_args = w.items[it];
+    __syncthreads();
+    const long long local = u - w.prefix[it];
+    const long long tiles = (long long)s_args.ntx * s_args.ntx;
+    const int zb = (int)(local / tiles);
+    const int tile = (int)(local - (long long)zb * tiles);
+    bp_tile<TS, TV, K, T, R, CHECK>(s_args, tile % s_args.ntx, tile / s_args.ntx, zb * K, sm);
+  }
+}
+
 using Kern = void (*)(BpArgs);
+using PKern = void (*)(BpWork);
+
+struct KernPair {
+  Kern direct;
+  PKern persistent;
+};
 
 template <class TS, class TV, int K, int T, int R>
-Kern pick_check(bool check) {
-  return check ? k_backproject<TS, TV, K, T, R, true> : k_backproject<TS, TV, K, T, R, false>;
+KernPair pick_check(bool check) {
+  if (check) return {k_backproject<TS, TV, K, T, R, true>, k_backproject_persistent<TS, TV, K, T, R, true>};
+  return {k_backproject<TS, TV, K, T, R, false>, k_backproject_persistent<TS, TV, K, T, R, false>};
 }
 
 // Instantiated configurations (k_slices, theta_stage, rows_per_thread).
 template <class TS, class TV>
-Kern pick(const tcp_bp_config& c, bool check) {
+KernPair pick(const tcp_bp_config& c, bool check) {
 #define TCP_BP_CASE(K, T, R) \
   if (c.k_slices == K && c.theta_stage == T && c.rows_per_thread == R) return pick_check<TS, TV, K, T, R>(check);
   TCP_BP_CASE(8, 16, 4)
@@ -212,23 +255,54 @@ Kern pick(const tcp_bp_config& c, bool check) {
   TCP_BP_CASE(2, 16, 4)
   TCP_BP_CASE(1, 32, 4)
 #undef TCP_BP_CASE
-  return nullptr;
+  return {nullptr, nullptr};
 }
 
 template <class TS>
-Kern pick_vol(int vdt, const tcp_bp_config& c, bool check) {
+KernPair pick_vol(int vdt, const tcp_bp_config& c, bool check) {
   switch (vdt) {
     case TCP_F32: return pick<TS, float>(c, check);
     case TCP_F16: return pick<TS, __half>(c, check);
     case TCP_BF16: return pick<TS, __nv_bfloat16>(c, check);
   }
-  return nullptr;
+  return {nullptr, nullptr};
+}
+
+KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
+  switch (sdt) {
+    case TCP_F32: return pick_vol<float>(vdt, c, check);
+    case TCP_F16: return pick_vol<__half>(vdt, c, check);
+    case TCP_BF16: return pick_vol<__nv_bfloat16>(vdt, c, check);
+  }
+  return {nullptr, nullptr};
 }
 
 }  // namespace
 
 bool valid_bp_config(const tcp_bp_config& c) {
-  return pick<float, float>(c, false) != nullptr;
+  return pick<float, float>(c, false).direct != nullptr;
+}
+
+int bp_threads(const tcp_bp_config& c) { return 32 * (32 / c.rows_per_thread); }
+
+tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks) {
+  KernPair kp = pick_all(sdt, vdt, cfg, checked_mode());
+  if (!kp.persistent) return fail(TCP_ERR_UNSUPPORTED, "backproject: no persistent kernel for this dtype/config");
+  int per_sm = 0, dev = 0, sms = 0;
+  TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp.persistent, bp_threads(cfg), 0));
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
+  TCP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  *blocks = std::max(1, per_sm) * sms;
+  return TCP_OK;
+}
+
+tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, const tcp_bp_config& cfg, int blocks,
+                                         cudaStream_t st) {
+  KernPair kp = pick_all(sdt, vdt, cfg, checked_mode());
+  if (!kp.persistent) return fail(TCP_ERR_UNSUPPORTED, "backproject: no persistent kernel for this dtype/config");
+  kp.persistent<<<blocks, bp_threads(cfg), 0, st>>>(w);
+  TCP_CUDA_TRY(cudaGetLastError());
+  return TCP_OK;
 }
 
 tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, int) {
@@ -242,15 +316,19 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st) {
-  const bool check = checked_mode();
-  Kern k = nullptr;
-  switch (sino.dtype) {
-    case TCP_F32: k = pick_vol<float>(vol.dtype, cfg, check); break;
-    case TCP_F16: k = pick_vol<__half>(vol.dtype, cfg, check); break;
-    case TCP_BF16: k = pick_vol<__nv_bfloat16>(vol.dtype, cfg, check); break;
-  }
+  Kern k = pick_all(sino.dtype, vol.dtype, cfg, checked_mode()).direct;
   if (!k) return fail(TCP_ERR_UNSUPPORTED, "backproject: no kernel for this dtype/config");
   if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
+  BpArgs a = make_bp_args(sino, trig, center, vol);
+  const int threads = bp_threads(cfg);
+  dim3 grid((unsigned)(a.ntx * a.ntx), (unsigned)((a.nz + cfg.k_slices - 1) / cfg.k_slices));
+  if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject: too many slice blocks");
+  k<<<grid, threads, 0, st>>>(a);
+  TCP_CUDA_TRY(cudaGetLastError());
+  return TCP_OK;
+}
+
+BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol) {
   BpArgs a;
   a.sino = sino.p;
   a.s_z = sino.s0;
@@ -267,12 +345,7 @@ tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double c
   a.center = center;
   a.half_n = 0.5 * (double)a.n;
   a.err = device_error_word();
-  const int threads = 32 * (32 / cfg.rows_per_thread);
-  dim3 grid((unsigned)(a.ntx * a.ntx), (unsigned)((a.nz + cfg.k_slices - 1) / cfg.k_slices));
-  if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject: too many slice blocks");
-  k<<<grid, threads, 0, st>>>(a);
-  TCP_CUDA_TRY(cudaGetLastError());
-  return TCP_OK;
+  return a;
 }
 
 }  // namespace tcp

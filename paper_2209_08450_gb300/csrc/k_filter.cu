@@ -1,18 +1,27 @@
 // One-dimensional FBP filter of every detector row (Sec. 2.2 of the TomocuPy
 // paper: Shepp-Logan / Parzen filtering in Fourier space, rows padded before
-// the FFT).
+// the FFT), optionally fused with the dark/flat normalisation and -log.
 //
 // GB300 design: the whole padded row lives in shared memory; no padded copy
 // ever touches HBM.  Two real rows travel as one complex row z = a + i b:
 // because the filter response is Hermitian (F[N-k] = conj(F[k])), filtering z
 // filters a and b independently, so one complex FFT pair serves two rows
-// without a separation step.  The FFT is a Stockham auto-sort transform with
-// radix-4 passes (one radix-2 pass when log2 N is odd), each thread holding up
-// to four butterflies in registers between the shared-memory read and write
-// phases.  Twiddles and the response are FP64-derived tables; the arithmetic
-// is FP32.  The response folds in the window, the pi/N_theta FBP weight, the
-// 1/N of the inverse transform and the phase that moves the rotation axis to
-// ndet/2.
+// without a separation step.  The FFT is a Stockham auto-sort transform
+// (radix-4 passes, one radix-2 pass when log2 N is odd) between two
+// shared-memory buffers, one barrier per pass.  Twiddles and the response are
+// FP64-derived tables; the arithmetic is FP32.  The response folds in the
+// window, the pi/N_theta FBP weight, the 1/N of the inverse transform and the
+// phase that moves the rotation axis to ndet/2.
+//
+// Fused mode reads uint16 projections and computes -ln((raw-dark)/(flat-dark))
+// in FP32 while filling shared memory, so an FP16/BF16 sinogram is rounded
+// once, after filtering.  Rounding the unfiltered sinogram to 16 bits would
+// lose accuracy: the ramp removes its large low-frequency content and keeps
+// the rounding noise (the large-minus-small hazard of Sec. 2.1).
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "tcp_internal.cuh"
 
 namespace tcp {
@@ -23,91 +32,82 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by -i (forward) or +i (inverse)
+// multiply by -i (forward transform) or +i (inverse)
 template <bool INV> __device__ __forceinline__ float2 rot(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-constexpr int kMaxB = 4;  // butterflies per thread per pass
-
-template <bool INV>
-__device__ void radix2_first(float2* x, int N, int nthreads) {
-  // Ns = 1: no twiddles.
+// Stockham pass of radix 2 with Ns = 1 (no twiddles): in -> out.
+__device__ __forceinline__ void radix2_first(const float2* in, float2* out, int N) {
   const int nb = N / 2;
-  float2 v[2 * kMaxB][2];
-#pragma unroll
-  for (int i = 0; i < 2 * kMaxB; ++i) {
-    const int b = threadIdx.x + i * nthreads;
-    if (b < nb) {
-      v[i][0] = x[b];
-      v[i][1] = x[b + nb];
-    }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const float2 v0 = in[b], v1 = in[b + nb];
+    out[2 * b] = cadd(v0, v1);
+    out[2 * b + 1] = csub(v0, v1);
   }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 2 * kMaxB; ++i) {
-    const int b = threadIdx.x + i * nthreads;
-    if (b < nb) {
-      x[2 * b] = cadd(v[i][0], v[i][1]);
-      x[2 * b + 1] = csub(v[i][0], v[i][1]);
-    }
-  }
-  __syncthreads();
 }
 
+// Stockham pass of radix 4: in -> out, sub-transform size Ns.
 template <bool INV>
-__device__ void radix4_pass(float2* x, int N, int Ns, const float2* tw, int nthreads) {
+__device__ __forceinline__ void radix4_pass(const float2* in, float2* out, int N, int Ns, const float2* tw) {
   const int nb = N / 4;
   const int step = N / (4 * Ns);
-  float2 v[kMaxB][4];
-#pragma unroll
-  for (int i = 0; i < kMaxB; ++i) {
-    const int b = threadIdx.x + i * nthreads;
-    if (b < nb) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) v[i][r] = x[b + r * nb];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kMaxB; ++i) {
-    const int b = threadIdx.x + i * nthreads;
-    if (b < nb) {
-      const int k = b & (Ns - 1);
-      if (Ns > 1) {
-#pragma unroll
-        for (int r = 1; r < 4; ++r) {
-          float2 w = __ldg(tw + r * k * step);
-          if (INV) w.y = -w.y;
-          v[i][r] = cmul(v[i][r], w);
-        }
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    float2 v0 = in[b], v1 = in[b + nb], v2 = in[b + 2 * nb], v3 = in[b + 3 * nb];
+    const int k = b & (Ns - 1);
+    if (Ns > 1) {
+      float2 w1 = __ldg(tw + k * step), w2 = __ldg(tw + 2 * k * step), w3 = __ldg(tw + 3 * k * step);
+      if (INV) {
+        w1.y = -w1.y;
+        w2.y = -w2.y;
+        w3.y = -w3.y;
       }
-      const float2 s02 = cadd(v[i][0], v[i][2]), d02 = csub(v[i][0], v[i][2]);
-      const float2 s13 = cadd(v[i][1], v[i][3]), d13 = rot<INV>(csub(v[i][1], v[i][3]));
-      const int o = (b - k) * 4 + k;
-      x[o] = cadd(s02, s13);
-      x[o + Ns] = cadd(d02, d13);
-      x[o + 2 * Ns] = csub(s02, s13);
-      x[o + 3 * Ns] = csub(d02, d13);
+      v1 = cmul(v1, w1);
+      v2 = cmul(v2, w2);
+      v3 = cmul(v3, w3);
     }
+    const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
+    const float2 s13 = cadd(v1, v3), d13 = rot<INV>(csub(v1, v3));
+    const int o = (b - k) * 4 + k;
+    out[o] = cadd(s02, s13);
+    out[o + Ns] = cadd(d02, d13);
+    out[o + 2 * Ns] = csub(s02, s13);
+    out[o + 3 * Ns] = csub(d02, d13);
   }
-  __syncthreads();
 }
 
+// Transform x (in buffer `a`, scratch `b`); returns the buffer with the result.
 template <bool INV>
-__device__ void fft(float2* x, int N, int log2N, const float2* tw, int nthreads) {
+__device__ float2* fft(float2* a, float2* b, int N, int log2N, const float2* tw) {
   int Ns = 1;
   if (log2N & 1) {
-    radix2_first<INV>(x, N, nthreads);
+    radix2_first(a, b, N);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
     Ns = 2;
   }
-  for (; Ns < N; Ns *= 4) radix4_pass<INV>(x, N, Ns, tw, nthreads);
+  for (; Ns < N; Ns *= 4) {
+    radix4_pass<INV>(a, b, N, Ns, tw);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
 }
 
 struct FiltArgs {
-  void* sino;
-  int64_t s0, s1;  // strides of the [d0][d1] row grid
-  int d1;          // rows per outer index
+  // source rows: filtered sinogram [d0][d1][nd] (in place) or raw projections
+  const void* src;
+  int64_t s0, s1;   // source strides (sino: z, theta; raw: theta, z)
+  const float* dark;
+  const float* flat;
+  int64_t dm, fm;   // z strides of the means
+  void* dst;        // sinogram [d0][d1][nd]
+  int64_t t0, t1;   // destination strides (z, theta)
+  int d1;           // rows per z (= ntheta)
   int64_t rows;
   int nd, npad, log2n, left;
   int pad_zero;
@@ -115,62 +115,71 @@ struct FiltArgs {
   const float2* tw;
 };
 
-template <class TS>
-__global__ void k_filter(FiltArgs a) {
-  extern __shared__ float2 buf[];
-  const int nthreads = blockDim.x;
-  TS* base = reinterpret_cast<TS*>(a.sino);
+template <bool RAW, class TIn>
+__device__ __forceinline__ float load_sample(const FiltArgs& a, int64_t z, int64_t t, int j) {
+  if constexpr (RAW) {
+    const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(a.src) + t * a.s0 + z * a.s1 + j);
+    return neglog_ratio((float)v, __ldg(a.dark + z * a.dm + j), __ldg(a.flat + z * a.fm + j));
+  } else {
+    return Store<TIn>::load(reinterpret_cast<const TIn*>(a.src) + z * a.s0 + t * a.s1 + j);
+  }
+}
+
+template <bool RAW, class TIn, class TOut>
+__global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
+  extern __shared__ float2 smem[];
+  float2* bufA = smem;
+  float2* bufB = smem + a.npad;
   const int64_t npairs = (a.rows + 1) / 2;
   for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int64_t r0 = 2 * p, r1 = 2 * p + 1;
     const bool has1 = r1 < a.rows;
-    TS* row0 = base + (r0 / a.d1) * a.s0 + (r0 % a.d1) * a.s1;
-    TS* row1 = has1 ? base + (r1 / a.d1) * a.s0 + (r1 % a.d1) * a.s1 : row0;
-    for (int m = threadIdx.x; m < a.npad; m += nthreads) {
+    const int64_t z0 = r0 / a.d1, t0 = r0 - z0 * a.d1;
+    const int64_t z1 = has1 ? r1 / a.d1 : z0, t1 = has1 ? r1 - z1 * a.d1 : t0;
+    for (int m = threadIdx.x; m < a.npad; m += blockDim.x) {
       int j = m - a.left;
       float re = 0.f, im = 0.f;
-      if (a.pad_zero) {
-        if (j >= 0 && j < a.nd) {
-          re = Store<TS>::load(row0 + j);
-          im = has1 ? Store<TS>::load(row1 + j) : 0.f;
-        }
-      } else {
-        j = min(max(j, 0), a.nd - 1);
-        re = Store<TS>::load(row0 + j);
-        im = has1 ? Store<TS>::load(row1 + j) : 0.f;
+      bool inside = true;
+      if (a.pad_zero) inside = j >= 0 && j < a.nd;
+      else j = min(max(j, 0), a.nd - 1);
+      if (inside) {
+        re = load_sample<RAW, TIn>(a, z0, t0, j);
+        im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
       }
-      buf[m] = make_float2(re, im);
+      bufA[m] = make_float2(re, im);
     }
     __syncthreads();
-    fft<false>(buf, a.npad, a.log2n, a.tw, nthreads);
+    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, a.tw);
     const int half = a.npad / 2;
-    for (int k = threadIdx.x; k < a.npad; k += nthreads) {
+    for (int k = threadIdx.x; k < a.npad; k += blockDim.x) {
       float2 F = __ldg(a.resp + (k <= half ? k : a.npad - k));
       if (k > half) F.y = -F.y;
-      buf[k] = cmul(buf[k], F);
+      x[k] = cmul(x[k], F);
     }
     __syncthreads();
-    fft<true>(buf, a.npad, a.log2n, a.tw, nthreads);
-    for (int j = threadIdx.x; j < a.nd; j += nthreads) {
-      const float2 v = buf[a.left + j];
-      Store<TS>::put(row0 + j, v.x);
-      if (has1) Store<TS>::put(row1 + j, v.y);
+    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, a.tw);
+    TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
+    TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
+    for (int j = threadIdx.x; j < a.nd; j += blockDim.x) {
+      const float2 v = y[a.left + j];
+      Store<TOut>::put(o0 + j, v.x);
+      if (has1) Store<TOut>::put(o1 + j, v.y);
     }
     __syncthreads();
   }
 }
 
-}  // namespace
+template <bool RAW, class TIn>
+void (*pick_out(int dt))(FiltArgs) {
+  switch (dt) {
+    case TCP_F32: return k_filter<RAW, TIn, float>;
+    case TCP_F16: return k_filter<RAW, TIn, __half>;
+    case TCP_BF16: return k_filter<RAW, TIn, __nv_bfloat16>;
+  }
+  return nullptr;
+}
 
-// sino: [d0][d1][nd] rows (d0*d1 rows).
-tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode, cudaStream_t st) {
-  FiltArgs a;
-  a.sino = sino.p;
-  a.s0 = sino.s0;
-  a.s1 = sino.s1;
-  a.d1 = (int)sino.d1;
-  a.rows = sino.d0 * sino.d1;
-  a.nd = (int)sino.d2;
+tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_mode, cudaStream_t st) {
   a.npad = ft.npad;
   a.log2n = 0;
   while ((1 << a.log2n) < a.npad) ++a.log2n;
@@ -179,21 +188,81 @@ tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode,
   a.resp = ft.response;
   a.tw = ft.twiddle;
   if (a.rows == 0 || a.nd == 0) return TCP_OK;
-  const int threads = std::max(32, std::min(512, a.npad / (4 * kMaxB)));
-  const size_t smem = (size_t)a.npad * sizeof(float2);
-  void (*k)(FiltArgs) = nullptr;
-  switch (sino.dtype) {
-    case TCP_F32: k = k_filter<float>; break;
-    case TCP_F16: k = k_filter<__half>; break;
-    case TCP_BF16: k = k_filter<__nv_bfloat16>; break;
-  }
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
-  TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int threads = std::max(32, std::min(256, a.npad / 8));
+  const size_t smem = 2 * (size_t)a.npad * sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
-  const int blocks = (int)std::min<int64_t>(npairs, 152 * 32);
+  int dev = 0;
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
+  // Kernel attributes and occupancy are looked up once per (device, kernel,
+  // padded length), so that later launches, including ones under CUDA-graph
+  // capture, only enqueue work.
+  static std::mutex mu;
+  static std::map<std::tuple<int, void*, int>, int> grid_cache;
+  int cap = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_tuple(dev, reinterpret_cast<void*>(k), a.npad);
+    auto it = grid_cache.find(key);
+    if (it == grid_cache.end()) {
+      TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 8192 * sizeof(float2))));
+      int per_sm = 1, sms = 0;
+      TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+      TCP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      it = grid_cache.emplace(key, std::max(1, per_sm) * sms * 8).first;
+    }
+    cap = it->second;
+  }
+  const int blocks = (int)std::min<int64_t>(npairs, cap);
   k<<<blocks, threads, smem, st>>>(a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
+}
+
+}  // namespace
+
+// In place: sino [d0][d1][nd] rows (d0*d1 rows).
+tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode, cudaStream_t st) {
+  FiltArgs a;
+  a.src = sino.p;
+  a.s0 = sino.s0;
+  a.s1 = sino.s1;
+  a.dst = sino.p;
+  a.t0 = sino.s0;
+  a.t1 = sino.s1;
+  a.dark = a.flat = nullptr;
+  a.dm = a.fm = 0;
+  a.d1 = (int)sino.d1;
+  a.rows = sino.d0 * sino.d1;
+  a.nd = (int)sino.d2;
+  void (*k)(FiltArgs) = nullptr;
+  switch (sino.dtype) {
+    case TCP_F32: k = k_filter<false, float, float>; break;
+    case TCP_F16: k = k_filter<false, __half, __half>; break;
+    case TCP_BF16: k = k_filter<false, __nv_bfloat16, __nv_bfloat16>; break;
+  }
+  return run(k, a, ft, pad_mode, st);
+}
+
+// Fused: raw [ntheta][nz][nd] u16, means [1][nz][nd] (s1 = z stride) ->
+// filtered sino [nz][ntheta][nd].
+tcp_status launch_normalize_filter(const View3& raw, const View3& dark, const View3& flat, const View3& sino,
+                                   const FilterTable& ft, int pad_mode, cudaStream_t st) {
+  FiltArgs a;
+  a.src = raw.p;
+  a.s0 = raw.s0;
+  a.s1 = raw.s1;
+  a.dark = reinterpret_cast<const float*>(dark.p);
+  a.flat = reinterpret_cast<const float*>(flat.p);
+  a.dm = dark.s1;
+  a.fm = flat.s1;
+  a.dst = sino.p;
+  a.t0 = sino.s0;
+  a.t1 = sino.s1;
+  a.d1 = (int)sino.d1;
+  a.rows = sino.d0 * sino.d1;
+  a.nd = (int)sino.d2;
+  return run(pick_out<true, uint16_t>(sino.dtype), a, ft, pad_mode, st);
 }
 
 }  // namespace tcp

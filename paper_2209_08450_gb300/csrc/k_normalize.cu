@@ -13,8 +13,6 @@
 namespace tcp {
 namespace {
 
-constexpr float kEps = 1e-6f;
-
 __global__ void k_frame_mean(const uint16_t* f, int nf, int64_t f0, int64_t f1, int nz, int nd,
                              float* mean, int64_t m0) {
   const int64_t total = (int64_t)nz * nd;
@@ -25,12 +23,6 @@ __global__ void k_frame_mean(const uint16_t* f, int nf, int64_t f0, int64_t f1, 
     for (int k = 0; k < nf; ++k) acc += __ldg(f + (int64_t)k * f0 + (int64_t)z * f1 + j);
     mean[(int64_t)z * m0 + j] = (float)((double)acc / (double)nf);
   }
-}
-
-__device__ __forceinline__ float neglog_ratio(float raw, float d, float f) {
-  float r = (raw - d) / (f - d);
-  if (!(r > kEps) || isinf(r)) r = kEps;
-  return -logf(r);
 }
 
 struct NormArgs {

@@ -236,12 +236,11 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
     fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
     View3 sv;
     sv.p = sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
-    TRY_S(launch_normalize(rv, dv, fv, sv, st));
+    TRY_S(launch_normalize_filter(rv, dv, fv, sv, ft, o.pad_mode, st));
     if (host_raw) {
       TCP_CUDA_TRY(cudaEventRecord(raw_free[b], st));
       if (k + B < nchunks) TRY_S(issue_copy_in(k + B));
     }
-    TRY_S(launch_filter(sv, ft, o.pad_mode, st));
     View3 vv;
     vv.dtype = vol->dtype; vv.d0 = c; vv.d1 = n; vv.d2 = n;
     if (host_vol) {

@@ -58,6 +58,16 @@ template <> struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ void put(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// ------------------------------------------------------ normalisation math --
+
+// Dark/flat correction and negative logarithm in FP32 (Sec. 2.2):
+// r = (raw - dark)/(flat - dark), r <- 1e-6 unless finite and > 1e-6, -ln r.
+__device__ __forceinline__ float neglog_ratio(float raw, float d, float f) {
+  float r = (raw - d) / (f - d);
+  if (!(r > 1e-6f) || isinf(r)) r = 1e-6f;
+  return -logf(r);
+}
+
 // ------------------------------------------------- canonical ray geometry --
 //
 // The ray coordinate of voxel (ix, iy) at angle theta is
@@ -127,11 +137,43 @@ tcp_status launch_frame_mean(const View3& frames, const View3& mean, cudaStream_
 tcp_status launch_normalize(const View3& raw, const View3& dark, const View3& flat, const View3& sino,
                             cudaStream_t st);
 tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode, cudaStream_t st);
+tcp_status launch_normalize_filter(const View3& raw, const View3& dark, const View3& flat, const View3& sino,
+                                   const FilterTable& ft, int pad_mode, cudaStream_t st);
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st);
 tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
                           cudaStream_t st);
 
+// Arguments of one backprojection (one dataset of a batch).
+struct BpArgs {
+  const void* sino;
+  int64_t s_z, s_t;  // sinogram strides (elements)
+  int nz, ntheta, ndet;
+  void* vol;
+  int64_t v_z, v_y;  // volume strides (elements)
+  int n;
+  int ntx;  // tiles along x (and y)
+  const double2* trig;
+  double center, half_n;
+  uint32_t* err;
+};
+
+// Work list of the persistent backprojector.
+struct BpWork {
+  const BpArgs* items;            // device array [nitems]
+  const long long* prefix;        // device array [nitems + 1], prefix sums of units
+  int nitems;
+  unsigned long long* counter;    // zeroed before each launch
+};
+
+BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol);
+int bp_threads(const tcp_bp_config& c);
+tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks);
+tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, const tcp_bp_config& cfg, int blocks,
+                                         cudaStream_t st);
+
+bool tuned_bp_config(int64_t nz, int64_t nt, int64_t nd, int64_t n, int sdt, int vdt, tcp_bp_config* cfg);
+tcp_bp_config bp_override();
 tcp_bp_config default_bp_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n, int sdt, int vdt);
 bool valid_bp_config(const tcp_bp_config& c);
 

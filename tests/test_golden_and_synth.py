@@ -69,3 +69,24 @@ def test_frames_statistics_and_seed():
     assert abs(raw[:, :, 15].mean() - (4e4 * np.exp(-2) + 100)) < 10
     raw2, *_ = synth.frames_from_line_integrals(p, np.random.default_rng(1), 4e4, 10, 10)
     assert np.array_equal(raw, raw2)
+
+
+def test_torch_sphere_generator_matches_host_closed_form():
+    import synth.gpu as sgpu
+    rng = np.random.default_rng(0)
+    sp = synth.porous_spheres(rng, 256, 64)
+    zs = np.arange(3) + 0.5
+    th = synth.uniform_theta(90)
+    a = sgpu.sphere_line_integrals(sp, zs, th, 256, 128.0, "cpu").numpy()
+    b = np.stack([synth.sphere_sinogram(sp, z, th, 256, 128.0) for z in zs], 1)
+    assert np.max(np.abs(a - b)) < 1e-5 * np.max(np.abs(b)) * 256
+
+
+def test_torch_ellipsoid_generator_statistics():
+    import synth.gpu as sgpu
+    raw, dark, flat, theta, c, mu = sgpu.ellipsoid_frames(64, 30, 3, seed=1, device="cpu", count=8)
+    assert raw.shape == (30, 3, 64) and dark.shape == (20, 3, 64) and flat.shape == (20, 3, 64)
+    u = raw.numpy().view(np.uint16)
+    assert u.max() <= 2e4 + 1000 and u.min() >= 0
+    assert abs(dark.numpy().view(np.uint16).mean() - 100) < 2
+    assert 31.5 - 2 <= c <= 31.5 + 2

@@ -242,9 +242,12 @@ def test_filter_explicit_ntheta_and_2d_rows():
 
 # -------------------------------------------------------------- end to end --
 
-def _fbp_gpu(ds, dt=torch.float32, vdt=None, kind="shepp"):
-    sino = tcp.normalize(u16(ds.raw), u16(ds.dark), u16(ds.flat), dtype=dt)
-    tcp.filter_(sino, ds.center, kind)
+def _fbp_gpu(ds, dt=torch.float32, vdt=None, kind="shepp", fused=False):
+    if fused:
+        sino = tcp.normalize_filter(u16(ds.raw), u16(ds.dark), u16(ds.flat), ds.center, kind, dtype=dt)
+    else:
+        sino = tcp.normalize(u16(ds.raw), u16(ds.dark), u16(ds.flat), dtype=dt)
+        tcp.filter_(sino, ds.center, kind)
     nd = ds.raw.shape[-1]
     return tcp.backproject(sino, ds.theta, nd / 2.0, dtype=vdt or dt)
 
@@ -258,10 +261,34 @@ def test_fbp_shepp_logan_256_fp32():
 
 @pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
 def test_fbp_shepp_logan_256_16bit(dt):
+    # 16-bit storage of the filtered sinogram and the volume (fused
+    # normalise+filter rounds once, after filtering)
     ds = synth.shepp_logan_dataset(nz=6)
-    got = host(_fbp_gpu(ds, dt))
+    got = host(_fbp_gpu(ds, dt, fused=True))
     ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
     assert rel(got, ref) <= 5e-3
+
+
+def test_fbp_shepp_logan_fp16_separate_steps():
+    # FP16 (11-bit significand) also holds the unfiltered sinogram well enough
+    ds = synth.shepp_logan_dataset(nz=4)
+    got = host(_fbp_gpu(ds, torch.float16, fused=False))
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    assert rel(got, ref) <= 5e-3
+
+
+@pytest.mark.parametrize("nd", [64, 203])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("means", [False, True])
+def test_normalize_filter_fused(nd, dt, means):
+    ds = synth.shepp_logan_dataset(ntheta=41, ndet=nd, nz=3, center=nd / 2 - 0.7, seed=nd + 1)
+    dark, flat = u16(ds.dark), u16(ds.flat)
+    if means:
+        dark, flat = tcp.frame_mean(dark), tcp.frame_mean(flat)
+    got = host(tcp.normalize_filter(u16(ds.raw), dark, flat, ds.center, "shepp", dtype=dt))
+    p = oracle.normalize(ds.raw, oracle.frame_mean(ds.dark), oracle.frame_mean(ds.flat))
+    ref = oracle.filter_sino(p, ds.center, "shepp", "edge")
+    assert rel(got, ref) <= TOL[dt]
 
 
 def test_fbp_ellipsoids_ragged():
