@@ -274,7 +274,7 @@ def main():
         return float(max(errs))
 
     zs = [int(x) for x in np.linspace(n // 5, 4 * n // 5, args.parity_slices)]
-    par = {"f32": parity(vol, zs)} if rank == 0 else {}
+    par = {"f32": parity(vol, zs)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
     s_chunk = torch.empty((args.chunk, nt, n), dtype=torch.float32, device=dev)
@@ -329,7 +329,7 @@ def main():
         vms = run_steps(dt, args.variant_steps, 1, vv)
         variants[name] = {"value": world * n ** 3 / (vms * 1e-3) / 1e9, "ms_per_step": vms,
                           "speedup_vs_f32": ms / vms}
-        if rank == 0:
+        if rank == 0 and zs:
             variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
         del vv
 
@@ -363,11 +363,11 @@ def main():
         e2e = {"value": world * n ** 3 / (ems * 1e-3) / 1e9, "unit": "GVoxel/s", "ms_per_step": ems,
                "h2d_bytes_per_step": raw_h.numel() * 2 + dark_h.numel() * 2 + flat_h.numel() * 2,
                "d2h_bytes_per_step": vol_h.numel() * 4}
-        if rank == 0:
+        if rank == 0 and zs:
             par["f32_e2e"] = parity(vol_h, zs[:1])
         del raw_h, vol_h
 
-    cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 else None
+    cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 and args.cpu_slices > 0 else None
     if rank == 0:
         launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
         out = {

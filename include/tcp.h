@@ -172,6 +172,17 @@ tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, c
                                 tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
                                 void* stream);
 
+/* tcp_normalize_filter with the response multiplied by `weight` instead of
+ * pi/ntheta (weight <= 0: pi/ntheta).  A weight that is a power of two times
+ * 1 (e.g. 1024 for FP16 storage) keeps small filtered values out of the FP16
+ * subnormal range; apply pi/ntheta/weight afterwards with
+ * tcp_backproject_ex (Sec. 2.1: reorder operations to stay in range).
+ * |filtered -log| <= 6.9 for every filter, so weight <= 2^13 cannot overflow
+ * FP16. */
+tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                   tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
+                                   double weight, void* stream);
+
 /* ----------------------------------------------------------- backproject -- */
 
 /* LineRec backprojection (Sec. 2.2, Sec. 3): for every voxel,
@@ -185,6 +196,11 @@ tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, c
  * FP32 in-tile offsets (|error| < 1e-5 px). */
 tcp_status tcp_backproject(const tcp_tensor* sino, const double* theta, double center,
                            tcp_tensor* vol, void* stream);
+
+/* tcp_backproject with every output voxel multiplied by `scale` (applied to
+ * the FP32 accumulator before the store). */
+tcp_status tcp_backproject_ex(const tcp_tensor* sino, const double* theta, double center,
+                              tcp_tensor* vol, double scale, void* stream);
 
 /* Adjoint Radon projector (not in the paper): the exact transpose of
  * tcp_backproject with the same interpolation weights,
@@ -228,7 +244,10 @@ typedef struct {
  * buffer; vol likewise.  Host inputs are copied on an internal copy stream into
  * a ring of device buffers while the previous chunk computes on `stream`; host
  * outputs are copied back on a third stream.  dark/flat: U16 frames or F32
- * means, on the device or the host.  Returns after queueing the work; the
+ * means, on the device or the host.  The intermediate sinogram holds the
+ * ramp-filtered -log times 2^10 for FP16 storage (times 1 otherwise); the
+ * pi/ntheta weight and the inverse storage scale are applied by the
+ * backprojector, so small values never fall into the FP16 subnormal range.  Returns after queueing the work; the
  * result is complete when `stream` is.  Device buffers of the ring are taken
  * from the stream-ordered allocator. */
 tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,

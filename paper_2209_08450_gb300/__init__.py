@@ -68,10 +68,11 @@ def normalize(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, out: to
 
 def normalize_filter(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, center: float,
                      filter: str = "shepp", pad: str = "edge", out: torch.Tensor | None = None,
-                     dtype=torch.float32, stream=None) -> torch.Tensor:
+                     dtype=torch.float32, weight: float | None = None, stream=None) -> torch.Tensor:
     """Fused normalise + filter: raw uint16 [theta][z][j] -> filtered sinogram
     [z][theta][j] in `dtype`, -log computed in FP32 in shared memory and the
-    result rounded once (the 16-bit-safe order of the two steps)."""
+    result rounded once (the 16-bit-safe order of the two steps).  `weight`
+    replaces the pi/ntheta factor (see backproject(scale=...))."""
     raw = _as_u16(raw)
     nt, nz, nd = raw.shape
     if out is None:
@@ -81,8 +82,8 @@ def normalize_filter(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, 
         return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
 
     r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
-    _lib.call("tcp_normalize_filter", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.FILTERS[filter],
-              float(center), _lib.PADS[pad], _lib.stream_ptr(stream))
+    _lib.call("tcp_normalize_filter_ex", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.FILTERS[filter],
+              float(center), _lib.PADS[pad], float(weight or 0.0), _lib.stream_ptr(stream))
     return out
 
 
@@ -96,16 +97,16 @@ def filter_(sino: torch.Tensor, center: float, filter: str = "shepp", pad: str =
 
 
 def backproject(sino: torch.Tensor, theta, center: float, n: int | None = None,
-                out: torch.Tensor | None = None, dtype=None, stream=None) -> torch.Tensor:
-    """LineRec backprojection sino[z][theta][j] -> vol[z][n][n] (sum over angles)."""
+                out: torch.Tensor | None = None, dtype=None, scale: float = 1.0, stream=None) -> torch.Tensor:
+    """LineRec backprojection sino[z][theta][j] -> vol[z][n][n]: scale x (sum over angles)."""
     th = _lib.theta_array(theta)
     nz, nt, nd = sino.shape
     if out is None:
         n = nd if n is None else n
         out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype or sino.dtype], device=sino.device)
     a, b = _lib.desc(sino), _lib.desc(out)
-    _lib.call("tcp_backproject", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
-              _lib.stream_ptr(stream))
+    _lib.call("tcp_backproject_ex", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
+              float(scale), _lib.stream_ptr(stream))
     return out
 
 

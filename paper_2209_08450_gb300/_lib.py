@@ -70,6 +70,8 @@ SIGNATURES = {
     "tcp_normalize": ([_T, _T, _T, _T, _P], _I32),
     "tcp_filter": ([_T, _I32, _D, _P], _I32),
     "tcp_normalize_filter": ([_T, _T, _T, _T, _I32, _D, _I32, _P], _I32),
+    "tcp_normalize_filter_ex": ([_T, _T, _T, _T, _I32, _D, _I32, _D, _P], _I32),
+    "tcp_backproject_ex": ([_T, _P, _D, _T, _D, _P], _I32),
     "tcp_filter_ex": ([_T, _I32, _D, _I32, _I64, _P], _I32),
     "tcp_backproject": ([_T, _P, _D, _T, _P], _I32),
     "tcp_project": ([_T, _P, _D, _T, _P], _I32),

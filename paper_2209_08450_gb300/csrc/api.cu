@@ -151,12 +151,12 @@ static std::vector<double> filter_response(int64_t npad, int32_t filter) {
 
 struct FiltKey {
   int dev;
-  int64_t npad, ndet, ntheta;
+  int64_t npad, ndet;
   int32_t filter;
-  double center;
+  double weight, center;
   bool operator==(const FiltKey& o) const {
-    return dev == o.dev && npad == o.npad && ndet == o.ndet && ntheta == o.ntheta && filter == o.filter &&
-           std::memcmp(&center, &o.center, sizeof(double)) == 0;
+    return dev == o.dev && npad == o.npad && ndet == o.ndet && filter == o.filter &&
+           std::memcmp(&weight, &o.weight, sizeof(double)) == 0 && std::memcmp(&center, &o.center, sizeof(double)) == 0;
   }
 };
 struct FiltKeyHash {
@@ -165,7 +165,7 @@ struct FiltKeyHash {
 static std::unordered_map<FiltKey, float2*, FiltKeyHash> g_resp;
 static std::unordered_map<uint64_t, float2*> g_tw;  // (dev << 32) | npad
 
-tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double center, FilterTable* out) {
+tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out) {
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
   const int64_t npad = padded_length(ndet);
@@ -174,7 +174,7 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double
   key.dev = dev;
   key.npad = npad;
   key.ndet = ndet;
-  key.ntheta = ntheta;
+  key.weight = weight;
   key.filter = filter;
   key.center = center;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -201,7 +201,7 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double
   if (rit == g_resp.end()) {
     const std::vector<double> H = filter_response(npad, filter);
     const double shift = center - 0.5 * (double)ndet;
-    const double scale = M_PI / (double)ntheta / (double)npad;
+    const double scale = weight / (double)npad;
     std::vector<float2> F(H.size());
     for (int64_t k = 0; k <= npad / 2; ++k) {
       const double ph = 2.0 * M_PI * ((double)k / (double)npad) * shift;
@@ -387,22 +387,30 @@ tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tc
   return normalize_impl(raw, dark, flat, sino, nullptr, TCP_PAD_EDGE, stream);
 }
 
-tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
-                                tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, void* stream) {
+tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                   tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, double weight,
+                                   void* stream) {
   if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "unknown filter");
   if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
   if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  if (!std::isfinite(weight)) return fail(TCP_ERR_ARG, "weight must be finite");
   if (sino && sino->ndim == 3 && sino->shape[2] > 4096)
     return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
   FilterTable ft;
   tcp_status s;
   if (raw && sino && raw->ndim == 3 && sino->ndim == 3 && numel(sino) > 0 && numel(raw) > 0) {
     if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
-    if ((s = get_filter_table(sino->shape[2], filter, sino->shape[1], center, &ft)) != TCP_OK) return s;
+    const double w = weight > 0 ? weight : M_PI / (double)sino->shape[1];
+    if ((s = get_filter_table(sino->shape[2], filter, w, center, &ft)) != TCP_OK) return s;
   } else {
     ft.npad = 0;
   }
   return normalize_impl(raw, dark, flat, sino, &ft, pad_mode, stream);
+}
+
+tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, void* stream) {
+  return tcp_normalize_filter_ex(raw, dark, flat, sino, filter, center, pad_mode, 0.0, stream);
 }
 
 static tcp_status normalize_impl(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
@@ -475,7 +483,7 @@ tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_
   const int64_t nt = ntheta > 0 ? ntheta : v.d1;
   if (numel(sino) == 0) return TCP_OK;
   FilterTable ft;
-  if ((s = get_filter_table(v.d2, filter, nt, center, &ft)) != TCP_OK) return s;
+  if ((s = get_filter_table(v.d2, filter, M_PI / (double)nt, center, &ft)) != TCP_OK) return s;
   return launch_filter(v, ft, pad_mode, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -503,7 +511,13 @@ tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, 
 
 tcp_status tcp_backproject(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol,
                            void* stream) {
+  return tcp_backproject_ex(sino, theta, center, vol, 1.0, stream);
+}
+
+tcp_status tcp_backproject_ex(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol,
+                              double scale, void* stream) {
   tcp_status s;
+  if (!std::isfinite(scale)) return fail(TCP_ERR_ARG, "scale must be finite");
   if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
   if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
   if (!is_float(sino->dtype) || !is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "sino/vol must be F32, F16 or BF16");
@@ -528,7 +542,7 @@ tcp_status tcp_backproject(const tcp_tensor* sino, const double* theta, double c
   if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
   tcp_bp_config cfg;
   tcp_get_backproject_config(sino->shape[0], nt, sino->shape[2], vol->shape[1], sino->dtype, vol->dtype, &cfg);
-  return launch_backproject(view3(sino), trig, center, view3(vol), cfg, st);
+  return launch_backproject(view3(sino), trig, center, view3(vol), cfg, st, (float)scale);
 }
 
 tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {

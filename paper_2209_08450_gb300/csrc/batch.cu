@@ -95,7 +95,8 @@ tcp_status set_config(tcp_batch* b, const tcp_bp_config& cfg) {
   std::vector<BpArgs> args;
   std::vector<long long> prefix(1, 0);
   for (const ItemRt& it : b->items) {
-    BpArgs a = make_bp_args(it.sino, it.trig, 0.5 * (double)it.sino.d2, it.vol);
+    const float scale = (float)(M_PI / (double)it.sino.d1 / storage_scale(b->sdt));
+    BpArgs a = make_bp_args(it.sino, it.trig, 0.5 * (double)it.sino.d2, it.vol, scale);
     args.push_back(a);
     const long long units = (long long)a.ntx * a.ntx * ((a.nz + cfg.k_slices - 1) / cfg.k_slices);
     prefix.push_back(prefix.back() + units);
@@ -248,7 +249,7 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     it.sino.p = w; it.sino.dtype = b->sdt; it.sino.d0 = nz; it.sino.d1 = nt; it.sino.d2 = nd;
     it.sino.s0 = nt * nd; it.sino.s1 = nd;
     if ((s = get_trig_table(in.theta, nt, &it.trig)) != TCP_OK) break;
-    if ((s = get_filter_table(nd, in.filter, nt, in.center, &it.ft)) != TCP_OK) break;
+    if ((s = get_filter_table(nd, in.filter, storage_scale(b->sdt), in.center, &it.ft)) != TCP_OK) break;
     b->items.push_back(it);
   }
   if (s == TCP_OK) {

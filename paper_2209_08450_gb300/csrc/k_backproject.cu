@@ -180,7 +180,7 @@ __device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0,
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int z = z0 + k;
-        if (z < a.nz) Store<TV>::put(vol + (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix, acc[r][k]);
+        if (z < a.nz) Store<TV>::put(vol + (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix, acc[r][k] * a.scale);
       }
     }
   }
@@ -315,11 +315,11 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
 }
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                              const tcp_bp_config& cfg, cudaStream_t st) {
+                              const tcp_bp_config& cfg, cudaStream_t st, float scale) {
   Kern k = pick_all(sino.dtype, vol.dtype, cfg, checked_mode()).direct;
   if (!k) return fail(TCP_ERR_UNSUPPORTED, "backproject: no kernel for this dtype/config");
   if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
-  BpArgs a = make_bp_args(sino, trig, center, vol);
+  BpArgs a = make_bp_args(sino, trig, center, vol, scale);
   const int threads = bp_threads(cfg);
   dim3 grid((unsigned)(a.ntx * a.ntx), (unsigned)((a.nz + cfg.k_slices - 1) / cfg.k_slices));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject: too many slice blocks");
@@ -328,8 +328,9 @@ tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double c
   return TCP_OK;
 }
 
-BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol) {
+BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol, float scale) {
   BpArgs a;
+  a.scale = scale;
   a.sino = sino.p;
   a.s_z = sino.s0;
   a.s_t = sino.s1;

@@ -7,8 +7,8 @@
 // because the filter response is Hermitian (F[N-k] = conj(F[k])), filtering z
 // filters a and b independently, so one complex FFT pair serves two rows
 // without a separation step.  The FFT is a Stockham auto-sort transform
-// (radix-4 passes, one radix-2 pass when log2 N is odd) between two
-// shared-memory buffers, one barrier per pass.  Twiddles and the response are
+// (radix-16 register butterflies, one pass of 8, 4 or 2 for the rest of
+// log2 N) between two shared-memory buffers, one barrier per pass.  Twiddles and the response are
 // FP64-derived tables; the arithmetic is FP32.  The response folds in the
 // window, the pi/N_theta FBP weight, the 1/N of the inverse transform and the
 // phase that moves the rotation axis to ndet/2.
@@ -37,63 +37,131 @@ template <bool INV> __device__ __forceinline__ float2 rot(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// Stockham pass of radix 2 with Ns = 1 (no twiddles): in -> out.
-__device__ __forceinline__ void radix2_first(const float2* in, float2* out, int N) {
-  const int nb = N / 2;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const float2 v0 = in[b], v1 = in[b + nb];
-    out[2 * b] = cadd(v0, v1);
-    out[2 * b + 1] = csub(v0, v1);
+// ------------------------------------------------------------ small DFTs --
+// In-register DFTs of 2, 4, 8 and 16 points, forward (W = e^{-2 pi i/R}) or
+// inverse.  Radix 16 is 4 x 4 Cooley-Tukey: four 4-point DFTs over the
+// stride-4 subsequences, twiddles W16^{kq}, four 4-point DFTs across them.
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  const float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
+  const float2 s13 = cadd(v1, v3), d13 = rot<INV>(csub(v1, v3));
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
+  v1 = cadd(d02, d13);
+  v3 = csub(d02, d13);
+}
+
+// multiply by W_R^e for a compile-time-known small angle (table of exact
+// constants for R = 8 and 16).
+template <bool INV>
+__device__ __forceinline__ float2 tw_const(float2 a, int e, int R) {
+  // e * (16 / R) indexes W16^m, m = 0..15
+  const int m = (e * (16 / R)) & 15;
+  constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f, H = 0.70710678118654752f;
+  const float cs[16] = {1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1, 0.f, S1, H, C1};
+  const float sn[16] = {0.f, S1, H, C1, 1.f, C1, H, S1, 0.f, -S1, -H, -C1, -1.f, -C1, -H, -S1};
+  // W16^m = cos(2 pi m/16) - i sin(2 pi m/16) (forward)
+  const float c = cs[m], s = INV ? sn[m] : -sn[m];
+  return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+  if constexpr (R == 2) {
+    dft2<INV>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // 2 x 4: two 4-point DFTs on even/odd, twiddle W8^q, 2-point across
+#pragma unroll
+    for (int k = 0; k < 2; ++k) dft4<INV>(v[k], v[k + 2], v[k + 4], v[k + 6]);
+    // now v[k + 2q] holds Y_k[q]
+    float2 o[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 a = v[2 * q], b = tw_const<INV>(v[1 + 2 * q], q, 8);
+      dft2<INV>(a, b);
+      o[q] = a;
+      o[q + 4] = b;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = o[i];
+  } else {
+    static_assert(R == 16, "radix");
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dft4<INV>(v[k], v[k + 4], v[k + 8], v[k + 12]);
+    // v[k + 4q] = Y_k[q]; twiddle by W16^{kq}
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+#pragma unroll
+      for (int q = 1; q < 4; ++q) v[k + 4 * q] = tw_const<INV>(v[k + 4 * q], k * q, 16);
+    float2 o[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 a = v[4 * q], b = v[4 * q + 1], c = v[4 * q + 2], d = v[4 * q + 3];
+      dft4<INV>(a, b, c, d);
+      o[q] = a;
+      o[q + 4] = b;
+      o[q + 8] = c;
+      o[q + 12] = d;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = o[i];
   }
 }
 
-// Stockham pass of radix 4: in -> out, sub-transform size Ns.
-template <bool INV>
-__device__ __forceinline__ void radix4_pass(const float2* in, float2* out, int N, int Ns, const float2* tw) {
-  const int nb = N / 4;
-  const int step = N / (4 * Ns);
+// Stockham pass of radix R: in -> out, sub-transform size Ns.
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int N, int Ns, const float2* tw) {
+  const int nb = N / R;
+  const int step = N / (R * Ns);
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    float2 v0 = in[b], v1 = in[b + nb], v2 = in[b + 2 * nb], v3 = in[b + 3 * nb];
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[b + r * nb];
     const int k = b & (Ns - 1);
     if (Ns > 1) {
-      float2 w1 = __ldg(tw + k * step), w2 = __ldg(tw + 2 * k * step), w3 = __ldg(tw + 3 * k * step);
-      if (INV) {
-        w1.y = -w1.y;
-        w2.y = -w2.y;
-        w3.y = -w3.y;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(tw + r * k * step);
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
       }
-      v1 = cmul(v1, w1);
-      v2 = cmul(v2, w2);
-      v3 = cmul(v3, w3);
     }
-    const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
-    const float2 s13 = cadd(v1, v3), d13 = rot<INV>(csub(v1, v3));
-    const int o = (b - k) * 4 + k;
-    out[o] = cadd(s02, s13);
-    out[o + Ns] = cadd(d02, d13);
-    out[o + 2 * Ns] = csub(s02, s13);
-    out[o + 3 * Ns] = csub(d02, d13);
+    dft<R, INV>(v);
+    const int o = (b - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[o + r * Ns] = v[r];
   }
 }
 
-// Transform x (in buffer `a`, scratch `b`); returns the buffer with the result.
+// Transform the data in `a` (scratch `b`); returns the buffer with the result.
+// Radix-16 passes while 16 divides the remaining length, then one pass of 8,
+// 4 or 2 for the remainder.
 template <bool INV>
 __device__ float2* fft(float2* a, float2* b, int N, int log2N, const float2* tw) {
   int Ns = 1;
-  if (log2N & 1) {
-    radix2_first(a, b, N);
+  int rem = log2N;
+  while (rem > 0) {
+    const int lg = rem >= 4 ? 4 : rem;
+    if (lg == 4) stockham_pass<16, INV>(a, b, N, Ns, tw);
+    else if (lg == 3) stockham_pass<8, INV>(a, b, N, Ns, tw);
+    else if (lg == 2) stockham_pass<4, INV>(a, b, N, Ns, tw);
+    else stockham_pass<2, INV>(a, b, N, Ns, tw);
     __syncthreads();
     float2* t = a;
     a = b;
     b = t;
-    Ns = 2;
-  }
-  for (; Ns < N; Ns *= 4) {
-    radix4_pass<INV>(a, b, N, Ns, tw);
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
+    Ns <<= lg;
+    rem -= lg;
   }
   return a;
 }
@@ -136,17 +204,25 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
     const bool has1 = r1 < a.rows;
     const int64_t z0 = r0 / a.d1, t0 = r0 - z0 * a.d1;
     const int64_t z1 = has1 ? r1 / a.d1 : z0, t1 = has1 ? r1 - z1 * a.d1 : t0;
-    for (int m = threadIdx.x; m < a.npad; m += blockDim.x) {
-      int j = m - a.left;
-      float re = 0.f, im = 0.f;
-      bool inside = true;
-      if (a.pad_zero) inside = j >= 0 && j < a.nd;
-      else j = min(max(j, 0), a.nd - 1);
-      if (inside) {
-        re = load_sample<RAW, TIn>(a, z0, t0, j);
-        im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
+    // real samples
+    for (int j = threadIdx.x; j < a.nd; j += blockDim.x) {
+      const float re = load_sample<RAW, TIn>(a, z0, t0, j);
+      const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
+      bufA[a.left + j] = make_float2(re, im);
+    }
+    // padding: zeros or the edge samples (each thread evaluates the two edges once)
+    {
+      float2 lo = make_float2(0.f, 0.f), hi = lo;
+      const int npadded = a.npad - a.nd;
+      if (!a.pad_zero && (int)threadIdx.x < npadded) {
+        lo = make_float2(load_sample<RAW, TIn>(a, z0, t0, 0), has1 ? load_sample<RAW, TIn>(a, z1, t1, 0) : 0.f);
+        hi = make_float2(load_sample<RAW, TIn>(a, z0, t0, a.nd - 1),
+                         has1 ? load_sample<RAW, TIn>(a, z1, t1, a.nd - 1) : 0.f);
       }
-      bufA[m] = make_float2(re, im);
+      for (int m = threadIdx.x; m < npadded; m += blockDim.x) {
+        if (m < a.left) bufA[m] = lo;
+        else bufA[a.nd + m] = hi;
+      }
     }
     __syncthreads();
     float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, a.tw);
@@ -189,7 +265,7 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
   a.tw = ft.twiddle;
   if (a.rows == 0 || a.nd == 0) return TCP_OK;
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
-  const int threads = std::max(32, std::min(256, a.npad / 8));
+  const int threads = std::max(32, std::min(256, a.npad / 16));
   const size_t smem = 2 * (size_t)a.npad * sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
   int dev = 0;

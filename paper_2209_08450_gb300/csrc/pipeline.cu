@@ -164,7 +164,13 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   FilterTable ft;
   tcp_status s;
   if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
-  if ((s = get_filter_table(nd, o.filter, nt, center, &ft)) != TCP_OK) return s;
+  // The stored sinogram carries the band-limited ramp times storage_scale;
+  // the pi/N_theta FBP weight and 1/storage_scale are applied when the
+  // backprojector writes each voxel (Sec. 2.1: reorder so 16-bit values stay
+  // in range).
+  const double sscale = storage_scale(sdt);
+  if ((s = get_filter_table(nd, o.filter, sscale, center, &ft)) != TCP_OK) return s;
+  const float bp_scale = (float)(M_PI / (double)nt / sscale);
   tcp_bp_config cfg;
   tcp_get_backproject_config(std::min(chunk, nz), nt, nd, n, sdt, vol->dtype, &cfg);
 
@@ -250,7 +256,7 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
       vv.p = (char*)vol->data + z0 * vol->stride[0] * esize(vol->dtype);
       vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
     }
-    TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st));
+    TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st, bp_scale));
     if (host_vol) {
       const int es = esize(vol->dtype);
       TCP_CUDA_TRY(cudaEventRecord(vol_ready[b], st));

@@ -120,8 +120,13 @@ struct FilterTable {
   const float2* twiddle = nullptr;   // npad twiddles exp(-2 pi i m / npad)
   int npad = 0;
 };
-tcp_status get_filter_table(int64_t ndet, int32_t filter, int64_t ntheta, double center,
-                            FilterTable* out);
+// weight multiplies the response (pi/N_theta for FBP; any value > 0).
+tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out);
+
+// Storage scale of a sinogram that the library writes in `dtype` and reads
+// back itself (pipeline, batch): FP16 keeps a 2^10 headroom so that filtered
+// values stay out of the subnormal range (|filtered -log| <= 6.9 < 65504/2^10).
+inline double storage_scale(int dtype) { return dtype == TCP_F16 ? 1024.0 : 1.0; }
 
 int64_t padded_length(int64_t ndet);
 
@@ -140,7 +145,7 @@ tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode,
 tcp_status launch_normalize_filter(const View3& raw, const View3& dark, const View3& flat, const View3& sino,
                                    const FilterTable& ft, int pad_mode, cudaStream_t st);
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                              const tcp_bp_config& cfg, cudaStream_t st);
+                              const tcp_bp_config& cfg, cudaStream_t st, float scale = 1.0f);
 tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
                           cudaStream_t st);
 
@@ -155,6 +160,7 @@ struct BpArgs {
   int ntx;  // tiles along x (and y)
   const double2* trig;
   double center, half_n;
+  float scale;  // multiplies every output voxel (1 for the plain sum)
   uint32_t* err;
 };
 
@@ -166,7 +172,7 @@ struct BpWork {
   unsigned long long* counter;    // zeroed before each launch
 };
 
-BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol);
+BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol, float scale = 1.0f);
 int bp_threads(const tcp_bp_config& c);
 tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks);
 tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, const tcp_bp_config& cfg, int blocks,

@@ -43,10 +43,15 @@ def _datasets(widths, angles, nz, seed0=10, vdt=torch.float32):
     return out
 
 
+def _means(t, z):
+    if t.dim() == 2:  # already FP32 means [nz][ndet]
+        return t[z:z + 1].double().cpu().numpy()
+    return oracle.frame_mean(_host_u16(t[:, z:z + 1]))
+
+
 def _check_sampled(d, z, tol, seed=0):
     raw = _host_u16(d["raw"][:, z:z + 1])
-    dm = oracle.frame_mean(_host_u16(d["dark"][:, z:z + 1]))
-    fm = oracle.frame_mean(_host_u16(d["flat"][:, z:z + 1]))
+    dm, fm = _means(d["dark"], z), _means(d["flat"], z)
     q = oracle.filter_sino(oracle.normalize(raw, dm, fm), d["center"], d.get("filter", "shepp"))[0]
     n = d["vol"].shape[-1]
     rng = np.random.default_rng(seed)

@@ -325,3 +325,21 @@ def test_fbp_pipeline_16bit_and_means():
         out = tcp.fbp(u16(ds.raw), dm, fm, ds.theta, ds.center, dtype=dt, chunk_nz=4)
         torch.cuda.synchronize()
         assert rel(host(out), ref) <= 5e-3
+
+
+def test_fbp_fp16_many_angles_keeps_filtered_values_in_range():
+    # 3000 angles: with pi/N_theta folded into an FP16 sinogram the filtered
+    # values would sit in the FP16 subnormal range; the pipeline stores them
+    # with a 2^10 headroom and applies pi/N_theta/2^10 in the backprojector.
+    import synth.gpu as sgpu
+    raw, dark, flat, theta, c, mu = sgpu.ellipsoid_frames(320, 3000, 4, seed=5, device=DEV, count=12)
+    nr = raw.cpu().numpy().view(np.uint16)
+    ref = oracle.fbp(nr, dark.cpu().numpy().view(np.uint16), flat.cpu().numpy().view(np.uint16), theta, c, "shepp")
+    for dt in (torch.float16, torch.bfloat16):
+        out = tcp.fbp(raw, dark, flat, theta, c, dtype=dt, chunk_nz=3)
+        torch.cuda.synchronize()
+        assert rel(host(out), ref) <= 5e-3
+    # the same through the public calls
+    s = tcp.normalize_filter(raw, dark, flat, c, dtype=torch.float16, weight=1024.0)
+    v = tcp.backproject(s, theta, 320 / 2.0, dtype=torch.float32, scale=np.pi / 3000 / 1024.0)
+    assert rel(host(v), ref) <= 5e-3
