@@ -139,6 +139,21 @@ tcp_status tcp_frame_mean(const tcp_tensor* frames, tcp_tensor* mean, void* stre
 tcp_status tcp_normalize(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
                          tcp_tensor* sino, void* stream);
 
+/* Allocation-free tcp_normalize for U16 dark/flat frames.  The paper has no
+ * counterpart: it is for callers that may not allocate device memory once
+ * they are running, such as an acquisition service that reserved all device
+ * memory for its own pool at start-up, or a framework whose allocator owns
+ * the device.  The frame means live in one fixed 8 MiB array inside the
+ * library (held on every GPU that loads it until exit); nz * ndet may not
+ * exceed 1,048,576 (else TCP_ERR_SHAPE).  No allocation of any kind is made.
+ * All calls on a device share that array: calls that overlap on the GPU race,
+ * so serialise them.  The first call on a device caches the array's device
+ * address; make it before any stream capture.  raw: U16 [ntheta][nz][ndet];
+ * dark, flat: U16 [nf][nz][ndet]; sino: F32/F16/BF16 [nz][ntheta][ndet].
+ * Result equals tcp_normalize with the same frames. */
+tcp_status tcp_normalize_noalloc(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                                 tcp_tensor* sino, void* stream);
+
 /* ---------------------------------------------------------------- filter -- */
 
 /* One-dimensional FBP filter of every detector row, in place (Sec. 2.2).
