@@ -118,12 +118,14 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
-// Stockham pass of radix R: in -> out, sub-transform size Ns.
+// Stockham pass of radix R: in -> out, sub-transform size Ns, by the gs
+// threads of one group (group-local index gt).
 template <int R, bool INV>
-__device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int N, int Ns, const float2* tw) {
+__device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int N, int Ns, const float2* tw,
+                                              int gt, int gs) {
   const int nb = N / R;
   const int step = N / (R * Ns);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+  for (int b = gt; b < nb; b += gs) {
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[b + r * nb];
@@ -145,17 +147,20 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
 
 // Transform the data in `a` (scratch `b`); returns the buffer with the result.
 // Radix-16 passes while 16 divides the remaining length, then one pass of 8,
-// 4 or 2 for the remainder.
+// 4 or 2 for the remainder.  Every thread of the block takes part in the
+// barriers; groups without a row pair (active == false) skip the arithmetic.
 template <bool INV>
-__device__ float2* fft(float2* a, float2* b, int N, int log2N, const float2* tw) {
+__device__ float2* fft(float2* a, float2* b, int N, int log2N, const float2* tw, int gt, int gs, bool active) {
   int Ns = 1;
   int rem = log2N;
   while (rem > 0) {
     const int lg = rem >= 4 ? 4 : rem;
-    if (lg == 4) stockham_pass<16, INV>(a, b, N, Ns, tw);
-    else if (lg == 3) stockham_pass<8, INV>(a, b, N, Ns, tw);
-    else if (lg == 2) stockham_pass<4, INV>(a, b, N, Ns, tw);
-    else stockham_pass<2, INV>(a, b, N, Ns, tw);
+    if (active) {
+      if (lg == 4) stockham_pass<16, INV>(a, b, N, Ns, tw, gt, gs);
+      else if (lg == 3) stockham_pass<8, INV>(a, b, N, Ns, tw, gt, gs);
+      else if (lg == 2) stockham_pass<4, INV>(a, b, N, Ns, tw, gt, gs);
+      else stockham_pass<2, INV>(a, b, N, Ns, tw, gt, gs);
+    }
     __syncthreads();
     float2* t = a;
     a = b;
@@ -178,6 +183,7 @@ struct FiltArgs {
   int d1;           // rows per z (= ntheta)
   int64_t rows;
   int nd, npad, log2n, left;
+  int gs;           // threads per row pair
   int pad_zero;
   const float2* resp;
   const float2* tw;
@@ -193,53 +199,66 @@ __device__ __forceinline__ float load_sample(const FiltArgs& a, int64_t z, int64
   }
 }
 
+// A block of 256 threads works on G = 256/gs row pairs at once, gs threads
+// per pair (gs = npad/16 clamped to [32, 256]): small transforms still fill the
+// block and share its barriers.
 template <bool RAW, class TIn, class TOut>
 __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
   extern __shared__ float2 smem[];
-  float2* bufA = smem;
-  float2* bufB = smem + a.npad;
+  const int gs = a.gs;
+  const int G = blockDim.x / gs;
+  const int g = threadIdx.x / gs, gt = threadIdx.x - g * gs;
+  float2* bufA = smem + (size_t)g * 2 * a.npad;
+  float2* bufB = bufA + a.npad;
   const int64_t npairs = (a.rows + 1) / 2;
-  for (int64_t p = blockIdx.x; p < npairs; p += gridDim.x) {
+  for (int64_t p0 = (int64_t)blockIdx.x * G; p0 < npairs; p0 += (int64_t)gridDim.x * G) {
+    const int64_t p = p0 + g;
+    const bool active = p < npairs;
     const int64_t r0 = 2 * p, r1 = 2 * p + 1;
-    const bool has1 = r1 < a.rows;
+    const bool has1 = active && r1 < a.rows;
     const int64_t z0 = r0 / a.d1, t0 = r0 - z0 * a.d1;
     const int64_t z1 = has1 ? r1 / a.d1 : z0, t1 = has1 ? r1 - z1 * a.d1 : t0;
-    // real samples
-    for (int j = threadIdx.x; j < a.nd; j += blockDim.x) {
-      const float re = load_sample<RAW, TIn>(a, z0, t0, j);
-      const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
-      bufA[a.left + j] = make_float2(re, im);
-    }
-    // padding: zeros or the edge samples (each thread evaluates the two edges once)
-    {
+    if (active) {
+      // real samples (unrolled so that several loads are in flight)
+#pragma unroll 4
+      for (int j = gt; j < a.nd; j += gs) {
+        const float re = load_sample<RAW, TIn>(a, z0, t0, j);
+        const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
+        bufA[a.left + j] = make_float2(re, im);
+      }
+      // padding: zeros or the edge samples (each thread evaluates the edges once)
       float2 lo = make_float2(0.f, 0.f), hi = lo;
       const int npadded = a.npad - a.nd;
-      if (!a.pad_zero && (int)threadIdx.x < npadded) {
+      if (!a.pad_zero && gt < npadded) {
         lo = make_float2(load_sample<RAW, TIn>(a, z0, t0, 0), has1 ? load_sample<RAW, TIn>(a, z1, t1, 0) : 0.f);
         hi = make_float2(load_sample<RAW, TIn>(a, z0, t0, a.nd - 1),
                          has1 ? load_sample<RAW, TIn>(a, z1, t1, a.nd - 1) : 0.f);
       }
-      for (int m = threadIdx.x; m < npadded; m += blockDim.x) {
+      for (int m = gt; m < npadded; m += gs) {
         if (m < a.left) bufA[m] = lo;
         else bufA[a.nd + m] = hi;
       }
     }
     __syncthreads();
-    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, a.tw);
+    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, a.tw, gt, gs, active);
     const int half = a.npad / 2;
-    for (int k = threadIdx.x; k < a.npad; k += blockDim.x) {
-      float2 F = __ldg(a.resp + (k <= half ? k : a.npad - k));
-      if (k > half) F.y = -F.y;
-      x[k] = cmul(x[k], F);
+    if (active) {
+      for (int k = gt; k < a.npad; k += gs) {
+        float2 F = __ldg(a.resp + (k <= half ? k : a.npad - k));
+        if (k > half) F.y = -F.y;
+        x[k] = cmul(x[k], F);
+      }
     }
     __syncthreads();
-    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, a.tw);
-    TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
-    TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
-    for (int j = threadIdx.x; j < a.nd; j += blockDim.x) {
-      const float2 v = y[a.left + j];
-      Store<TOut>::put(o0 + j, v.x);
-      if (has1) Store<TOut>::put(o1 + j, v.y);
+    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, a.tw, gt, gs, active);
+    if (active) {
+      TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
+      TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
+      for (int j = gt; j < a.nd; j += gs) {
+        const float2 v = y[a.left + j];
+        Store<TOut>::put(o0 + j, v.x);
+        if (has1) Store<TOut>::put(o1 + j, v.y);
+      }
     }
     __syncthreads();
   }
@@ -265,8 +284,9 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
   a.tw = ft.twiddle;
   if (a.rows == 0 || a.nd == 0) return TCP_OK;
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
-  const int threads = std::max(32, std::min(256, a.npad / 16));
-  const size_t smem = 2 * (size_t)a.npad * sizeof(float2);
+  a.gs = std::max(32, std::min(256, a.npad / 16));
+  const int threads = 256;
+  const size_t smem = (size_t)(threads / a.gs) * 2 * (size_t)a.npad * sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
@@ -289,7 +309,8 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
     }
     cap = it->second;
   }
-  const int blocks = (int)std::min<int64_t>(npairs, cap);
+  const int G = threads / a.gs;
+  const int blocks = (int)std::min<int64_t>((npairs + G - 1) / G, cap);
   k<<<blocks, threads, smem, st>>>(a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
