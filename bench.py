@@ -196,8 +196,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048)
+    ap.add_argument("--nz", type=int, default=0, help="slices (default: size); a small case of the same launches")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"], help="storage of the headline path")
     ap.add_argument("--chunk", type=int, default=32)
-    ap.add_argument("--variants", default="f16,bf16")
+    ap.add_argument("--variants", default="f32,f16,bf16")
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=4)
@@ -226,10 +228,13 @@ def main():
 
     # ---- input: seeded synthetic dataset, resident in HBM (not timed)
     t_gen = time.perf_counter()
-    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, nt, n, seed=rank, device=dev)
+    nz = args.nz or n
+    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, nt, n, seed=rank, device=dev,
+                                                            slices=np.arange((n - nz) // 2, (n - nz) // 2 + nz))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    nchunks = (n + args.chunk - 1) // args.chunk
+    nchunks = (nz + args.chunk - 1) // args.chunk
+    hdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
 
     def run_steps(dtype, steps, warmup, out):
         stream = torch.cuda.current_stream()
@@ -249,12 +254,12 @@ def main():
         barrier(world, local)
         return reduce_max(e0.elapsed_time(e1) / steps, world, dev)
 
-    # ---- headline: FP32 storage and arithmetic
-    vol = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    # ---- headline: FP32 storage and arithmetic (unless --dtype says otherwise)
+    vol = torch.empty((nz, n, n), dtype=hdt, device=dev)
     with ClockSampler(local) as clk:
-        ms = run_steps(torch.float32, args.steps, args.warmup, vol)
+        ms = run_steps(hdt, args.steps, args.warmup, vol)
     clocks = clk.summary()
-    value = world * n ** 3 / (ms * 1e-3) / 1e9
+    value = world * nz * n * n / (ms * 1e-3) / 1e9
 
     # ---- parity on sampled slices (oracle on the same uint16 frames)
     def parity(v, zs):
@@ -273,14 +278,14 @@ def main():
             errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         return float(max(errs))
 
-    zs = [int(x) for x in np.linspace(n // 5, 4 * n // 5, args.parity_slices)]
-    par = {"f32": parity(vol, zs)} if rank == 0 and zs else {}
+    zs = [int(x) for x in np.linspace(nz // 5, 4 * nz // 5, args.parity_slices)]
+    par = {args.dtype: parity(vol, zs)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
-    s_chunk = torch.empty((args.chunk, nt, n), dtype=torch.float32, device=dev)
+    s_chunk = torch.empty((args.chunk, nt, n), dtype=hdt, device=dev)
     v_chunk = vol[:args.chunk]
     dm, fm = tcp.frame_mean(dark), tcp.frame_mean(flat)
-    z0 = n // 2
+    z0 = max(0, nz // 2 - args.chunk)
     tcp.normalize_filter(raw[:, z0:z0 + args.chunk], dm[z0:z0 + args.chunk], fm[z0:z0 + args.chunk], center,
                          out=s_chunk)
 
@@ -305,17 +310,18 @@ def main():
     except Exception:
         pass
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    bp_peak = sms * 16 * clk_max * 1e6  # FP32: two 128-B shared-memory wavefronts per warp-wide interpolation
-    roofline = {"bound": "alu", "kernel": "k_backproject (LineRec, FP32)", "achieved": interps / (bp_ms * 1e-3) / 1e9,
+    per_clk = 16 if args.dtype == "f32" else 32  # shared-memory wavefronts: 2 (FP32) or 1 (16-bit pair) per 32 interps
+    bp_peak = sms * per_clk * clk_max * 1e6
+    roofline = {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % args.dtype, "achieved": interps / (bp_ms * 1e-3) / 1e9,
                 "peak": bp_peak / 1e9, "unit": "Ginterp/s", "frac": interps / (bp_ms * 1e-3) / bp_peak,
                 "traffic": None, "ms_per_launch": bp_ms, "interps_per_launch": interps,
-                "peak_basis": "shared-memory pipe: %d SMs x 16 interp/clk x %.0f MHz (max SM clock)" % (sms, clk_max)}
+                "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
     hbm = 6767.4
     try:
         hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
         pass
-    nf_bytes = nt * args.chunk * n * 2 + args.chunk * nt * n * 4
+    nf_bytes = nt * args.chunk * n * 2 + args.chunk * nt * n * s_chunk.element_size()
     secondary = {"normalize_filter": {"bound": "hbm", "achieved": nf_bytes / (nf_ms * 1e-3) / 1e9, "peak": hbm,
                                       "unit": "GB/s", "frac": nf_bytes / (nf_ms * 1e-3) / 1e9 / hbm,
                                       "ms_per_launch": nf_ms}}
@@ -323,12 +329,12 @@ def main():
 
     # ---- 16-bit storage variants (FP32 accumulation)
     variants = {}
-    for name in [v for v in args.variants.split(",") if v]:
-        dt = {"f16": torch.float16, "bf16": torch.bfloat16}[name]
-        vv = torch.empty((n, n, n), dtype=dt, device=dev)
+    for name in [v for v in args.variants.split(",") if v and v != args.dtype]:
+        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[name]
+        vv = torch.empty((nz, n, n), dtype=dt, device=dev)
         vms = run_steps(dt, args.variant_steps, 1, vv)
-        variants[name] = {"value": world * n ** 3 / (vms * 1e-3) / 1e9, "ms_per_step": vms,
-                          "speedup_vs_f32": ms / vms}
+        variants[name] = {"value": world * nz * n * n / (vms * 1e-3) / 1e9, "ms_per_step": vms,
+                          "speedup_vs_headline": ms / vms}
         if rank == 0 and zs:
             variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
         del vv
@@ -342,7 +348,7 @@ def main():
         raw_h.copy_(raw)
         dark_h = dark.cpu().pin_memory()
         flat_h = flat.cpu().pin_memory()
-        vol_h = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+        vol_h = torch.empty((nz, n, n), dtype=hdt, pin_memory=True)
         stream = torch.cuda.current_stream()
 
         def e2e_step():
@@ -360,11 +366,11 @@ def main():
         wall = (time.perf_counter() - t0) / args.steps * 1e3
         barrier(world, local)
         ems = reduce_max(max(e0.elapsed_time(e1) / args.steps, wall), world, dev)
-        e2e = {"value": world * n ** 3 / (ems * 1e-3) / 1e9, "unit": "GVoxel/s", "ms_per_step": ems,
+        e2e = {"value": world * nz * n * n / (ems * 1e-3) / 1e9, "unit": "GVoxel/s", "ms_per_step": ems,
                "h2d_bytes_per_step": raw_h.numel() * 2 + dark_h.numel() * 2 + flat_h.numel() * 2,
-               "d2h_bytes_per_step": vol_h.numel() * 4}
+               "d2h_bytes_per_step": vol_h.numel() * vol_h.element_size()}
         if rank == 0 and zs:
-            par["f32_e2e"] = parity(vol_h, zs[:1])
+            par[args.dtype + "_e2e"] = parity(vol_h, zs[:1])
         del raw_h, vol_h
 
     cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 and args.cpu_slices > 0 else None
@@ -373,10 +379,10 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": "GVoxel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": "f32", "data": DATA,
-            "config": {"workload": "%d^3 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
-                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (n, nt, n, n, args.chunk),
-                       "n": n, "ntheta": nt, "chunk_nz": args.chunk,
+            "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": args.dtype, "data": DATA,
+            "config": {"workload": "%dx%d^2 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
+                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, args.chunk),
+                       "n": n, "nz": nz, "ntheta": nt, "chunk_nz": args.chunk,
                        "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw.numel() * 2 / 1e9)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,

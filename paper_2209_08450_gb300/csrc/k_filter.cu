@@ -118,6 +118,10 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
+// Shared-memory index of element i: one pad slot per 16 elements, so that the
+// stride-16 stores of the first radix-16 pass fall in distinct banks.
+__device__ __forceinline__ int pi16(int i) { return i + (i >> 4); }
+
 // Stockham pass of radix R: in -> out, sub-transform size Ns, by the gs
 // threads of one group (group-local index gt).
 template <int R, bool INV>
@@ -128,7 +132,7 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
   for (int b = gt; b < nb; b += gs) {
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[b + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
     const int k = b & (Ns - 1);
     if (Ns > 1) {
 #pragma unroll
@@ -141,7 +145,7 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
     dft<R, INV>(v);
     const int o = (b - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[o + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) out[pi16(o + r * Ns)] = v[r];
   }
 }
 
@@ -208,8 +212,9 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
   const int gs = a.gs;
   const int G = blockDim.x / gs;
   const int g = threadIdx.x / gs, gt = threadIdx.x - g * gs;
-  float2* bufA = smem + (size_t)g * 2 * a.npad;
-  float2* bufB = bufA + a.npad;
+  const int plen = a.npad + a.npad / 16;  // padded buffer length
+  float2* bufA = smem + (size_t)g * 2 * plen;
+  float2* bufB = bufA + plen;
   const int64_t npairs = (a.rows + 1) / 2;
   for (int64_t p0 = (int64_t)blockIdx.x * G; p0 < npairs; p0 += (int64_t)gridDim.x * G) {
     const int64_t p = p0 + g;
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       for (int j = gt; j < a.nd; j += gs) {
         const float re = load_sample<RAW, TIn>(a, z0, t0, j);
         const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
-        bufA[a.left + j] = make_float2(re, im);
+        bufA[pi16(a.left + j)] = make_float2(re, im);
       }
       // padding: zeros or the edge samples (each thread evaluates the edges once)
       float2 lo = make_float2(0.f, 0.f), hi = lo;
@@ -235,8 +240,8 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
                          has1 ? load_sample<RAW, TIn>(a, z1, t1, a.nd - 1) : 0.f);
       }
       for (int m = gt; m < npadded; m += gs) {
-        if (m < a.left) bufA[m] = lo;
-        else bufA[a.nd + m] = hi;
+        if (m < a.left) bufA[pi16(m)] = lo;
+        else bufA[pi16(a.nd + m)] = hi;
       }
     }
     __syncthreads();
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       for (int k = gt; k < a.npad; k += gs) {
         float2 F = __ldg(a.resp + (k <= half ? k : a.npad - k));
         if (k > half) F.y = -F.y;
-        x[k] = cmul(x[k], F);
+        x[pi16(k)] = cmul(x[pi16(k)], F);
       }
     }
     __syncthreads();
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
       TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
       for (int j = gt; j < a.nd; j += gs) {
-        const float2 v = y[a.left + j];
+        const float2 v = y[pi16(a.left + j)];
         Store<TOut>::put(o0 + j, v.x);
         if (has1) Store<TOut>::put(o1 + j, v.y);
       }
@@ -286,7 +291,7 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
   a.gs = std::max(32, std::min(256, a.npad / 16));
   const int threads = 256;
-  const size_t smem = (size_t)(threads / a.gs) * 2 * (size_t)a.npad * sizeof(float2);
+  const size_t smem = (size_t)(threads / a.gs) * 2 * (size_t)(a.npad + a.npad / 16) * sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
@@ -301,7 +306,8 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
     auto key = std::make_tuple(dev, reinterpret_cast<void*>(k), a.npad);
     auto it = grid_cache.find(key);
     if (it == grid_cache.end()) {
-      TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * 8192 * sizeof(float2))));
+      TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(2 * (8192 + 512) * sizeof(float2))));
       int per_sm = 1, sms = 0;
       TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
       TCP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
