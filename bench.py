@@ -187,6 +187,92 @@ def run_reference(args):
     }), flush=True)
 
 
+# ------------------------------------------------------- other hot-path rows --
+
+def measure_rows(dev) -> dict:
+    """Differentiable least-squares pair (512 x 512 x 64, 720 angles, 512-pixel
+    detector) and the uneven batch (6 stacks, one persistent graph replay)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import synth.gpu as sgpu
+    import paper_2209_08450_gb300 as tcp
+    from paper_2209_08450_gb300 import autograd as ag
+    from paper_2209_08450_gb300.batch import Batch
+
+    def ev_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    # a7: gradient descent on ||P x - y||^2 through the autograd pair
+    n, nz, nt = 512, 64, 720
+    theta = synth.uniform_theta(nt)
+    ells = synth.random_ellipsoids(np.random.default_rng(4), 64, n, float(nz))
+    x_true = sgpu.rasterize_ellipsoids(ells, n, np.arange(nz) + 0.5 - nz / 2.0, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    y = tcp.project(x_true, theta, n / 2.0, ndet=n)
+    y = y + 1e-2 * torch.randn(y.shape, generator=g, device=dev)
+    losses = []
+    t0 = time.perf_counter()
+    ag.lsq_gradient_descent(y, theta, n / 2.0, n, iters=50, callback=lambda i, l: losses.append(l))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    x = torch.zeros_like(x_true)
+    pj = ev_time(lambda: tcp.project(x_true, theta, n / 2.0, out=y), 3)
+    bj = ev_time(lambda: tcp.backproject(y, theta, n / 2.0, out=x), 3)
+    interps = nz * n * n * nt
+    out["a7_least_squares"] = {
+        "workload": "512x512x64 ellipsoids, 720 angles, 512-pixel detector, sigma 1e-2, 50 GD iterations",
+        "seconds_50_iterations": wall, "loss_ratio_50": losses[-1] / losses[0],
+        "project_ms": pj, "backproject_ms": bj, "project_ginterp_s": interps / pj / 1e6,
+        "backproject_ginterp_s": interps / bj / 1e6}
+    del x_true, y, x
+    # a8: six uneven stacks, FP16 storage, one graph replay
+    widths = (512, 768, 1024, 1536, 2048, 2560)
+    angles = (400, 900, 1200, 1800, 2048, 3000)
+    ds = []
+    for i, (w, a) in enumerate(zip(widths, angles)):
+        raw, dark, flat, th, c, mu = sgpu.ellipsoid_frames(w, a, 32, seed=10 + i, device=dev, count=24)
+        ds.append(dict(raw=raw, dark=dark, flat=flat, theta=th, center=c,
+                       vol=torch.empty((32, w, w), dtype=torch.float32, device=dev)))
+    b = Batch(ds, sino_dtype=torch.float16, autotune=True)
+    st = torch.cuda.Stream()
+    b.capture(st)
+    torch.cuda.synchronize()
+
+    def replay():
+        b.replay(st)
+    replay()
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(3):
+        replay()
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    vox = sum(32 * w * w for w in widths)
+    interps = sum(32 * w * w * a for w, a in zip(widths, angles))
+    info = b.info()
+    out["a8_uneven_batch"] = {
+        "workload": "6 stacks x 32 slices, widths 512-2560, 400-3000 angles, FP16 sinograms, one graph replay",
+        "ms_per_replay": ms, "gvoxel_s": vox / ms / 1e6, "ginterp_s": interps / ms / 1e6,
+        "config": info["config"], "tuned_ms": info["tuned_ms"], "grid_blocks": info["grid_blocks"],
+        "work_units": info["work_units"]}
+    b.close()
+    return out
+
+
 # ------------------------------------------------------------- GPU leg --
 
 def main():
@@ -205,6 +291,7 @@ def main():
     ap.add_argument("--cpu-slices", type=int, default=4)
     ap.add_argument("--ref-slices", type=int, default=1)
     ap.add_argument("--parity-slices", type=int, default=2)
+    ap.add_argument("--no-rows", action="store_true", help="skip the least-squares and batch rows")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -234,6 +321,7 @@ def main():
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     nchunks = (nz + args.chunk - 1) // args.chunk
+    raw_bytes = raw.numel() * 2
     hdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
 
     def run_steps(dtype, steps, warmup, out):
@@ -373,6 +461,11 @@ def main():
             par[args.dtype + "_e2e"] = parity(vol_h, zs[:1])
         del raw_h, vol_h
 
+    rows = None
+    if not args.no_rows and world == 1:
+        del raw, dark, flat
+        torch.cuda.empty_cache()
+        rows = measure_rows(dev)
     cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 and args.cpu_slices > 0 else None
     if rank == 0:
         launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
@@ -383,11 +476,11 @@ def main():
             "config": {"workload": "%dx%d^2 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
                                    "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, args.chunk),
                        "n": n, "nz": nz, "ntheta": nt, "chunk_nz": args.chunk,
-                       "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw.numel() * 2 / 1e9)},
+                       "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f16": 5e-3, "bf16": 5e-3},
-            "variants": variants, "input_generation_s": t_gen,
+            "variants": variants, "rows": rows, "input_generation_s": t_gen,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -21,6 +21,9 @@
 //     16-bit weights (Sec. 2.1: 16-bit storage, wider accumulation).
 //   * Lanes of a warp are adjacent voxels in x, so their window indices are
 //     consecutive or equal: every shared load is one conflict-free wavefront.
+#include <mutex>
+#include <set>
+
 #include "tcp_internal.cuh"
 
 namespace tcp {
@@ -90,28 +93,92 @@ template <> struct Interp<__nv_bfloat16> {
   }
 };
 
+// ------------------------------------------------------- shared layouts --
+//
+// FP32 sinograms: two stage buffers win[2][T][K][WIN] (floats), filled with
+//   4-byte cp.async (zero-filled outside the detector) one stage ahead of the
+//   compute, so the global-load latency overlaps the interpolation loop.
+// 16-bit sinograms, K >= 2: win[T][WIN][K] with the K slices of one detector
+//   sample adjacent (K * 2 bytes), so that one vector load fetches sample i of
+//   every slice and a second one sample i + 1; two slices are accumulated per
+//   packed fma.rn.f32x2.
+// 16-bit sinograms, K == 1: win[T][K][WIN] of (q[i], q[i+1]) pairs.
+
 template <class TS, int K, int T>
-struct BpSmem {
-  Geo geo[T];
-  int wst[T];
-  typename Win<TS>::type win[T * K * kWin];
+struct BpLayout {
+  static constexpr bool kF32 = std::is_same<TS, float>::value;
+  static constexpr bool kInter = !kF32 && K >= 2;
+  static constexpr int kStages = kF32 ? 2 : 1;
+  static constexpr int kWinWords = kInter ? T * kWin * K / 2 : T * K * kWin;  // 4-byte words per stage
+  static constexpr size_t kGeoBytes = sizeof(Geo) * T * kStages;
+  static constexpr size_t kWstBytes = sizeof(int) * T * kStages;
+  static constexpr size_t kBytes = kGeoBytes + kWstBytes + 4ull * kWinWords * kStages;
 };
 
-// One work unit: the aligned 32x32 voxel tile (gx, gy) times slices
-// [z0, z0 + K), summed over every angle.  Ends with a block barrier, so the
-// shared buffers may be reused by the next unit.
-template <class TS, class TV, int K, int T, int R, bool CHECK>
-__device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0, BpSmem<TS, K, T>& sm) {
-  using WT = typename Win<TS>::type;
-  using I = Interp<TS>;
-  constexpr int NW = 32 / R;  // warps per block (rows per pass)
-  constexpr int NT = 32 * NW;
-  Geo* geo = sm.geo;
-  int* wst = sm.wst;
-  WT* win = sm.win;
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Geometry of angle t0 + t for the tile: window start and in-tile constants.
+__device__ __forceinline__ void tile_geometry(const BpArgs& a, int gx, int gy, int th, Geo* geo, int* wst) {
+  const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
+  // Lowest reachable index over the tile, one sample of rounding margin.
+  const float lo = o.f0 + fminf(0.f, 31.f * o.c) + fminf(0.f, 31.f * o.s);
+  const int ws = o.i0 + (int)floorf(lo) - 1;
+  *geo = Geo{o.i0 - ws, o.f0, o.c, o.s};
+  *wst = ws;
+}
+
+template <bool CHECK>
+__device__ __forceinline__ int window_index(const BpArgs& a, const Geo& g, float fdx, float fdy, float* w) {
+  const float s = rel_coord(g.f0, g.c, g.s, fdx, fdy);
+  const float fl = floorf(s);
+  *w = s - fl;
+  int idx = (int)fl + g.base;
+  if (CHECK) {
+    if (idx < 0 || idx > kWin - 2) {
+      atomicOr(a.err, kErrBpWindow);
+      idx = 0;
+    }
+  }
+  return idx;
+}
+
+template <class TV, int K, int R>
+__device__ __forceinline__ void store_tile(const BpArgs& a, int gx, int gy, int z0, const float (&acc)[R][K]) {
+  constexpr int NW = 32 / R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TS* sino = reinterpret_cast<const TS*>(a.sino);
+  TV* vol = reinterpret_cast<TV*>(a.vol);
+  const int ix = gx * kTile + lane;
+  if (ix >= a.n) return;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int iy = gy * kTile + warp + NW * r;
+    if (iy >= a.n) continue;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int z = z0 + k;
+      if (z < a.nz) Store<TV>::put(vol + (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix, acc[r][k] * a.scale);
+    }
+  }
+}
+
+// --- FP32: double-buffered cp.async staging -------------------------------
+template <class TV, int K, int T, int R, bool CHECK>
+__device__ __forceinline__ void bp_tile_f32(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
+  using L = BpLayout<float, K, T>;
+  constexpr int NW = 32 / R, NT = 32 * NW;
+  Geo* geo = reinterpret_cast<Geo*>(smem);
+  int* wst = reinterpret_cast<int*>(smem + L::kGeoBytes);
+  float* win = reinterpret_cast<float*>(smem + L::kGeoBytes + L::kWstBytes);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* sino = reinterpret_cast<const float*>(a.sino);
+  const int nstages = (a.ntheta + T - 1) / T;
 
   float acc[R][K];
 #pragma unroll
@@ -119,77 +186,239 @@ __device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0,
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
 
-  const float fdx = (float)lane;
+  auto issue = [&](int s) {  // copy the windows of stage s into buffer s & 1
+    const int b = s & 1, t0 = s * T, nt = min(T, a.ntheta - t0);
+    float* wb = win + b * (T * K * kWin);
+    const int* ws = wst + b * T;
+    for (int e = threadIdx.x; e < nt * K * kWin; e += NT) {
+      const int t = e / (K * kWin);
+      const int rem = e - t * (K * kWin);
+      const int k = rem / kWin;
+      const int i = rem - k * kWin;
+      const int z = z0 + k, j = ws[t] + i;
+      const bool ok = z < a.nz && j >= 0 && j < a.ndet;
+      const float* src = ok ? sino + (int64_t)z * a.s_z + (int64_t)(t0 + t) * a.s_t + j : sino;
+      cp_async4(wb + e, src, ok);
+    }
+    cp_async_commit();
+  };
+
+  if (threadIdx.x < min(T, a.ntheta)) tile_geometry(a, gx, gy, threadIdx.x, geo + threadIdx.x, wst + threadIdx.x);
+  __syncthreads();
+  issue(0);
+  for (int s = 0; s < nstages; ++s) {
+    const int b = s & 1;
+    if (s + 1 < nstages) {
+      const int t1 = (s + 1) * T;
+      const int bn = (s + 1) & 1;
+      if ((int)threadIdx.x < min(T, a.ntheta - t1))
+        tile_geometry(a, gx, gy, t1 + threadIdx.x, geo + bn * T + threadIdx.x, wst + bn * T + threadIdx.x);
+    }
+    __syncthreads();  // next geometry ready; buffer (s+1)&1 no longer read
+    if (s + 1 < nstages) {
+      issue(s + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // stage s landed for every thread
+    const int nt = min(T, a.ntheta - s * T);
+    const float* wbase = win + b * (T * K * kWin);
+    for (int t = 0; t < nt; ++t) {
+      const Geo g = geo[b * T + t];
+      const float* wb = wbase + t * (K * kWin);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float w;
+        const int idx = window_index<CHECK>(a, g, (float)lane, (float)(warp + NW * r), &w);
+        const float w0 = 1.f - w;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          acc[r][k] = __fmaf_rn(w0, wb[k * kWin + idx], acc[r][k]);
+          acc[r][k] = __fmaf_rn(w, wb[k * kWin + idx + 1], acc[r][k]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  store_tile<TV, K, R>(a, gx, gy, z0, acc);
+}
+
+// --- 16-bit, K >= 2: slice-interleaved window, packed FP32x2 FMAs ---------
+template <class TS> __device__ __forceinline__ float2 unpack2(uint32_t v);
+template <> __device__ __forceinline__ float2 unpack2<__half>(uint32_t v) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+template <> __device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t v) {
+  return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+
+__device__ __forceinline__ unsigned long long pack2(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long w, unsigned long long x) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(x));
+}
+
+template <int K>
+__device__ __forceinline__ void load_words(const uint32_t* p, uint32_t (&v)[K / 2]) {
+  if constexpr (K == 2) {
+    v[0] = p[0];
+  } else if constexpr (K == 4) {
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < K / 8; ++c) {
+      const uint4 q = *reinterpret_cast<const uint4*>(p + 4 * c);
+      v[4 * c] = q.x;
+      v[4 * c + 1] = q.y;
+      v[4 * c + 2] = q.z;
+      v[4 * c + 3] = q.w;
+    }
+  }
+}
+
+template <class TS, class TV, int K, int T, int R, bool CHECK>
+__device__ __forceinline__ void bp_tile_16i(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
+  using L = BpLayout<TS, K, T>;
+  constexpr int NW = 32 / R, NT = 32 * NW, KW = K / 2;  // words per detector sample
+  Geo* geo = reinterpret_cast<Geo*>(smem);
+  int* wst = reinterpret_cast<int*>(smem + L::kGeoBytes);
+  uint32_t* win = reinterpret_cast<uint32_t*>(smem + L::kGeoBytes + L::kWstBytes);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned short* sino = reinterpret_cast<const unsigned short*>(a.sino);
+
+  unsigned long long acc[R][KW];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < KW; ++c) acc[r][c] = 0ull;
 
   for (int t0 = 0; t0 < a.ntheta; t0 += T) {
     const int nt = min(T, a.ntheta - t0);
-    if (threadIdx.x < nt) {
-      const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[t0 + threadIdx.x]);
-      // Lowest reachable index over the tile, one sample of rounding margin.
-      const float lo = o.f0 + fminf(0.f, 31.f * o.c) + fminf(0.f, 31.f * o.s);
-      const int ws = o.i0 + (int)floorf(lo) - 1;
-      geo[threadIdx.x] = Geo{o.i0 - ws, o.f0, o.c, o.s};
-      wst[threadIdx.x] = ws;
+    if ((int)threadIdx.x < nt) tile_geometry(a, gx, gy, t0 + threadIdx.x, geo + threadIdx.x, wst + threadIdx.x);
+    __syncthreads();
+    // word e = ((t * WIN) + i) * KW + kp holds slices (2kp, 2kp + 1) of sample
+    // i: consecutive threads write consecutive words (no bank conflicts).
+    for (int e = threadIdx.x; e < nt * kWin * KW; e += NT) {
+      const int t = e / (kWin * KW);
+      const int rem = e - t * (kWin * KW);
+      const int i = rem / KW;
+      const int kp = rem - i * KW;
+      const int z = z0 + 2 * kp, j = wst[t] + i;
+      uint32_t v = 0;
+      if (j >= 0 && j < a.ndet) {
+        const int64_t off = (int64_t)(t0 + t) * a.s_t + j;
+        const uint32_t lo = z < a.nz ? __ldg(sino + (int64_t)z * a.s_z + off) : 0u;
+        const uint32_t hi = z + 1 < a.nz ? __ldg(sino + (int64_t)(z + 1) * a.s_z + off) : 0u;
+        v = lo | (hi << 16);
+      }
+      win[e] = v;
     }
     __syncthreads();
-    // Stage the windows: element e = (t, k, i), i fastest -> coalesced rows.
+    for (int t = 0; t < nt; ++t) {
+      const Geo g = geo[t];
+      const uint32_t* wb = win + t * (kWin * KW);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float w;
+        const int idx = window_index<CHECK>(a, g, (float)lane, (float)(warp + NW * r), &w);
+        uint32_t q0[KW], q1[KW];
+        load_words<K>(wb + idx * KW, q0);
+        load_words<K>(wb + (idx + 1) * KW, q1);
+        const unsigned long long w0 = pack2(1.f - w, 1.f - w), w1 = pack2(w, w);
+#pragma unroll
+        for (int c = 0; c < KW; ++c) {
+          const float2 x0 = unpack2<TS>(q0[c]), x1 = unpack2<TS>(q1[c]);
+          ffma2(acc[r][c], w0, pack2(x0.x, x0.y));
+          ffma2(acc[r][c], w1, pack2(x1.x, x1.y));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  float out[R][K];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < KW; ++c) {
+      float x, y;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(acc[r][c]));
+      out[r][2 * c] = x;
+      out[r][2 * c + 1] = y;
+    }
+  store_tile<TV, K, R>(a, gx, gy, z0, out);
+}
+
+// --- 16-bit, K == 1: (q[i], q[i+1]) pairs, mixed-precision FMAs -----------
+template <class TS, class TV, int K, int T, int R, bool CHECK>
+__device__ __forceinline__ void bp_tile_pairs(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
+  using L = BpLayout<TS, K, T>;
+  using I = Interp<TS>;
+  constexpr int NW = 32 / R, NT = 32 * NW;
+  Geo* geo = reinterpret_cast<Geo*>(smem);
+  int* wst = reinterpret_cast<int*>(smem + L::kGeoBytes);
+  uint32_t* win = reinterpret_cast<uint32_t*>(smem + L::kGeoBytes + L::kWstBytes);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const TS* sino = reinterpret_cast<const TS*>(a.sino);
+  float acc[R][K];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
+  for (int t0 = 0; t0 < a.ntheta; t0 += T) {
+    const int nt = min(T, a.ntheta - t0);
+    if ((int)threadIdx.x < nt) tile_geometry(a, gx, gy, t0 + threadIdx.x, geo + threadIdx.x, wst + threadIdx.x);
+    __syncthreads();
     for (int e = threadIdx.x; e < nt * K * kWin; e += NT) {
       const int t = e / (K * kWin);
       const int rem = e - t * (K * kWin);
       const int k = rem / kWin;
       const int i = rem - k * kWin;
       const int z = z0 + k;
-      WT v = WT(0);
-      if (z < a.nz) {
-        const TS* row = sino + (int64_t)z * a.s_z + (int64_t)(t0 + t) * a.s_t;
-        v = I::stage(row, wst[t] + i, a.ndet);
-      }
+      uint32_t v = 0;
+      if (z < a.nz) v = I::stage(sino + (int64_t)z * a.s_z + (int64_t)(t0 + t) * a.s_t, wst[t] + i, a.ndet);
       win[e] = v;
     }
     __syncthreads();
-
     for (int t = 0; t < nt; ++t) {
       const Geo g = geo[t];
-      const WT* wb = win + t * (K * kWin);
+      const uint32_t* wb = win + t * (K * kWin);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float s = rel_coord(g.f0, g.c, g.s, fdx, (float)(warp + NW * r));
-        const float fl = floorf(s);
-        const typename I::W w = I::weights(s - fl);
-        int idx = (int)fl + g.base;
-        if (CHECK) {
-          if (idx < 0 || idx > kWin - 2) {
-            atomicOr(a.err, kErrBpWindow);
-            idx = 0;
-          }
-        }
+        float w;
+        const int idx = window_index<CHECK>(a, g, (float)lane, (float)(warp + NW * r), &w);
+        const typename I::W wt = I::weights(w);
 #pragma unroll
-        for (int k = 0; k < K; ++k) I::acc(acc[r][k], wb, k * kWin + idx, w);
+        for (int k = 0; k < K; ++k) I::acc(acc[r][k], wb, k * kWin + idx, wt);
       }
     }
     __syncthreads();
   }
-
-  TV* vol = reinterpret_cast<TV*>(a.vol);
-  const int ix = gx * kTile + lane;
-  if (ix < a.n) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int iy = gy * kTile + warp + NW * r;
-      if (iy >= a.n) continue;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int z = z0 + k;
-        if (z < a.nz) Store<TV>::put(vol + (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix, acc[r][k] * a.scale);
-      }
-    }
-  }
+  store_tile<TV, K, R>(a, gx, gy, z0, acc);
 }
+
+// One work unit: the aligned 32x32 voxel tile (gx, gy) times slices
+// [z0, z0 + K), summed over every angle.  Ends with a block barrier, so the
+// shared buffers may be reused by the next unit.
+template <class TS, class TV, int K, int T, int R, bool CHECK>
+__device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
+  using L = BpLayout<TS, K, T>;
+  if constexpr (L::kF32) bp_tile_f32<TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
+  else if constexpr (L::kInter) bp_tile_16i<TS, TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
+  else bp_tile_pairs<TS, TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
+  __syncthreads();
+}
+
+extern __shared__ __align__(16) unsigned char bp_smem[];
 
 template <class TS, class TV, int K, int T, int R, bool CHECK>
 __global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
-  __shared__ BpSmem<TS, K, T> sm;
-  bp_tile<TS, TV, K, T, R, CHECK>(a, blockIdx.x % a.ntx, blockIdx.x / a.ntx, blockIdx.y * K, sm);
+  bp_tile<TS, TV, K, T, R, CHECK>(a, blockIdx.x % a.ntx, blockIdx.x / a.ntx, blockIdx.y * K, bp_smem);
 }
 
 // Persistent form for batches of datasets with uneven widths and angle
@@ -200,7 +429,6 @@ __global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
 // state), so every launch completes regardless of scheduling.
 template <class TS, class TV, int K, int T, int R, bool CHECK>
 __global__ void __launch_bounds__(32 * (32 / R)) k_backproject_persistent(BpWork w) {
-  __shared__ BpSmem<TS, K, T> sm;
   __shared__ long long s_unit;
   __shared__ int s_item;
   __shared__ BpArgs s_args;
@@ -224,7 +452,7 @@ __global__ void __launch_bounds__(32 * (32 / R)) k_backproject_persistent(BpWork
     const long long tiles = (long long)s_args.ntx * s_args.ntx;
     const int zb = (int)(local / tiles);
     const int tile = (int)(local - (long long)zb * tiles);
-    bp_tile<TS, TV, K, T, R, CHECK>(s_args, tile % s_args.ntx, tile / s_args.ntx, zb * K, sm);
+    bp_tile<TS, TV, K, T, R, CHECK>(s_args, tile % s_args.ntx, tile / s_args.ntx, zb * K, bp_smem);
   }
 }
 
@@ -234,12 +462,26 @@ using PKern = void (*)(BpWork);
 struct KernPair {
   Kern direct;
   PKern persistent;
+  size_t smem;  // dynamic shared memory per block
 };
 
 template <class TS, class TV, int K, int T, int R>
 KernPair pick_check(bool check) {
-  if (check) return {k_backproject<TS, TV, K, T, R, true>, k_backproject_persistent<TS, TV, K, T, R, true>};
-  return {k_backproject<TS, TV, K, T, R, false>, k_backproject_persistent<TS, TV, K, T, R, false>};
+  const size_t sm = BpLayout<TS, K, T>::kBytes;
+  if (check) return {k_backproject<TS, TV, K, T, R, true>, k_backproject_persistent<TS, TV, K, T, R, true>, sm};
+  return {k_backproject<TS, TV, K, T, R, false>, k_backproject_persistent<TS, TV, K, T, R, false>, sm};
+}
+
+// Opt every kernel of a pair in to its dynamic shared memory once.
+tcp_status prepare(const KernPair& kp) {
+  static std::mutex mu;
+  static std::set<const void*> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(reinterpret_cast<const void*>(kp.direct))) return TCP_OK;
+  TCP_CUDA_TRY(cudaFuncSetAttribute(kp.direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem));
+  TCP_CUDA_TRY(cudaFuncSetAttribute(kp.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem));
+  done.insert(reinterpret_cast<const void*>(kp.direct));
+  return TCP_OK;
 }
 
 // Instantiated configurations (k_slices, theta_stage, rows_per_thread).
@@ -255,7 +497,7 @@ KernPair pick(const tcp_bp_config& c, bool check) {
   TCP_BP_CASE(2, 16, 4)
   TCP_BP_CASE(1, 32, 4)
 #undef TCP_BP_CASE
-  return {nullptr, nullptr};
+  return {nullptr, nullptr, 0};
 }
 
 template <class TS>
@@ -265,7 +507,7 @@ KernPair pick_vol(int vdt, const tcp_bp_config& c, bool check) {
     case TCP_F16: return pick<TS, __half>(c, check);
     case TCP_BF16: return pick<TS, __nv_bfloat16>(c, check);
   }
-  return {nullptr, nullptr};
+  return {nullptr, nullptr, 0};
 }
 
 KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
@@ -274,7 +516,7 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
     case TCP_F16: return pick_vol<__half>(vdt, c, check);
     case TCP_BF16: return pick_vol<__nv_bfloat16>(vdt, c, check);
   }
-  return {nullptr, nullptr};
+  return {nullptr, nullptr, 0};
 }
 
 }  // namespace
@@ -288,8 +530,10 @@ int bp_threads(const tcp_bp_config& c) { return 32 * (32 / c.rows_per_thread); }
 tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks) {
   KernPair kp = pick_all(sdt, vdt, cfg, checked_mode());
   if (!kp.persistent) return fail(TCP_ERR_UNSUPPORTED, "backproject: no persistent kernel for this dtype/config");
+  tcp_status s = prepare(kp);
+  if (s != TCP_OK) return s;
   int per_sm = 0, dev = 0, sms = 0;
-  TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp.persistent, bp_threads(cfg), 0));
+  TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kp.persistent, bp_threads(cfg), kp.smem));
   TCP_CUDA_TRY(cudaGetDevice(&dev));
   TCP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   *blocks = std::max(1, per_sm) * sms;
@@ -300,7 +544,9 @@ tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, cons
                                          cudaStream_t st) {
   KernPair kp = pick_all(sdt, vdt, cfg, checked_mode());
   if (!kp.persistent) return fail(TCP_ERR_UNSUPPORTED, "backproject: no persistent kernel for this dtype/config");
-  kp.persistent<<<blocks, bp_threads(cfg), 0, st>>>(w);
+  tcp_status s = prepare(kp);
+  if (s != TCP_OK) return s;
+  kp.persistent<<<blocks, bp_threads(cfg), kp.smem, st>>>(w);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
 }
@@ -316,14 +562,17 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st, float scale) {
-  Kern k = pick_all(sino.dtype, vol.dtype, cfg, checked_mode()).direct;
+  const KernPair kp = pick_all(sino.dtype, vol.dtype, cfg, checked_mode());
+  Kern k = kp.direct;
   if (!k) return fail(TCP_ERR_UNSUPPORTED, "backproject: no kernel for this dtype/config");
+  tcp_status ps = prepare(kp);
+  if (ps != TCP_OK) return ps;
   if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
   BpArgs a = make_bp_args(sino, trig, center, vol, scale);
   const int threads = bp_threads(cfg);
   dim3 grid((unsigned)(a.ntx * a.ntx), (unsigned)((a.nz + cfg.k_slices - 1) / cfg.k_slices));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject: too many slice blocks");
-  k<<<grid, threads, 0, st>>>(a);
+  k<<<grid, threads, kp.smem, st>>>(a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
 }
