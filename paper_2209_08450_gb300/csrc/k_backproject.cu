@@ -109,9 +109,12 @@ struct BpLayout {
   static constexpr bool kF32 = std::is_same<TS, float>::value;
   static constexpr bool kInter = !kF32 && K >= 2;
   static constexpr int kStages = kF32 ? 2 : 1;
+  // Geometry ring: FP32 writes the geometry of stage s+1 before the barrier
+  // that ends stage s-1, so it needs three slots (s-1, s, s+1).
+  static constexpr int kGeoSlots = kF32 ? 3 : 1;
   static constexpr int kWinWords = kInter ? T * kWin * K / 2 : T * K * kWin;  // 4-byte words per stage
-  static constexpr size_t kGeoBytes = sizeof(Geo) * T * kStages;
-  static constexpr size_t kWstBytes = sizeof(int) * T * kStages;
+  static constexpr size_t kGeoBytes = sizeof(Geo) * T * kGeoSlots;
+  static constexpr size_t kWstBytes = sizeof(int) * T * kGeoSlots;
   static constexpr size_t kBytes = kGeoBytes + kWstBytes + 4ull * kWinWords * kStages;
 };
 
@@ -189,7 +192,7 @@ __device__ __forceinline__ void bp_tile_f32(const BpArgs& a, int gx, int gy, int
   auto issue = [&](int s) {  // copy the windows of stage s into buffer s & 1
     const int b = s & 1, t0 = s * T, nt = min(T, a.ntheta - t0);
     float* wb = win + b * (T * K * kWin);
-    const int* ws = wst + b * T;
+    const int* ws = wst + (s % 3) * T;
     for (int e = threadIdx.x; e < nt * K * kWin; e += NT) {
       const int t = e / (K * kWin);
       const int rem = e - t * (K * kWin);
@@ -209,12 +212,14 @@ __device__ __forceinline__ void bp_tile_f32(const BpArgs& a, int gx, int gy, int
   for (int s = 0; s < nstages; ++s) {
     const int b = s & 1;
     if (s + 1 < nstages) {
+      // slot (s+1)%3 was last read by stage s-2, which every thread finished
+      // before the previous iteration's barriers
       const int t1 = (s + 1) * T;
-      const int bn = (s + 1) & 1;
+      const int gn = (s + 1) % 3;
       if ((int)threadIdx.x < min(T, a.ntheta - t1))
-        tile_geometry(a, gx, gy, t1 + threadIdx.x, geo + bn * T + threadIdx.x, wst + bn * T + threadIdx.x);
+        tile_geometry(a, gx, gy, t1 + threadIdx.x, geo + gn * T + threadIdx.x, wst + gn * T + threadIdx.x);
     }
-    __syncthreads();  // next geometry ready; buffer (s+1)&1 no longer read
+    __syncthreads();  // next geometry ready; window buffer (s+1)&1 no longer read
     if (s + 1 < nstages) {
       issue(s + 1);
       cp_async_wait<1>();
@@ -225,7 +230,7 @@ __device__ __forceinline__ void bp_tile_f32(const BpArgs& a, int gx, int gy, int
     const int nt = min(T, a.ntheta - s * T);
     const float* wbase = win + b * (T * K * kWin);
     for (int t = 0; t < nt; ++t) {
-      const Geo g = geo[b * T + t];
+      const Geo g = geo[(s % 3) * T + t];
       const float* wb = wbase + t * (K * kWin);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
