@@ -228,12 +228,16 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
 
 /* Backprojector launch configuration.  k_slices: slices per thread block
  * (1, 2, 4, 8 or 16); theta_stage: angles staged in shared memory per step
- * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4). */
+ * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4).
+ * kernel: 0 = FP32 pipes (every dtype); 1 = tensor cores (tcgen05.mma with
+ * TMEM accumulators, FP16/BF16 sinograms whose row and slice strides are
+ * multiples of 8 elements; other inputs fall back to kernel 0, and the
+ * other fields are ignored). */
 typedef struct {
   int32_t k_slices;
   int32_t theta_stage;
   int32_t rows_per_thread;
-  int32_t reserved;
+  int32_t kernel;
 } tcp_bp_config;
 
 /* Fix the backprojector configuration for later calls (NULL: automatic). */

@@ -139,11 +139,14 @@ def cache_clear() -> None:
     _lib.call("tcp_cache_clear")
 
 
-def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, rows_per_thread: int = 4) -> None:
+def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, rows_per_thread: int = 4,
+                           kernel: int = 0) -> None:
+    """Fix the backprojector configuration (None: automatic).  kernel=1 selects
+    the tensor-core backprojector for FP16/BF16 sinograms."""
     if k_slices is None:
         _lib.load().tcp_set_backproject_config(None)
         return
-    c = _lib.BpConfig(k_slices, theta_stage, rows_per_thread, 0)
+    c = _lib.BpConfig(k_slices, theta_stage, rows_per_thread, kernel)
     _lib.call("tcp_set_backproject_config", ctypes.byref(c))
 
 
@@ -151,7 +154,7 @@ def get_backproject_config(nz, ntheta, ndet, n, sino_dtype=torch.float32, vol_dt
     c = _lib.BpConfig()
     _lib.call("tcp_get_backproject_config", nz, ntheta, ndet, n, _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype]],
               _lib._TORCH_DTYPE[_lib.DTYPES[vol_dtype]], ctypes.byref(c))
-    return (c.k_slices, c.theta_stage, c.rows_per_thread)
+    return (c.k_slices, c.theta_stage, c.rows_per_thread, c.kernel)
 
 
 def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center: float,

@@ -42,7 +42,7 @@ class TcpTensor(ctypes.Structure):
 
 class BpConfig(ctypes.Structure):
     _fields_ = [("k_slices", ctypes.c_int32), ("theta_stage", ctypes.c_int32),
-                ("rows_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("rows_per_thread", ctypes.c_int32), ("kernel", ctypes.c_int32)]
 
 
 class FbpOpts(ctypes.Structure):

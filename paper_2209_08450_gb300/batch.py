@@ -85,4 +85,4 @@ def autotune_backproject(sino: torch.Tensor, theta, center: float, vol: torch.Te
     ms = ctypes.c_float()
     _lib.call("tcp_autotune_backproject", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center),
               _lib.ref(b), _lib.stream_ptr(stream), ctypes.byref(c), ctypes.byref(ms))
-    return (c.k_slices, c.theta_stage, c.rows_per_thread), ms.value
+    return (c.k_slices, c.theta_stage, c.rows_per_thread, c.kernel), ms.value

@@ -354,7 +354,9 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
   TCP_CUDA_TRY(cudaEventCreate(&e0));
   TCP_CUDA_TRY(cudaEventCreate(&e1));
   tcp_status s = TCP_OK;
-  for (const tcp_bp_config& c : kCandidates) {
+  std::vector<tcp_bp_config> cands(std::begin(kCandidates), std::end(kCandidates));
+  if (sino->dtype == TCP_F16 || sino->dtype == TCP_BF16) cands.push_back(tcp_bp_config{8, 16, 4, 1});
+  for (const tcp_bp_config& c : cands) {
     if ((s = tcp_set_backproject_config(&c)) != TCP_OK) break;
     if ((s = tcp_backproject(sino, theta, center, vol, stream)) != TCP_OK) break;  // warm-up
     cudaEventRecord(e0, st);

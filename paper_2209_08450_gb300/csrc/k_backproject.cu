@@ -38,23 +38,10 @@ struct Geo {
 
 // Shared-memory element of the staged window.
 template <class TS> struct Win;
-template <> struct Win<float> { using type = float; };
 template <> struct Win<__half> { using type = uint32_t; };         // (q[i], q[i+1]) as f16x2
 template <> struct Win<__nv_bfloat16> { using type = uint32_t; };  // (q[i], q[i+1]) as bf16x2
 
 template <class TS> struct Interp;
-
-template <> struct Interp<float> {
-  static __device__ __forceinline__ float stage(const float* row, int j, int ndet) {
-    return (j >= 0 && j < ndet) ? __ldg(row + j) : 0.f;
-  }
-  struct W { float w0, w1; };
-  static __device__ __forceinline__ W weights(float w) { return {1.f - w, w}; }
-  static __device__ __forceinline__ void acc(float& a, const float* p, int off, const W& w) {
-    a = __fmaf_rn(w.w0, p[off], a);
-    a = __fmaf_rn(w.w1, p[off + 1], a);
-  }
-};
 
 __device__ __forceinline__ uint16_t ld_u16(const void* row, int j, int ndet) {
   return (j >= 0 && j < ndet) ? __ldg(reinterpret_cast<const unsigned short*>(row) + j) : (uint16_t)0;
@@ -527,6 +514,7 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
 }  // namespace
 
 bool valid_bp_config(const tcp_bp_config& c) {
+  if (c.kernel != 0 && c.kernel != 1) return false;
   return pick<float, float>(c, false).direct != nullptr;
 }
 
@@ -567,6 +555,10 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st, float scale) {
+  if (cfg.kernel == 1 && tc_eligible(sino)) {
+    if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
+    return launch_backproject_tc(sino, trig, center, vol, scale, st);
+  }
   const KernPair kp = pick_all(sino.dtype, vol.dtype, cfg, checked_mode());
   Kern k = kp.direct;
   if (!k) return fail(TCP_ERR_UNSUPPORTED, "backproject: no kernel for this dtype/config");

@@ -1,0 +1,415 @@
+// LineRec backprojection on the 5th-generation tensor cores, for 16-bit
+// sinograms (Sec. 2.2 / Sec. 3 of the TomocuPy paper; 16-bit storage with
+// FP32 accumulation, Sec. 2.1).
+//
+// For one angle, the backprojection of a voxel tile into K slices is a matrix
+// product: vol[v][z] += sum_j W[v][j] q[z][j], where row v of W holds the
+// two linear-interpolation weights (1 - w, w) at the detector samples floor(s)
+// and floor(s) + 1 of that voxel's ray, inside a 32-sample window that covers
+// the tile.  Only 2 of 32 entries per row are non-zero, but the tensor pipe
+// runs ~30x the FP32 FMA rate, and the slice dimension (N = 256) reuses every
+// weight 256 times.
+//
+//   A = W      128 voxels (a 16 x 8 voxel tile) x 32 samples, built by 4 warps
+//              in shared memory (64-byte-swizzled K-major layout);
+//   B = q      N slices x 32 samples of one sinogram row, one TMA tile copy
+//              (64-byte swizzle, zero fill outside the detector);
+//   D          128 x N FP32 accumulators in tensor memory for the whole angle
+//              loop; read back once with tcgen05.ld at the end.
+//
+// Pipeline per CTA (128 threads): angles in stages of S = 4, two stage
+// buffers.  Thread 0 issues the TMA copies of stage s+1 before the four warps
+// build the weights of stage s, then issues 2 MMAs (K = 16 each) per angle and
+// commits them to the stage's "empty" barrier.  The MMAs of stage s overlap
+// the weight building of stage s+1.  Every mbarrier wait is bounded by a clock
+// budget; on timeout the kernel records kErrTimeout, stops issuing, drains what
+// it issued (bounded) and frees its tensor memory.
+//
+// The ray coordinate and the weights come from the same canonical geometry as
+// the CUDA-core backprojector (FP64 tile origin + FP32 in-tile offsets), the
+// weights rounded to the sinogram's 16-bit type.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tcp_internal.cuh"
+
+namespace tcp {
+namespace {
+
+constexpr int kTcM = 128;          // voxels per tile (16 x 8)
+constexpr int kTcK = 32;           // detector samples per angle window
+constexpr int kTcS = 4;            // angles per stage
+constexpr int kTcRowBytes = 64;    // one K-major row of 32 x 16-bit
+constexpr int kTcAngleA = kTcM * kTcRowBytes;  // 8 KB of weights per angle
+constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
+
+struct TcGeo {
+  int base;  // i0 - j0
+  float f0, c, s;
+  int j0;
+  int pad[3];
+};
+
+struct TcArgs {
+  int nz, ntheta, ndet, n;
+  int nsub_x, nsub_y;  // 16 x 8 sub-tiles along x and y
+  int N;               // slices per CTA (multiple of 16, <= 256)
+  void* vol;
+  int vdt;
+  int64_t v_z, v_y;
+  const double2* trig;
+  double center, half_n;
+  float scale;
+  uint32_t idesc;
+  uint32_t* err;
+  int check;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after ~kTcBudget cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > kTcBudget) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3fff);      // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)4 << 61;                      // layout: 64-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <class TS> __device__ __forceinline__ uint16_t weight_bits(float w);
+template <> __device__ __forceinline__ uint16_t weight_bits<__half>(float w) {
+  return __half_as_ushort(__float2half_rn(w));
+}
+template <> __device__ __forceinline__ uint16_t weight_bits<__nv_bfloat16>(float w) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(w));
+}
+
+template <class TV>
+__device__ __forceinline__ void put(void* base, int64_t off, float v) {
+  Store<TV>::put(reinterpret_cast<TV*>(base) + off, v);
+}
+
+// shared memory: [A: 2 x S x 8 KB][B: 2 x S x N*64 B][geo 2 x S][bars][tmem slot]
+template <class TS>
+__global__ void __launch_bounds__(128, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int N = a.N;
+  const int bBytes = N * kTcRowBytes;  // per angle
+  unsigned char* Abuf = smem;
+  unsigned char* Bbuf = smem + 2 * kTcS * kTcAngleA;
+  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + 2 * kTcS * bBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(geo + 2 * kTcS);  // full[2], empty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // sub-tile (16 x 8 voxels) of a 32 x 32 canonical tile; blocked order over
+  // 8 x 16 sub-tiles (128 x 128 voxels) so that a wave covers a compact region
+  const int per_blk = 8 * 16;
+  const int blk = blockIdx.x / per_blk, inblk = blockIdx.x % per_blk;
+  const int blocks_x = (a.nsub_x + 7) / 8;
+  const int sub_x = (blk % blocks_x) * 8 + (inblk % 8);
+  const int sub_y = (blk / blocks_x) * 16 + (inblk / 8);
+  const int z0 = blockIdx.y * N;
+  const bool live_tile = sub_x < a.nsub_x && sub_y < a.nsub_y;
+  const int gx = sub_x >> 1, gy = sub_y >> 2;      // canonical 32 x 32 tile
+  const int ox = (sub_x & 1) * 16, oy = (sub_y & 3) * 8;  // sub-tile offset inside it
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
+
+  if (tid == 0) {
+    s_abort = 0;
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(full0 + 8 * b, 1);
+      mbar_init(empty0 + 8 * b, 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // tensor memory for D: N columns of FP32 (power of two >= 32)
+    const uint32_t cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = *tmem_slot;
+  const uint32_t tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+
+  const int nstages = (a.ntheta + kTcS - 1) / kTcS;
+  // voxel of this builder thread inside the canonical tile
+  const float fdx = (float)(ox + (tid & 15)), fdy = (float)(oy + (tid >> 4));
+
+  auto geometry = [&](int s) {  // threads 0..S-1: angle s*S + tid
+    const int th = s * kTcS + tid;
+    if (tid < kTcS && th < a.ntheta) {
+      const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
+      // lowest index reachable by the sub-tile (corners), one sample of margin,
+      // rounded down to 8 samples (16-byte TMA coordinate)
+      const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
+                       fminf((float)oy * o.s, (float)(oy + 7) * o.s);
+      const int jl = o.i0 + (int)floorf(lo) - 1;
+      const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
+      TcGeo g;
+      g.base = o.i0 - j0;
+      g.f0 = o.f0;
+      g.c = o.c;
+      g.s = o.s;
+      g.j0 = j0;
+      geo[(s & 1) * kTcS + tid] = g;
+    }
+  };
+  auto issue_tma = [&](int s) {  // thread 0
+    const int b = s & 1;
+    const int nt = min(kTcS, a.ntheta - s * kTcS);
+    mbar_expect_tx(full0 + 8 * b, (uint32_t)(nt * bBytes));
+    for (int t = 0; t < nt; ++t)
+      tma_load_3d(smem_u32(Bbuf + (b * kTcS + t) * bBytes), &tmap, full0 + 8 * b, geo[b * kTcS + t].j0,
+                  s * kTcS + t, z0);
+  };
+
+  uint32_t issued_commits = 0;  // thread 0: MMA commits so far (per buffer parity)
+  if (live_tile) geometry(0);
+  __syncthreads();
+  if (live_tile && tid == 0) issue_tma(0);
+
+  for (int s = 0; s < nstages && live_tile; ++s) {
+    const int b = s & 1;
+    if (s + 1 < nstages) geometry(s + 1);  // slot (s+1)&1 was last read in stage s-1
+    __syncthreads();
+    if (tid == 0 && s + 1 < nstages && !s_abort) {
+      // buffer (s+1)&1 is free once the MMAs of stage s-1 completed
+      if (s >= 1 && !mbar_wait(empty0 + 8 * ((s + 1) & 1), ((s - 1) >> 1) & 1)) {
+        atomicOr(a.err, kErrTimeout);
+        s_abort = 1;
+      } else {
+        issue_tma(s + 1);
+      }
+    }
+    // build the weights of stage s (buffer b: its previous MMAs, stage s-2,
+    // were waited for by thread 0 before the barrier above in stage s-1)
+    const int nt = min(kTcS, a.ntheta - s * kTcS);
+    for (int t = 0; t < nt; ++t) {
+      const TcGeo g = geo[b * kTcS + t];
+      const float sr = rel_coord(g.f0, g.c, g.s, fdx, fdy);
+      const float fl = floorf(sr);
+      const float w = sr - fl;
+      int idx = (int)fl + g.base;
+      if (a.check && (idx < 0 || idx > kTcK - 2)) {
+        atomicOr(a.err, kErrBpWindow);
+        idx = 0;
+      }
+      unsigned char* row = Abuf + (b * kTcS + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
+      const int swz = (tid & 7) >> 1;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+      const int k1 = idx + 1;
+      *reinterpret_cast<uint16_t*>(row + (((idx >> 3) ^ swz) << 4) + (idx & 7) * 2) = weight_bits<TS>(1.f - w);
+      *reinterpret_cast<uint16_t*>(row + (((k1 >> 3) ^ swz) << 4) + (k1 & 7) * 2) = weight_bits<TS>(w);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && !s_abort) {
+      if (!mbar_wait(full0 + 8 * b, (s >> 1) & 1)) {
+        atomicOr(a.err, kErrTimeout);
+        s_abort = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int t = 0; t < nt; ++t) {
+          const uint32_t aa = smem_u32(Abuf + (b * kTcS + t) * kTcAngleA);
+          const uint32_t bb = smem_u32(Bbuf + (b * kTcS + t) * bBytes);
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+            mma_f16(tmem_d, sw64_desc(aa + 32 * kk), sw64_desc(bb + 32 * kk), a.idesc, (s | t | kk) ? 1u : 0u);
+        }
+        mma_commit(empty0 + 8 * b);
+        ++issued_commits;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+  }
+
+  // wait for the last MMAs, then read D and store the tile
+  __shared__ int s_ok;
+  if (tid == 0) {
+    s_ok = live_tile && !s_abort;
+    if (live_tile && issued_commits > 0) {
+      const int last = (int)issued_commits - 1;  // commits were issued for stages 0..last in order
+      if (!mbar_wait(empty0 + 8 * (last & 1), (last >> 1) & 1)) {
+        atomicOr(a.err, kErrTimeout);
+        s_ok = 0;
+      }
+    }
+    if (s_abort && issued_commits > 0) s_ok = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (s_ok) {
+    const int m = tid;  // TMEM lane = voxel row of the tile; warp w owns lanes 32w..32w+31
+    const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + (m >> 4);
+    const bool inside = ix < a.n && iy < a.n;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (inside) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int z = z0 + c0 + q;
+          if (z < a.nz) {
+            const int64_t off = (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix;
+            const float v = __uint_as_float(r[q]) * a.scale;
+            if (a.vdt == TCP_F32) put<float>(a.vol, off, v);
+            else if (a.vdt == TCP_F16) put<__half>(a.vol, off, v);
+            else put<__nv_bfloat16>(a.vol, off, v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(tmem_cols) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int N) {
+  return 1024 + 2 * kTcS * kTcAngleA + 2 * (size_t)kTcS * N * kTcRowBytes + 2 * kTcS * sizeof(TcGeo) + 64;
+}
+
+int tc_slices(int64_t nz) {
+  const int64_t r = ((nz + 15) / 16) * 16;
+  return (int)std::min<int64_t>(256, std::max<int64_t>(16, r));
+}
+
+bool tc_eligible(const View3& sino) {
+  if (sino.dtype != TCP_F16 && sino.dtype != TCP_BF16) return false;
+  if ((uintptr_t)sino.p % 16 != 0) return false;
+  if ((sino.s1 * 2) % 16 != 0 || (sino.s0 * 2) % 16 != 0) return false;
+  if (sino.d1 < 1 || sino.d2 < 1 || sino.d0 < 1) return false;
+  return encode_fn() != nullptr;
+}
+
+tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
+                                 float scale, cudaStream_t st) {
+  if (!tc_eligible(sino)) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: sinogram not eligible");
+  const int nz = (int)sino.d0, nt = (int)sino.d1, nd = (int)sino.d2, n = (int)vol.d1;
+  if (nz == 0 || n == 0) return TCP_OK;
+  const int N = tc_slices(nz);
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {(cuuint64_t)nd, (cuuint64_t)nt, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)sino.s1 * 2, (cuuint64_t)sino.s0 * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kTcK, 1u, (cuuint32_t)N};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode_fn()(&map, sino.dtype == TCP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                 3, sino.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TCP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  TcArgs a;
+  a.nz = nz;
+  a.ntheta = nt;
+  a.ndet = nd;
+  a.n = n;
+  a.nsub_x = (n + 15) / 16;
+  a.nsub_y = (n + 7) / 8;
+  // sub-tiles are taken inside whole 32 x 32 canonical tiles
+  a.nsub_x = ((n + kTile - 1) / kTile) * 2;
+  a.nsub_y = ((n + kTile - 1) / kTile) * 4;
+  a.N = N;
+  a.vol = vol.p;
+  a.vdt = vol.dtype;
+  a.v_z = vol.s0;
+  a.v_y = vol.s1;
+  a.trig = trig.dev;
+  a.center = center;
+  a.half_n = 0.5 * (double)n;
+  a.scale = scale;
+  // instruction descriptor: D FP32, A/B F16 or BF16, K-major, N >> 3, M >> 4
+  const uint32_t fmt = sino.dtype == TCP_F16 ? 0u : 1u;
+  a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  a.err = device_error_word();
+  a.check = checked_mode() ? 1 : 0;
+  const size_t smem = tc_smem_bytes(N);
+  void (*k)(const CUtensorMap, TcArgs) =
+      sino.dtype == TCP_F16 ? k_backproject_tc<__half> : k_backproject_tc<__nv_bfloat16>;
+  TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 15) / 16;
+  dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 16), (unsigned)((nz + N - 1) / N));
+  if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");
+  k<<<grid, 128, smem, st>>>(map, a);
+  TCP_CUDA_TRY(cudaGetLastError());
+  return TCP_OK;
+}
+
+}  // namespace tcp

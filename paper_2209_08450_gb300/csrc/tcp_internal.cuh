@@ -172,6 +172,10 @@ struct BpWork {
   unsigned long long* counter;    // zeroed before each launch
 };
 
+bool tc_eligible(const View3& sino);
+tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
+                                 float scale, cudaStream_t st);
+
 BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol, float scale = 1.0f);
 int bp_threads(const tcp_bp_config& c);
 tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks);

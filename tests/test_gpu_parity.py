@@ -343,3 +343,35 @@ def test_fbp_fp16_many_angles_keeps_filtered_values_in_range():
     s = tcp.normalize_filter(raw, dark, flat, c, dtype=torch.float16, weight=1024.0)
     v = tcp.backproject(s, theta, 320 / 2.0, dtype=torch.float32, scale=np.pi / 3000 / 1024.0)
     assert rel(host(v), ref) <= 5e-3
+
+
+# ------------------------------------------------- tensor-core backprojector --
+
+@pytest.mark.parametrize("sdt", [torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (16, 13, 64, 100, 31.7), (40, 129, 200, 160, 99.2)])
+def test_backproject_tensor_cores(sdt, nz, nt, nd, n, center):
+    q, theta, c = _bp_case(nz, nt, nd, n, center, nz + nt + nd)
+    qd = to_dev(q, sdt)
+    ref = oracle.backproject(host(qd), theta, c, n)
+    try:
+        tcp.set_backproject_config(8, 16, 4, kernel=1)
+        got = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
+    finally:
+        tcp.set_backproject_config(None)
+    cuda_core = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
+    assert rel(got, ref) <= 5e-3
+    assert rel(got, cuda_core) <= 5e-3
+
+
+def test_backproject_tensor_cores_256_slices_and_scale():
+    # one full 256-slice block plus a ragged second block, 16-bit volume
+    q, theta, c = _bp_case(300, 24, 64, 64, 32.4, 1)
+    qd = to_dev(q, torch.float16)
+    try:
+        tcp.set_backproject_config(8, 16, 4, kernel=1)
+        got = host(tcp.backproject(qd, theta, c, n=64, dtype=torch.float16, scale=0.5))
+    finally:
+        tcp.set_backproject_config(None)
+    ref = 0.5 * oracle.backproject(host(qd), theta, c, 64)
+    assert rel(got, ref) <= 5e-3
