@@ -17,13 +17,12 @@
 //   D          128 x N FP32 accumulators in tensor memory for the whole angle
 //              loop; read back once with tcgen05.ld at the end.
 //
-// Pipeline per CTA (128 threads): angles in stages of S = 4, two stage
-// buffers.  Thread 0 issues the TMA copies of stage s+1 before the four warps
-// build the weights of stage s, then issues 2 MMAs (K = 16 each) per angle and
-// commits them to the stage's "empty" barrier.  The MMAs of stage s overlap
-// the weight building of stage s+1.  Every mbarrier wait is bounded by a clock
-// budget; on timeout the kernel records kErrTimeout, stops issuing, drains what
-// it issued (bounded) and frees its tensor memory.
+// Pipeline per CTA: warp-specialised roles (weight builders, TMA producer,
+// MMA issuer) exchange stages of two angles through a ring of four shared
+// buffers guarded by mbarriers, so weight building, copies and MMAs overlap.
+// Every mbarrier wait is bounded by a clock budget; on timeout the kernel
+// records kErrTimeout, every role stops, the issued MMAs are drained (bounded)
+// and the tensor memory is freed.
 //
 // The ray coordinate and the weights come from the same canonical geometry as
 // the CUDA-core backprojector (FP64 tile origin + FP32 in-tile offsets), the
@@ -40,7 +39,6 @@ namespace {
 
 constexpr int kTcM = 128;          // voxels per tile (16 x 8)
 constexpr int kTcK = 32;           // detector samples per angle window
-constexpr int kTcS = 4;            // angles per stage
 constexpr int kTcRowBytes = 64;    // one K-major row of 32 x 16-bit
 constexpr int kTcAngleA = kTcM * kTcRowBytes;  // 8 KB of weights per angle
 constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
@@ -133,23 +131,57 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
   Store<TV>::put(reinterpret_cast<TV*>(base) + off, v);
 }
 
-// shared memory: [A: 2 x S x 8 KB][B: 2 x S x N*64 B][geo 2 x S][bars][tmem slot]
+// Warp roles (192 threads):
+//   warps 0-3  build the weight matrices A (one voxel row per thread) and, at
+//              the end, read D out of tensor memory and store the tile;
+//   warp 4     producer: tile geometry of each angle and the TMA copies of B;
+//   warp 5     issues the MMAs (one elected thread) and commits them.
+// Stages of S angles cycle through NB buffers; per buffer four mbarriers:
+//   geo_full  (producer -> builders)   geometry of the stage is written;
+//   full_a    (builders -> MMA)        A built (4 warp arrivals);
+//   full_b    (TMA -> MMA)             B landed (transaction bytes);
+//   empty     (MMA commit -> producer) the stage's MMAs completed: A, B and
+//                                      the geometry slot may be reused.
+// Stage s uses buffer s % NB at phase (s / NB) & 1.
+constexpr int kTcNB = 4;   // stage buffers
+constexpr int kTcS2 = 2;   // angles per stage
+
+struct TcBars {
+  uint64_t geo_full[kTcNB], full_a[kTcNB], full_b[kTcNB], empty[kTcNB], done;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kTcBudget) {
+      *abort = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// shared memory: [A: NB x S x 8 KB][B: NB x S x N*64 B][geo NB x S][barriers]
 template <class TS>
-__global__ void __launch_bounds__(128, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+__global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
-  const int bBytes = N * kTcRowBytes;  // per angle
+  const int bBytes = N * kTcRowBytes;  // B bytes per angle
   unsigned char* Abuf = smem;
-  unsigned char* Bbuf = smem + 2 * kTcS * kTcAngleA;
-  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + 2 * kTcS * bBytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(geo + 2 * kTcS);  // full[2], empty[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
-  __shared__ int s_abort;
+  unsigned char* Bbuf = smem + kTcNB * kTcS2 * kTcAngleA;
+  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + kTcNB * kTcS2 * bBytes);
+  TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcNB * kTcS2);
+  volatile int* abort = &bars->abort;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // sub-tile (16 x 8 voxels) of a 32 x 32 canonical tile; blocked order over
-  // 8 x 16 sub-tiles (128 x 128 voxels) so that a wave covers a compact region
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int per_blk = 8 * 16;
   const int blk = blockIdx.x / per_blk, inblk = blockIdx.x % per_blk;
   const int blocks_x = (a.nsub_x + 7) / 8;
@@ -157,168 +189,162 @@ __global__ void __launch_bounds__(128, 1) k_backproject_tc(const __grid_constant
   const int sub_y = (blk / blocks_x) * 16 + (inblk / 8);
   const int z0 = blockIdx.y * N;
   const bool live_tile = sub_x < a.nsub_x && sub_y < a.nsub_y;
-  const int gx = sub_x >> 1, gy = sub_y >> 2;      // canonical 32 x 32 tile
-  const int ox = (sub_x & 1) * 16, oy = (sub_y & 3) * 8;  // sub-tile offset inside it
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
+  const int gx = sub_x >> 1, gy = sub_y >> 2;
+  const int ox = (sub_x & 1) * 16, oy = (sub_y & 3) * 8;
+  const uint32_t tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const int nstages = (a.ntheta + kTcS2 - 1) / kTcS2;
 
   if (tid == 0) {
-    s_abort = 0;
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(full0 + 8 * b, 1);
-      mbar_init(empty0 + 8 * b, 1);
+    bars->abort = 0;
+    for (int b = 0; b < kTcNB; ++b) {
+      mbar_init(smem_u32(&bars->geo_full[b]), 1);
+      mbar_init(smem_u32(&bars->full_a[b]), 4);
+      mbar_init(smem_u32(&bars->full_b[b]), 1);
+      mbar_init(smem_u32(&bars->empty[b]), 1);
     }
+    mbar_init(smem_u32(&bars->done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {  // tensor memory for D: N columns of FP32 (power of two >= 32)
-    const uint32_t cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(cols)
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tmem)),
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem_d = *tmem_slot;
-  const uint32_t tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const uint32_t tmem_d = bars->tmem;
+  int mma_stages = 0;  // MMA thread: stages whose MMAs were issued
 
-  const int nstages = (a.ntheta + kTcS - 1) / kTcS;
-  // voxel of this builder thread inside the canonical tile
-  const float fdx = (float)(ox + (tid & 15)), fdy = (float)(oy + (tid >> 4));
-
-  auto geometry = [&](int s) {  // threads 0..S-1: angle s*S + tid
-    const int th = s * kTcS + tid;
-    if (tid < kTcS && th < a.ntheta) {
-      const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
-      // lowest index reachable by the sub-tile (corners), one sample of margin,
-      // rounded down to 8 samples (16-byte TMA coordinate)
-      const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
-                       fminf((float)oy * o.s, (float)(oy + 7) * o.s);
-      const int jl = o.i0 + (int)floorf(lo) - 1;
-      const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
-      TcGeo g;
-      g.base = o.i0 - j0;
-      g.f0 = o.f0;
-      g.c = o.c;
-      g.s = o.s;
-      g.j0 = j0;
-      geo[(s & 1) * kTcS + tid] = g;
-    }
-  };
-  auto issue_tma = [&](int s) {  // thread 0
-    const int b = s & 1;
-    const int nt = min(kTcS, a.ntheta - s * kTcS);
-    mbar_expect_tx(full0 + 8 * b, (uint32_t)(nt * bBytes));
-    for (int t = 0; t < nt; ++t)
-      tma_load_3d(smem_u32(Bbuf + (b * kTcS + t) * bBytes), &tmap, full0 + 8 * b, geo[b * kTcS + t].j0,
-                  s * kTcS + t, z0);
-  };
-
-  uint32_t issued_commits = 0;  // thread 0: MMA commits so far (per buffer parity)
-  if (live_tile) geometry(0);
-  __syncthreads();
-  if (live_tile && tid == 0) issue_tma(0);
-
-  for (int s = 0; s < nstages && live_tile; ++s) {
-    const int b = s & 1;
-    if (s + 1 < nstages) geometry(s + 1);  // slot (s+1)&1 was last read in stage s-1
-    __syncthreads();
-    if (tid == 0 && s + 1 < nstages && !s_abort) {
-      // buffer (s+1)&1 is free once the MMAs of stage s-1 completed
-      if (s >= 1 && !mbar_wait(empty0 + 8 * ((s + 1) & 1), ((s - 1) >> 1) & 1)) {
-        atomicOr(a.err, kErrTimeout);
-        s_abort = 1;
-      } else {
-        issue_tma(s + 1);
-      }
-    }
-    // build the weights of stage s (buffer b: its previous MMAs, stage s-2,
-    // were waited for by thread 0 before the barrier above in stage s-1)
-    const int nt = min(kTcS, a.ntheta - s * kTcS);
-    for (int t = 0; t < nt; ++t) {
-      const TcGeo g = geo[b * kTcS + t];
-      const float sr = rel_coord(g.f0, g.c, g.s, fdx, fdy);
-      const float fl = floorf(sr);
-      const float w = sr - fl;
-      int idx = (int)fl + g.base;
-      if (a.check && (idx < 0 || idx > kTcK - 2)) {
-        atomicOr(a.err, kErrBpWindow);
-        idx = 0;
-      }
-      unsigned char* row = Abuf + (b * kTcS + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
-      const int swz = (tid & 7) >> 1;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-      const int k1 = idx + 1;
-      *reinterpret_cast<uint16_t*>(row + (((idx >> 3) ^ swz) << 4) + (idx & 7) * 2) = weight_bits<TS>(1.f - w);
-      *reinterpret_cast<uint16_t*>(row + (((k1 >> 3) ^ swz) << 4) + (k1 & 7) * 2) = weight_bits<TS>(w);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && !s_abort) {
-      if (!mbar_wait(full0 + 8 * b, (s >> 1) & 1)) {
-        atomicOr(a.err, kErrTimeout);
-        s_abort = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int t = 0; t < nt; ++t) {
-          const uint32_t aa = smem_u32(Abuf + (b * kTcS + t) * kTcAngleA);
-          const uint32_t bb = smem_u32(Bbuf + (b * kTcS + t) * bBytes);
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
-            mma_f16(tmem_d, sw64_desc(aa + 32 * kk), sw64_desc(bb + 32 * kk), a.idesc, (s | t | kk) ? 1u : 0u);
+  if (live_tile) {
+    if (warp == 4) {
+      // ---- producer: geometry and TMA of B
+      for (int s = 0; s < nstages; ++s) {
+        const int b = s % kTcNB, k = s / kTcNB;
+        if (s >= kTcNB && !wait_or_abort(smem_u32(&bars->empty[b]), (k - 1) & 1, abort, a.err)) break;
+        const int nt = min(kTcS2, a.ntheta - s * kTcS2);
+        if (lane < nt) {
+          const int th = s * kTcS2 + lane;
+          const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
+          const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
+                           fminf((float)oy * o.s, (float)(oy + 7) * o.s);
+          const int jl = o.i0 + (int)floorf(lo) - 1;
+          const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
+          TcGeo g;
+          g.base = o.i0 - j0;
+          g.f0 = o.f0;
+          g.c = o.c;
+          g.s = o.s;
+          g.j0 = j0;
+          geo[b * kTcS2 + lane] = g;
         }
-        mma_commit(empty0 + 8 * b);
-        ++issued_commits;
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(smem_u32(&bars->geo_full[b]));
+          const uint32_t fb = smem_u32(&bars->full_b[b]);
+          mbar_expect_tx(fb, (uint32_t)(nt * bBytes));
+          for (int t = 0; t < nt; ++t)
+            tma_load_3d(smem_u32(Bbuf + (b * kTcS2 + t) * bBytes), &tmap, fb, geo[b * kTcS2 + t].j0,
+                        s * kTcS2 + t, z0);
+        }
+        __syncwarp();
+      }
+    } else if (warp == 5) {
+      // ---- MMA issuer
+      if (lane == 0) {
+        for (int s = 0; s < nstages; ++s) {
+          const int b = s % kTcNB, k = s / kTcNB;
+          if (!wait_or_abort(smem_u32(&bars->full_a[b]), k & 1, abort, a.err)) break;
+          if (!wait_or_abort(smem_u32(&bars->full_b[b]), k & 1, abort, a.err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int nt = min(kTcS2, a.ntheta - s * kTcS2);
+          for (int t = 0; t < nt; ++t) {
+            const uint32_t aa = smem_u32(Abuf + (b * kTcS2 + t) * kTcAngleA);
+            const uint32_t bb = smem_u32(Bbuf + (b * kTcS2 + t) * bBytes);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+              mma_f16(tmem_d, sw64_desc(aa + 32 * kk), sw64_desc(bb + 32 * kk), a.idesc, (s | t | kk) ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&bars->empty[b]));
+          ++mma_stages;
+        }
+        // every issued MMA completes before `done` arrives
+        mma_commit(smem_u32(&bars->done));
+      }
+      __syncwarp();
+    } else {
+      // ---- builders: one voxel row of A per thread
+      const float fdx = (float)(ox + (tid & 15)), fdy = (float)(oy + (tid >> 4));
+      const int swz = (tid & 7) >> 1;
+      for (int s = 0; s < nstages; ++s) {
+        const int b = s % kTcNB, k = s / kTcNB;
+        if (!wait_or_abort(smem_u32(&bars->geo_full[b]), k & 1, abort, a.err)) break;
+        const int nt = min(kTcS2, a.ntheta - s * kTcS2);
+        for (int t = 0; t < nt; ++t) {
+          const TcGeo g = geo[b * kTcS2 + t];
+          const float sr = rel_coord(g.f0, g.c, g.s, fdx, fdy);
+          const float fl = floorf(sr);
+          const float w = sr - fl;
+          int idx = (int)fl + g.base;
+          if (a.check && (idx < 0 || idx > kTcK - 2)) {
+            atomicOr(a.err, kErrBpWindow);
+            idx = 0;
+          }
+          unsigned char* row = Abuf + (b * kTcS2 + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+          const int k1 = idx + 1;
+          *reinterpret_cast<uint16_t*>(row + (((idx >> 3) ^ swz) << 4) + (idx & 7) * 2) = weight_bits<TS>(1.f - w);
+          *reinterpret_cast<uint16_t*>(row + (((k1 >> 3) ^ swz) << 4) + (k1 & 7) * 2) = weight_bits<TS>(w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->full_a[b]));
       }
     }
-    __syncthreads();
-    if (s_abort) break;
   }
 
-  // wait for the last MMAs, then read D and store the tile
-  __shared__ int s_ok;
-  if (tid == 0) {
-    s_ok = live_tile && !s_abort;
-    if (live_tile && issued_commits > 0) {
-      const int last = (int)issued_commits - 1;  // commits were issued for stages 0..last in order
-      if (!mbar_wait(empty0 + 8 * (last & 1), (last >> 1) & 1)) {
-        atomicOr(a.err, kErrTimeout);
-        s_ok = 0;
-      }
-    }
-    if (s_abort && issued_commits > 0) s_ok = 0;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // ---- epilogue (builder warps): wait for the last MMAs, read D, store
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (s_ok) {
-    const int m = tid;  // TMEM lane = voxel row of the tile; warp w owns lanes 32w..32w+31
-    const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + (m >> 4);
-    const bool inside = ix < a.n && iy < a.n;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (inside) {
+  if (live_tile && warp < 4) {
+    bool ok = !*abort && wait_or_abort(smem_u32(&bars->done), 0, abort, a.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int m = tid;  // TMEM lane = voxel row; warp w owns lanes 32w..32w+31
+      const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + (m >> 4);
+      const bool inside = ix < a.n && iy < a.n;
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (inside) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int z = z0 + c0 + q;
-          if (z < a.nz) {
-            const int64_t off = (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix;
-            const float v = __uint_as_float(r[q]) * a.scale;
-            if (a.vdt == TCP_F32) put<float>(a.vol, off, v);
-            else if (a.vdt == TCP_F16) put<__half>(a.vol, off, v);
-            else put<__nv_bfloat16>(a.vol, off, v);
+          for (int q = 0; q < 16; ++q) {
+            const int z = z0 + c0 + q;
+            if (z < a.nz) {
+              const int64_t off = (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix;
+              const float v = __uint_as_float(r[q]) * a.scale;
+              if (a.vdt == TCP_F32) put<float>(a.vol, off, v);
+              else if (a.vdt == TCP_F16) put<__half>(a.vol, off, v);
+              else put<__nv_bfloat16>(a.vol, off, v);
+            }
           }
         }
       }
+    }
+  }
+  // On an abort, MMAs already issued may still run: wait (bounded) for them
+  // before the tensor memory is released.
+  if (live_tile && warp == 5 && lane == 0 && *abort && mma_stages > 0) {
+    const long long t0 = clock64();
+    while (!mbar_try(smem_u32(&bars->done), 0) && clock64() - t0 < kTcBudget) {
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -344,7 +370,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 size_t tc_smem_bytes(int N) {
-  return 1024 + 2 * kTcS * kTcAngleA + 2 * (size_t)kTcS * N * kTcRowBytes + 2 * kTcS * sizeof(TcGeo) + 64;
+  return 1024 + (size_t)kTcNB * kTcS2 * kTcAngleA + (size_t)kTcNB * kTcS2 * N * kTcRowBytes +
+         (size_t)kTcNB * kTcS2 * sizeof(TcGeo) + sizeof(TcBars);
 }
 
 int tc_slices(int64_t nz) {
@@ -407,7 +434,7 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 15) / 16;
   dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 16), (unsigned)((nz + N - 1) / N));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");
-  k<<<grid, 128, smem, st>>>(map, a);
+  k<<<grid, 192, smem, st>>>(map, a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
 }
