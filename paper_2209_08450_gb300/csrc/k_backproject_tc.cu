@@ -143,8 +143,9 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
 //   empty     (MMA commit -> producer) the stage's MMAs completed: A, B and
 //                                      the geometry slot may be reused.
 // Stage s uses buffer s % NB at phase (s / NB) & 1.
-constexpr int kTcNB = 4;   // stage buffers
-constexpr int kTcS2 = 2;   // angles per stage
+constexpr int kTcNB = 4;       // stage buffers
+constexpr int kTcS2 = 2;       // angles per stage
+constexpr int kTcGeoRing = 64; // geometry ring (two chunks of 32 angles)
 
 struct TcBars {
   uint64_t geo_full[kTcNB], full_a[kTcNB], full_b[kTcNB], empty[kTcNB], done;
@@ -177,8 +178,8 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   const int bBytes = N * kTcRowBytes;  // B bytes per angle
   unsigned char* Abuf = smem;
   unsigned char* Bbuf = smem + kTcNB * kTcS2 * kTcAngleA;
-  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + kTcNB * kTcS2 * bBytes);
-  TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcNB * kTcS2);
+  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + kTcNB * kTcS2 * bBytes);  // ring: angle th -> geo[th % 64]
+  TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcGeoRing);
   volatile int* abort = &bars->abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -220,33 +221,43 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   if (live_tile) {
     if (warp == 4) {
       // ---- producer: geometry and TMA of B
+      // Geometry is computed 32 angles at a time (one per lane), so the
+      // angle-table load and the FP64 origin arithmetic are paid once per 32
+      // angles.  Ring slot th % 64 is rewritten for the angles of chunk c
+      // (32c .. 32c+31) only after the producer waited for the stage that is
+      // kTcNB stages before chunk c's first one, which is well after the last
+      // stage that read chunk c-2.
+      constexpr int kStagesPerChunk = 32 / kTcS2;
       for (int s = 0; s < nstages; ++s) {
         const int b = s % kTcNB, k = s / kTcNB;
         if (s >= kTcNB && !wait_or_abort(smem_u32(&bars->empty[b]), (k - 1) & 1, abort, a.err)) break;
-        const int nt = min(kTcS2, a.ntheta - s * kTcS2);
-        if (lane < nt) {
+        if (s % kStagesPerChunk == 0) {
           const int th = s * kTcS2 + lane;
-          const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
-          const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
-                           fminf((float)oy * o.s, (float)(oy + 7) * o.s);
-          const int jl = o.i0 + (int)floorf(lo) - 1;
-          const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
-          TcGeo g;
-          g.base = o.i0 - j0;
-          g.f0 = o.f0;
-          g.c = o.c;
-          g.s = o.s;
-          g.j0 = j0;
-          geo[b * kTcS2 + lane] = g;
+          if (th < a.ntheta) {
+            const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
+            const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
+                             fminf((float)oy * o.s, (float)(oy + 7) * o.s);
+            const int jl = o.i0 + (int)floorf(lo) - 1;
+            const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
+            TcGeo g;
+            g.base = o.i0 - j0;
+            g.f0 = o.f0;
+            g.c = o.c;
+            g.s = o.s;
+            g.j0 = j0;
+            geo[th % kTcGeoRing] = g;
+          }
+          __syncwarp();
         }
-        __syncwarp();
+        const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         if (lane == 0) {
           mbar_arrive(smem_u32(&bars->geo_full[b]));
           const uint32_t fb = smem_u32(&bars->full_b[b]);
           mbar_expect_tx(fb, (uint32_t)(nt * bBytes));
-          for (int t = 0; t < nt; ++t)
-            tma_load_3d(smem_u32(Bbuf + (b * kTcS2 + t) * bBytes), &tmap, fb, geo[b * kTcS2 + t].j0,
-                        s * kTcS2 + t, z0);
+          for (int t = 0; t < nt; ++t) {
+            const int th = s * kTcS2 + t;
+            tma_load_3d(smem_u32(Bbuf + (b * kTcS2 + t) * bBytes), &tmap, fb, geo[th % kTcGeoRing].j0, th, z0);
+          }
         }
         __syncwarp();
       }
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
         if (!wait_or_abort(smem_u32(&bars->geo_full[b]), k & 1, abort, a.err)) break;
         const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         for (int t = 0; t < nt; ++t) {
-          const TcGeo g = geo[b * kTcS2 + t];
+          const TcGeo g = geo[(s * kTcS2 + t) % kTcGeoRing];
           const float sr = rel_coord(g.f0, g.c, g.s, fdx, fdy);
           const float fl = floorf(sr);
           const float w = sr - fl;
@@ -371,7 +382,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 size_t tc_smem_bytes(int N) {
   return 1024 + (size_t)kTcNB * kTcS2 * kTcAngleA + (size_t)kTcNB * kTcS2 * N * kTcRowBytes +
-         (size_t)kTcNB * kTcS2 * sizeof(TcGeo) + sizeof(TcBars);
+         (size_t)kTcGeoRing * sizeof(TcGeo) + sizeof(TcBars);
 }
 
 int tc_slices(int64_t nz) {
