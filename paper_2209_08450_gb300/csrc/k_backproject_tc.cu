@@ -43,13 +43,6 @@ constexpr int kTcRowBytes = 64;    // one K-major row of 32 x 16-bit
 constexpr int kTcAngleA = kTcM * kTcRowBytes;  // 8 KB of weights per angle
 constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
 
-struct TcGeo {
-  int base;  // i0 - j0
-  float f0, c, s;
-  int j0;
-  int pad[3];
-};
-
 struct TcArgs {
   int nz, ntheta, ndet, n;
   int nsub_x, nsub_y;  // 16 x 8 sub-tiles along x and y
@@ -134,21 +127,30 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
 // Warp roles (192 threads):
 //   warps 0-3  build the weight matrices A (one voxel row per thread) and, at
 //              the end, read D out of tensor memory and store the tile;
-//   warp 4     producer: tile geometry of each angle and the TMA copies of B;
+//   warp 4     producer: tile geometry (32 angles per pass) and the TMA
+//              copies of B;
 //   warp 5     issues the MMAs (one elected thread) and commits them.
-// Stages of S angles cycle through NB buffers; per buffer four mbarriers:
-//   geo_full  (producer -> builders)   geometry of the stage is written;
-//   full_a    (builders -> MMA)        A built (4 warp arrivals);
-//   full_b    (TMA -> MMA)             B landed (transaction bytes);
-//   empty     (MMA commit -> producer) the stage's MMAs completed: A, B and
-//                                      the geometry slot may be reused.
-// Stage s uses buffer s % NB at phase (s / NB) & 1.
-constexpr int kTcNB = 4;       // stage buffers
-constexpr int kTcS2 = 2;       // angles per stage
-constexpr int kTcGeoRing = 64; // geometry ring (two chunks of 32 angles)
+// A stage is two angles.  A (built in the SM, cheap) cycles through kTcNA
+// buffers; B (copied from L2, ~2 us away) through kTcNBB buffers so that
+// about 192 KB of copies are in flight.  Barriers:
+//   geo_full[s % NBB] producer -> builders: geometry of stage s is written
+//   full_a  [s % NA ] builders -> MMA: A of stage s built (4 warp arrivals)
+//   empty_a [s % NA ] MMA commit -> builders: A buffer free again
+//   full_b  [s % NBB] TMA -> MMA: B of stage s landed (transaction bytes)
+//   empty_b [s % NBB] MMA commit -> producer: B buffer free again
+// Stage s waits the phase (s / ring) & 1 of its ring slot.
+constexpr int kTcNA = 2;        // A stage buffers
+constexpr int kTcNBB = 6;       // B stage buffers
+constexpr int kTcS2 = 2;        // angles per stage
+constexpr int kTcGeoRing = 64;  // geometry ring (two chunks of 32 angles)
+
+struct TcGeoP {  // packed geometry of one angle (16 bytes)
+  int bj;        // low 16 bits: i0 - j0, high 16 bits: j0 (both signed)
+  float f0, c, s;
+};
 
 struct TcBars {
-  uint64_t geo_full[kTcNB], full_a[kTcNB], full_b[kTcNB], empty[kTcNB], done;
+  uint64_t geo_full[kTcNBB], full_b[kTcNBB], empty_b[kTcNBB], full_a[kTcNA], empty_a[kTcNA], done;
   uint32_t tmem;
   int abort;
 };
@@ -169,7 +171,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// shared memory: [A: NB x S x 8 KB][B: NB x S x N*64 B][geo NB x S][barriers]
+// shared memory: [A: NA x S x 8 KB][B: NBB x S x N*64 B][geo ring][barriers]
 template <class TS>
 __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -177,8 +179,8 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   const int N = a.N;
   const int bBytes = N * kTcRowBytes;  // B bytes per angle
   unsigned char* Abuf = smem;
-  unsigned char* Bbuf = smem + kTcNB * kTcS2 * kTcAngleA;
-  TcGeo* geo = reinterpret_cast<TcGeo*>(Bbuf + kTcNB * kTcS2 * bBytes);  // ring: angle th -> geo[th % 64]
+  unsigned char* Bbuf = smem + kTcNA * kTcS2 * kTcAngleA;
+  TcGeoP* geo = reinterpret_cast<TcGeoP*>(Bbuf + kTcNBB * kTcS2 * bBytes);  // angle th -> geo[th % 64]
   TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcGeoRing);
   volatile int* abort = &bars->abort;
 
@@ -197,11 +199,14 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
 
   if (tid == 0) {
     bars->abort = 0;
-    for (int b = 0; b < kTcNB; ++b) {
-      mbar_init(smem_u32(&bars->geo_full[b]), 1);
-      mbar_init(smem_u32(&bars->full_a[b]), 4);
-      mbar_init(smem_u32(&bars->full_b[b]), 1);
-      mbar_init(smem_u32(&bars->empty[b]), 1);
+    for (int i = 0; i < kTcNBB; ++i) {
+      mbar_init(smem_u32(&bars->geo_full[i]), 1);
+      mbar_init(smem_u32(&bars->full_b[i]), 1);
+      mbar_init(smem_u32(&bars->empty_b[i]), 1);
+    }
+    for (int i = 0; i < kTcNA; ++i) {
+      mbar_init(smem_u32(&bars->full_a[i]), 4);
+      mbar_init(smem_u32(&bars->empty_a[i]), 1);
     }
     mbar_init(smem_u32(&bars->done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,17 +225,13 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
 
   if (live_tile) {
     if (warp == 4) {
-      // ---- producer: geometry and TMA of B
-      // Geometry is computed 32 angles at a time (one per lane), so the
-      // angle-table load and the FP64 origin arithmetic are paid once per 32
-      // angles.  Ring slot th % 64 is rewritten for the angles of chunk c
-      // (32c .. 32c+31) only after the producer waited for the stage that is
-      // kTcNB stages before chunk c's first one, which is well after the last
-      // stage that read chunk c-2.
+      // ---- producer.  Ring slot th % 64 of chunk c (angles 32c .. 32c+31)
+      // is rewritten only after empty_b of stage 16c - kTcNBB completed, which
+      // is after the builders finished every stage of chunk c - 2.
       constexpr int kStagesPerChunk = 32 / kTcS2;
       for (int s = 0; s < nstages; ++s) {
-        const int b = s % kTcNB, k = s / kTcNB;
-        if (s >= kTcNB && !wait_or_abort(smem_u32(&bars->empty[b]), (k - 1) & 1, abort, a.err)) break;
+        const int ib = s % kTcNBB, kb = s / kTcNBB;
+        if (s >= kTcNBB && !wait_or_abort(smem_u32(&bars->empty_b[ib]), (kb - 1) & 1, abort, a.err)) break;
         if (s % kStagesPerChunk == 0) {
           const int th = s * kTcS2 + lane;
           if (th < a.ntheta) {
@@ -239,24 +240,24 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
                              fminf((float)oy * o.s, (float)(oy + 7) * o.s);
             const int jl = o.i0 + (int)floorf(lo) - 1;
             const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
-            TcGeo g;
-            g.base = o.i0 - j0;
+            TcGeoP g;
+            g.bj = ((o.i0 - j0) & 0xffff) | (j0 << 16);
             g.f0 = o.f0;
             g.c = o.c;
             g.s = o.s;
-            g.j0 = j0;
             geo[th % kTcGeoRing] = g;
           }
           __syncwarp();
         }
         const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         if (lane == 0) {
-          mbar_arrive(smem_u32(&bars->geo_full[b]));
-          const uint32_t fb = smem_u32(&bars->full_b[b]);
+          mbar_arrive(smem_u32(&bars->geo_full[ib]));
+          const uint32_t fb = smem_u32(&bars->full_b[ib]);
           mbar_expect_tx(fb, (uint32_t)(nt * bBytes));
           for (int t = 0; t < nt; ++t) {
             const int th = s * kTcS2 + t;
-            tma_load_3d(smem_u32(Bbuf + (b * kTcS2 + t) * bBytes), &tmap, fb, geo[th % kTcGeoRing].j0, th, z0);
+            tma_load_3d(smem_u32(Bbuf + (ib * kTcS2 + t) * bBytes), &tmap, fb, geo[th % kTcGeoRing].bj >> 16, th,
+                        z0);
           }
         }
         __syncwarp();
@@ -265,19 +266,20 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
       // ---- MMA issuer
       if (lane == 0) {
         for (int s = 0; s < nstages; ++s) {
-          const int b = s % kTcNB, k = s / kTcNB;
-          if (!wait_or_abort(smem_u32(&bars->full_a[b]), k & 1, abort, a.err)) break;
-          if (!wait_or_abort(smem_u32(&bars->full_b[b]), k & 1, abort, a.err)) break;
+          const int ia = s % kTcNA, ib = s % kTcNBB;
+          if (!wait_or_abort(smem_u32(&bars->full_a[ia]), (s / kTcNA) & 1, abort, a.err)) break;
+          if (!wait_or_abort(smem_u32(&bars->full_b[ib]), (s / kTcNBB) & 1, abort, a.err)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int nt = min(kTcS2, a.ntheta - s * kTcS2);
           for (int t = 0; t < nt; ++t) {
-            const uint32_t aa = smem_u32(Abuf + (b * kTcS2 + t) * kTcAngleA);
-            const uint32_t bb = smem_u32(Bbuf + (b * kTcS2 + t) * bBytes);
+            const uint32_t aa = smem_u32(Abuf + (ia * kTcS2 + t) * kTcAngleA);
+            const uint32_t bb = smem_u32(Bbuf + (ib * kTcS2 + t) * bBytes);
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk)
               mma_f16(tmem_d, sw64_desc(aa + 32 * kk), sw64_desc(bb + 32 * kk), a.idesc, (s | t | kk) ? 1u : 0u);
           }
-          mma_commit(smem_u32(&bars->empty[b]));
+          mma_commit(smem_u32(&bars->empty_a[ia]));
+          mma_commit(smem_u32(&bars->empty_b[ib]));
           ++mma_stages;
         }
         // every issued MMA completes before `done` arrives
@@ -289,20 +291,21 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
       const float fdx = (float)(ox + (tid & 15)), fdy = (float)(oy + (tid >> 4));
       const int swz = (tid & 7) >> 1;
       for (int s = 0; s < nstages; ++s) {
-        const int b = s % kTcNB, k = s / kTcNB;
-        if (!wait_or_abort(smem_u32(&bars->geo_full[b]), k & 1, abort, a.err)) break;
+        const int ia = s % kTcNA, ib = s % kTcNBB;
+        if (!wait_or_abort(smem_u32(&bars->geo_full[ib]), (s / kTcNBB) & 1, abort, a.err)) break;
+        if (s >= kTcNA && !wait_or_abort(smem_u32(&bars->empty_a[ia]), (s / kTcNA - 1) & 1, abort, a.err)) break;
         const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         for (int t = 0; t < nt; ++t) {
-          const TcGeo g = geo[(s * kTcS2 + t) % kTcGeoRing];
+          const TcGeoP g = geo[(s * kTcS2 + t) % kTcGeoRing];
           const float sr = rel_coord(g.f0, g.c, g.s, fdx, fdy);
           const float fl = floorf(sr);
           const float w = sr - fl;
-          int idx = (int)fl + g.base;
+          int idx = (int)fl + (int)(short)(g.bj & 0xffff);
           if (a.check && (idx < 0 || idx > kTcK - 2)) {
             atomicOr(a.err, kErrBpWindow);
             idx = 0;
           }
-          unsigned char* row = Abuf + (b * kTcS2 + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
+          unsigned char* row = Abuf + (ia * kTcS2 + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
 #pragma unroll
           for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
           const int k1 = idx + 1;
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars->full_a[b]));
+        if (lane == 0) mbar_arrive(smem_u32(&bars->full_a[ia]));
       }
     }
   }
@@ -381,8 +384,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 size_t tc_smem_bytes(int N) {
-  return 1024 + (size_t)kTcNB * kTcS2 * kTcAngleA + (size_t)kTcNB * kTcS2 * N * kTcRowBytes +
-         (size_t)kTcGeoRing * sizeof(TcGeo) + sizeof(TcBars);
+  return 1024 + (size_t)kTcNA * kTcS2 * kTcAngleA + (size_t)kTcNBB * kTcS2 * N * kTcRowBytes +
+         (size_t)kTcGeoRing * sizeof(TcGeoP) + sizeof(TcBars);
 }
 
 int tc_slices(int64_t nz) {
