@@ -284,7 +284,8 @@ def main():
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=0, help="slices (default: size); a small case of the same launches")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"], help="storage of the headline path")
-    ap.add_argument("--chunk", type=int, default=32)
+    ap.add_argument("--chunk", type=int, default=32, help="slices per chunk for FP32")
+    ap.add_argument("--chunk16", type=int, default=256, help="slices per chunk for 16-bit storage")
     ap.add_argument("--variants", default="f32,f16,bf16")
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
@@ -320,15 +321,18 @@ def main():
                                                             slices=np.arange((n - nz) // 2, (n - nz) // 2 + nz))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    nchunks = (nz + args.chunk - 1) // args.chunk
     raw_bytes = raw.numel() * 2
     hdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+
+    def chunk_for(dtype):  # FP32: --chunk; 16-bit: --chunk16 (the tensor-core backprojector's N)
+        return args.chunk if dtype == torch.float32 else args.chunk16
+    nchunks = (nz + chunk_for(hdt) - 1) // chunk_for(hdt)
 
     def run_steps(dtype, steps, warmup, out):
         stream = torch.cuda.current_stream()
 
         def step():
-            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=args.chunk, stream=stream)
+            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(dtype), stream=stream)
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
@@ -370,12 +374,12 @@ def main():
     par = {args.dtype: parity(vol, zs)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
-    s_chunk = torch.empty((args.chunk, nt, n), dtype=hdt, device=dev)
-    v_chunk = vol[:args.chunk]
+    kc = min(chunk_for(hdt), nz)
+    s_chunk = torch.empty((kc, nt, n), dtype=hdt, device=dev)
+    v_chunk = vol[:kc]
     dm, fm = tcp.frame_mean(dark), tcp.frame_mean(flat)
-    z0 = max(0, nz // 2 - args.chunk)
-    tcp.normalize_filter(raw[:, z0:z0 + args.chunk], dm[z0:z0 + args.chunk], fm[z0:z0 + args.chunk], center,
-                         out=s_chunk)
+    z0 = max(0, nz // 2 - kc)
+    tcp.normalize_filter(raw[:, z0:z0 + kc], dm[z0:z0 + kc], fm[z0:z0 + kc], center, out=s_chunk)
 
     def time_kernel(fn, reps=5):
         fn()
@@ -389,9 +393,9 @@ def main():
         return a.elapsed_time(b) / reps
 
     bp_ms = time_kernel(lambda: tcp.backproject(s_chunk, theta, n / 2.0, out=v_chunk))
-    nf_ms = time_kernel(lambda: tcp.normalize_filter(raw[:, z0:z0 + args.chunk], dm[z0:z0 + args.chunk],
-                                                     fm[z0:z0 + args.chunk], center, out=s_chunk))
-    interps = args.chunk * n * n * nt
+    nf_ms = time_kernel(lambda: tcp.normalize_filter(raw[:, z0:z0 + kc], dm[z0:z0 + kc], fm[z0:z0 + kc], center,
+                                                     out=s_chunk))
+    interps = kc * n * n * nt
     clk_max = 2070.0
     try:
         clk_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
@@ -409,7 +413,7 @@ def main():
         hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
         pass
-    nf_bytes = nt * args.chunk * n * 2 + args.chunk * nt * n * s_chunk.element_size()
+    nf_bytes = nt * kc * n * 2 + kc * nt * n * s_chunk.element_size()
     secondary = {"normalize_filter": {"bound": "hbm", "achieved": nf_bytes / (nf_ms * 1e-3) / 1e9, "peak": hbm,
                                       "unit": "GB/s", "frac": nf_bytes / (nf_ms * 1e-3) / 1e9 / hbm,
                                       "ms_per_launch": nf_ms}}
@@ -440,7 +444,7 @@ def main():
         stream = torch.cuda.current_stream()
 
         def e2e_step():
-            tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=args.chunk, stream=stream)
+            tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=chunk_for(hdt), stream=stream)
         e2e_step()
         torch.cuda.synchronize()
         barrier(world, local)
@@ -474,8 +478,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": args.dtype, "data": DATA,
             "config": {"workload": "%dx%d^2 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
-                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, args.chunk),
-                       "n": n, "nz": nz, "ntheta": nt, "chunk_nz": args.chunk,
+                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, chunk_for(hdt)),
+                       "n": n, "nz": nz, "ntheta": nt, "chunk_nz": chunk_for(hdt),
                        "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,

@@ -232,7 +232,8 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * kernel: 0 = FP32 pipes (every dtype); 1 = tensor cores (tcgen05.mma with
  * TMEM accumulators, FP16/BF16 sinograms whose row and slice strides are
  * multiples of 8 elements; other inputs fall back to kernel 0, and the
- * other fields are ignored). */
+ * other fields are ignored).  The automatic choice is kernel 1 for 16-bit
+ * sinograms with at least 32 slices. */
 typedef struct {
   int32_t k_slices;
   int32_t theta_stage;
@@ -249,7 +250,7 @@ tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, 
 /* ------------------------------------------------------------- pipeline -- */
 
 typedef struct {
-  int32_t chunk_nz;     /* slices per chunk (default 16 when <= 0) */
+  int32_t chunk_nz;     /* slices per chunk (<= 0: 256 for 16-bit sinograms, 32 for FP32) */
   int32_t sino_dtype;   /* storage of the intermediate sinogram chunk */
   int32_t filter;       /* tcp_filter_kind */
   int32_t pad_mode;     /* tcp_pad_mode */

@@ -158,7 +158,7 @@ def get_backproject_config(nz, ntheta, ndet, n, sino_dtype=torch.float32, vol_dt
 
 
 def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center: float,
-        out: torch.Tensor | None = None, dtype=torch.float32, n: int | None = None, chunk_nz: int = 16,
+        out: torch.Tensor | None = None, dtype=torch.float32, n: int | None = None, chunk_nz: int = 0,
         filter: str = "shepp", pad: str = "edge", sino_dtype=None, n_buffers: int = 2,
         stream=None) -> torch.Tensor:
     """Chunked FBP (normalise -> filter -> backproject per z-slab, Sec. 2.3).

@@ -143,9 +143,11 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "fbp: ndet > 4096");
   tcp_fbp_opts o{};
   if (opts) o = *opts;
-  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : 16;
   const int sdt = (o.sino_dtype == TCP_F32 || o.sino_dtype == TCP_F16 || o.sino_dtype == TCP_BF16) ? o.sino_dtype
                                                                                                    : vol->dtype;
+  // default chunk: 256 slices for 16-bit sinograms (the tensor-core
+  // backprojector's N), 32 otherwise
+  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : (sdt == TCP_F32 ? 32 : 256);
   if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
   if (o.pad_mode != TCP_PAD_EDGE && o.pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
   const int B = o.n_buffers == 3 ? 3 : 2;
