@@ -10,16 +10,19 @@
 // runs ~30x the FP32 FMA rate, and the slice dimension (N = 256) reuses every
 // weight 256 times.
 //
-//   A = W      128 voxels (a 16 x 8 voxel tile) x 32 samples, built by 4 warps
-//              in shared memory (64-byte-swizzled K-major layout);
+//   A = W      two 128 x 32 halves (a 16 x 16 voxel tile: rows 0-7 and 8-15)
+//              built by 8 warps in shared memory (64-byte-swizzled K-major);
 //   B = q      N slices x 32 samples of one sinogram row, one TMA tile copy
-//              (64-byte swizzle, zero fill outside the detector);
-//   D          128 x N FP32 accumulators in tensor memory for the whole angle
-//              loop; read back once with tcgen05.ld at the end.
+//              (64-byte swizzle, zero fill outside the detector), shared by
+//              both halves: the footprint of a 16 x 16 tile spans at most
+//              15 sqrt(2) < 22 samples, so 32 still cover it after the window
+//              start is rounded down to 16 bytes;
+//   D          two 128 x N FP32 accumulators in tensor memory (2N columns)
+//              for the whole angle loop; read back once with tcgen05.ld.
 //
 // Pipeline per CTA: warp-specialised roles (weight builders, TMA producer,
-// MMA issuer) exchange stages of two angles through a ring of four shared
-// buffers guarded by mbarriers, so weight building, copies and MMAs overlap.
+// MMA issuer) exchange stages of two angles through rings of shared buffers
+// guarded by mbarriers, so weight building, copies and MMAs overlap.
 // Every mbarrier wait is bounded by a clock budget; on timeout the kernel
 // records kErrTimeout, every role stops, the issued MMAs are drained (bounded)
 // and the tensor memory is freed.
@@ -37,15 +40,19 @@
 namespace tcp {
 namespace {
 
-constexpr int kTcM = 128;          // voxels per tile (16 x 8)
+constexpr int kTcM = 128;          // voxels per MMA (16 x 8)
+constexpr int kTcH = 2;            // MMAs (accumulators) per tile: 16 x 16 voxels
 constexpr int kTcK = 32;           // detector samples per angle window
 constexpr int kTcRowBytes = 64;    // one K-major row of 32 x 16-bit
-constexpr int kTcAngleA = kTcM * kTcRowBytes;  // 8 KB of weights per angle
+constexpr int kTcHalfA = kTcM * kTcRowBytes;   // 8 KB of weights per half
+constexpr int kTcAngleA = kTcH * kTcHalfA;     // 16 KB of weights per angle
+constexpr int kTcBuilders = 4 * kTcH;          // builder warps (one voxel row per thread)
+constexpr int kTcThreads = 32 * (kTcBuilders + 2);
 constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
 
 struct TcArgs {
   int nz, ntheta, ndet, n;
-  int nsub_x, nsub_y;  // 16 x 8 sub-tiles along x and y
+  int nsub_x, nsub_y;  // 16 x 16 sub-tiles along x and y
   int N;               // slices per CTA (multiple of 16, <= 256)
   void* vol;
   int vdt;
@@ -124,23 +131,25 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
   Store<TV>::put(reinterpret_cast<TV*>(base) + off, v);
 }
 
-// Warp roles (192 threads):
-//   warps 0-3  build the weight matrices A (one voxel row per thread) and, at
-//              the end, read D out of tensor memory and store the tile;
-//   warp 4     producer: tile geometry (32 angles per pass) and the TMA
+// Warp roles (320 threads):
+//   warps 0-7  build the weight matrices A (one voxel row per thread; warps
+//              4h .. 4h+3 own half h) and, at the end, read D out of tensor
+//              memory (warp w reads lanes 32 (w % 4) .. of accumulator w / 4)
+//              and store the tile;
+//   warp 8     producer: tile geometry (32 angles per pass) and the TMA
 //              copies of B;
-//   warp 5     issues the MMAs (one elected thread) and commits them.
+//   warp 9     issues the MMAs (one elected thread) and commits them.
 // A stage is two angles.  A (built in the SM, cheap) cycles through kTcNA
 // buffers; B (copied from L2, ~2 us away) through kTcNBB buffers so that
-// about 192 KB of copies are in flight.  Barriers:
+// about 160 KB of copies are in flight.  Barriers:
 //   geo_full[s % NBB] producer -> builders: geometry of stage s is written
-//   full_a  [s % NA ] builders -> MMA: A of stage s built (4 warp arrivals)
+//   full_a  [s % NA ] builders -> MMA: A of stage s built (8 warp arrivals)
 //   empty_a [s % NA ] MMA commit -> builders: A buffer free again
 //   full_b  [s % NBB] TMA -> MMA: B of stage s landed (transaction bytes)
 //   empty_b [s % NBB] MMA commit -> producer: B buffer free again
 // Stage s waits the phase (s / ring) & 1 of its ring slot.
 constexpr int kTcNA = 2;        // A stage buffers
-constexpr int kTcNBB = 6;       // B stage buffers
+constexpr int kTcNBB = 5;       // B stage buffers
 constexpr int kTcS2 = 2;        // angles per stage
 constexpr int kTcGeoRing = 64;  // geometry ring (two chunks of 32 angles)
 
@@ -171,9 +180,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// shared memory: [A: NA x S x 8 KB][B: NBB x S x N*64 B][geo ring][barriers]
+// shared memory: [A: NA x S x 16 KB][B: NBB x S x N*64 B][geo ring][barriers]
 template <class TS>
-__global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
@@ -185,16 +194,17 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   volatile int* abort = &bars->abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int per_blk = 8 * 16;
+  // CTAs run in blocks of 8 x 8 sub-tiles (128 x 128 voxels) for L2 reuse
+  const int per_blk = 8 * 8;
   const int blk = blockIdx.x / per_blk, inblk = blockIdx.x % per_blk;
   const int blocks_x = (a.nsub_x + 7) / 8;
   const int sub_x = (blk % blocks_x) * 8 + (inblk % 8);
-  const int sub_y = (blk / blocks_x) * 16 + (inblk / 8);
+  const int sub_y = (blk / blocks_x) * 8 + (inblk / 8);
   const int z0 = blockIdx.y * N;
   const bool live_tile = sub_x < a.nsub_x && sub_y < a.nsub_y;
-  const int gx = sub_x >> 1, gy = sub_y >> 2;
-  const int ox = (sub_x & 1) * 16, oy = (sub_y & 3) * 8;
-  const uint32_t tmem_cols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const int gx = sub_x >> 1, gy = sub_y >> 1;
+  const int ox = (sub_x & 1) * 16, oy = (sub_y & 1) * 16;
+  const uint32_t tmem_cols = kTcH * N <= 32 ? 32 : (kTcH * N <= 64 ? 64 : (kTcH * N <= 128 ? 128 : (kTcH * N <= 256 ? 256 : 512)));
   const int nstages = (a.ntheta + kTcS2 - 1) / kTcS2;
 
   if (tid == 0) {
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
       mbar_init(smem_u32(&bars->empty_b[i]), 1);
     }
     for (int i = 0; i < kTcNA; ++i) {
-      mbar_init(smem_u32(&bars->full_a[i]), 4);
+      mbar_init(smem_u32(&bars->full_a[i]), kTcBuilders);
       mbar_init(smem_u32(&bars->empty_a[i]), 1);
     }
     mbar_init(smem_u32(&bars->done), 1);
@@ -224,7 +234,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   int mma_stages = 0;  // MMA thread: stages whose MMAs were issued
 
   if (live_tile) {
-    if (warp == 4) {
+    if (warp == kTcBuilders) {
       // ---- producer.  Ring slot th % 64 of chunk c (angles 32c .. 32c+31)
       // is rewritten only after empty_b of stage 16c - kTcNBB completed, which
       // is after the builders finished every stage of chunk c - 2.
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
           if (th < a.ntheta) {
             const TileOrigin o = tile_origin(gx, gy, a.half_n, a.center, a.trig[th]);
             const float lo = o.f0 + fminf((float)ox * o.c, (float)(ox + 15) * o.c) +
-                             fminf((float)oy * o.s, (float)(oy + 7) * o.s);
+                             fminf((float)oy * o.s, (float)(oy + 15) * o.s);
             const int jl = o.i0 + (int)floorf(lo) - 1;
             const int j0 = jl >= 0 ? (jl & ~7) : -((-jl + 7) & ~7);
             TcGeoP g;
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
         }
         __syncwarp();
       }
-    } else if (warp == 5) {
+    } else if (warp == kTcBuilders + 1) {
       // ---- MMA issuer
       if (lane == 0) {
         for (int s = 0; s < nstages; ++s) {
@@ -275,8 +285,11 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
             const uint32_t aa = smem_u32(Abuf + (ia * kTcS2 + t) * kTcAngleA);
             const uint32_t bb = smem_u32(Bbuf + (ib * kTcS2 + t) * bBytes);
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-              mma_f16(tmem_d, sw64_desc(aa + 32 * kk), sw64_desc(bb + 32 * kk), a.idesc, (s | t | kk) ? 1u : 0u);
+            for (int h = 0; h < kTcH; ++h)
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk)
+                mma_f16(tmem_d + (uint32_t)(h * N), sw64_desc(aa + h * kTcHalfA + 32 * kk), sw64_desc(bb + 32 * kk),
+                        a.idesc, (s | t | kk) ? 1u : 0u);
           }
           mma_commit(smem_u32(&bars->empty_a[ia]));
           mma_commit(smem_u32(&bars->empty_b[ib]));
@@ -287,9 +300,10 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
       }
       __syncwarp();
     } else {
-      // ---- builders: one voxel row of A per thread
-      const float fdx = (float)(ox + (tid & 15)), fdy = (float)(oy + (tid >> 4));
-      const int swz = (tid & 7) >> 1;
+      // ---- builders: one voxel row of A per thread; warps 4h .. 4h+3 build half h
+      const int h = warp >> 2, m = tid & (kTcM - 1);
+      const float fdx = (float)(ox + (m & 15)), fdy = (float)(oy + 8 * h + (m >> 4));
+      const int swz = (m & 7) >> 1;
       for (int s = 0; s < nstages; ++s) {
         const int ia = s % kTcNA, ib = s % kTcNBB;
         if (!wait_or_abort(smem_u32(&bars->geo_full[ib]), (s / kTcNBB) & 1, abort, a.err)) break;
@@ -305,7 +319,8 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
             atomicOr(a.err, kErrBpWindow);
             idx = 0;
           }
-          unsigned char* row = Abuf + (ia * kTcS2 + t) * kTcAngleA + (tid >> 3) * 512 + (tid & 7) * kTcRowBytes;
+          unsigned char* row =
+              Abuf + (ia * kTcS2 + t) * kTcAngleA + h * kTcHalfA + (m >> 3) * 512 + (m & 7) * kTcRowBytes;
 #pragma unroll
           for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
           const int k1 = idx + 1;
@@ -321,16 +336,17 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
 
   // ---- epilogue (builder warps): wait for the last MMAs, read D, store
   __syncthreads();
-  if (live_tile && warp < 4) {
+  if (live_tile && warp < kTcBuilders) {
     bool ok = !*abort && wait_or_abort(smem_u32(&bars->done), 0, abort, a.err);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      const int m = tid;  // TMEM lane = voxel row; warp w owns lanes 32w..32w+31
-      const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + (m >> 4);
+      // TMEM lane = voxel row of a half; warp w reads lanes 32 (w % 4) .. of half w / 4
+      const int h = warp >> 2, m = tid & (kTcM - 1);
+      const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + 8 * h + (m >> 4);
       const bool inside = ix < a.n && iy < a.n;
       for (int c0 = 0; c0 < N; c0 += 16) {
         uint32_t r[16];
-        const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem_d + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * N + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
             "%14, %15}, [%16];"
@@ -356,7 +372,7 @@ __global__ void __launch_bounds__(192, 1) k_backproject_tc(const __grid_constant
   }
   // On an abort, MMAs already issued may still run: wait (bounded) for them
   // before the tensor memory is released.
-  if (live_tile && warp == 5 && lane == 0 && *abort && mma_stages > 0) {
+  if (live_tile && warp == kTcBuilders + 1 && lane == 0 && *abort && mma_stages > 0) {
     const long long t0 = clock64();
     while (!mbar_try(smem_u32(&bars->done), 0) && clock64() - t0 < kTcBudget) {
     }
@@ -422,11 +438,9 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   a.ntheta = nt;
   a.ndet = nd;
   a.n = n;
-  a.nsub_x = (n + 15) / 16;
-  a.nsub_y = (n + 7) / 8;
-  // sub-tiles are taken inside whole 32 x 32 canonical tiles
+  // 16 x 16 sub-tiles are taken inside whole 32 x 32 canonical tiles
   a.nsub_x = ((n + kTile - 1) / kTile) * 2;
-  a.nsub_y = ((n + kTile - 1) / kTile) * 4;
+  a.nsub_y = ((n + kTile - 1) / kTile) * 2;
   a.N = N;
   a.vol = vol.p;
   a.vdt = vol.dtype;
@@ -445,10 +459,10 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   void (*k)(const CUtensorMap, TcArgs) =
       sino.dtype == TCP_F16 ? k_backproject_tc<__half> : k_backproject_tc<__nv_bfloat16>;
   TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 15) / 16;
-  dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 16), (unsigned)((nz + N - 1) / N));
+  const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 7) / 8;
+  dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 8), (unsigned)((nz + N - 1) / N));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");
-  k<<<grid, 192, smem, st>>>(map, a);
+  k<<<grid, kTcThreads, smem, st>>>(map, a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
 }
