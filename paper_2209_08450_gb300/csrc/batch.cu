@@ -355,7 +355,10 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
   TCP_CUDA_TRY(cudaEventCreate(&e1));
   tcp_status s = TCP_OK;
   std::vector<tcp_bp_config> cands(std::begin(kCandidates), std::end(kCandidates));
-  if (sino->dtype == TCP_F16 || sino->dtype == TCP_BF16) cands.push_back(tcp_bp_config{8, 16, 4, 1});
+  if (sino->dtype == TCP_F16 || sino->dtype == TCP_BF16) {
+    cands.push_back(tcp_bp_config{8, 2, 4, 1});
+    cands.push_back(tcp_bp_config{8, 1, 4, 1});
+  }
   for (const tcp_bp_config& c : cands) {
     if ((s = tcp_set_backproject_config(&c)) != TCP_OK) break;
     if ((s = tcp_backproject(sino, theta, center, vol, stream)) != TCP_OK) break;  // warm-up

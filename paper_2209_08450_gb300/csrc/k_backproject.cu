@@ -515,6 +515,7 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
 
 bool valid_bp_config(const tcp_bp_config& c) {
   if (c.kernel != 0 && c.kernel != 1) return false;
+  if (c.kernel == 1) return true;  // theta_stage 1 or 2 picks the stage size; the rest is ignored
   return pick<float, float>(c, false).direct != nullptr;
 }
 
@@ -559,7 +560,7 @@ tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double c
                               const tcp_bp_config& cfg, cudaStream_t st, float scale) {
   if (cfg.kernel == 1 && tc_eligible(sino)) {
     if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
-    return launch_backproject_tc(sino, trig, center, vol, scale, st);
+    return launch_backproject_tc(sino, trig, center, vol, scale, cfg.theta_stage, st);
   }
   const KernPair kp = pick_all(sino.dtype, vol.dtype, cfg, checked_mode());
   Kern k = kp.direct;

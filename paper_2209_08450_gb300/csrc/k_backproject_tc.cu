@@ -49,6 +49,7 @@ constexpr int kTcAngleA = kTcH * kTcHalfA;     // 16 KB of weights per angle
 constexpr int kTcBuilders = 4 * kTcH;          // builder warps (one voxel row per thread)
 constexpr int kTcThreads = 32 * (kTcBuilders + 2);
 constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
+constexpr size_t kTcSmemLimit = 232448;        // opt-in shared memory per block
 
 struct TcArgs {
   int nz, ntheta, ndet, n;
@@ -63,6 +64,7 @@ struct TcArgs {
   uint32_t idesc;
   uint32_t* err;
   int check;
+  int na, nbb;  // A and B ring depths (stages)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -139,19 +141,25 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
 //   warp 8     producer: tile geometry (32 angles per pass) and the TMA
 //              copies of B;
 //   warp 9     issues the MMAs (one elected thread) and commits them.
-// A stage is two angles.  A (built in the SM, cheap) cycles through kTcNA
-// buffers; B (copied from L2, ~2 us away) through kTcNBB buffers so that
-// about 160 KB of copies are in flight.  Barriers:
+// A stage is S angles (1 or 2).  A (built in the SM, cheap) cycles through NA
+// buffers; B (copied from L2, microseconds away) through NBB buffers, as many
+// as the remaining shared memory holds, so that up to ~180 KB of copies are
+// in flight.  Each cross-role hand-off costs the MMA thread a wake-up, so a
+// stage has one barrier for "ready" and one for "consumed":
 //   geo_full[s % NBB] producer -> builders: geometry of stage s is written
-//   full_a  [s % NA ] builders -> MMA: A of stage s built (8 warp arrivals)
-//   empty_a [s % NA ] MMA commit -> builders: A buffer free again
-//   full_b  [s % NBB] TMA -> MMA: B of stage s landed (transaction bytes)
-//   empty_b [s % NBB] MMA commit -> producer: B buffer free again
-// Stage s waits the phase (s / ring) & 1 of its ring slot.
-constexpr int kTcNA = 2;        // A stage buffers
-constexpr int kTcNBB = 5;       // B stage buffers
-constexpr int kTcS2 = 2;        // angles per stage
+//   full    [s % NBB] builders (8 warp arrivals) + producer (expect_tx and the
+//                     TMA bytes) -> MMA: A and B of stage s are in place
+//   empty   [s % NBB] MMA commit -> producer (B slot s % NBB free) and
+//                     builders (A slot s % NA free once stage s - NA is
+//                     consumed; NA <= NBB)
+// Stage s waits the phase (s / NBB) & 1 of its ring slot.
+constexpr int kTcMaxNA = 4;     // A stage buffers (at most)
+constexpr int kTcMaxNBB = 32;   // B stage buffers (at most)
 constexpr int kTcGeoRing = 64;  // geometry ring (two chunks of 32 angles)
+// The geometry of chunk c overwrites that of chunk c - 2 once empty of
+// stage c * 32 / S - NBB has completed; the builders are then done with
+// every stage up to there, which covers chunk c - 2 if NBB <= 32 / S + 1.
+__host__ __device__ constexpr int tc_max_nbb(int S) { return 32 / S < kTcMaxNBB ? 32 / S : kTcMaxNBB; }
 
 struct TcGeoP {  // packed geometry of one angle (16 bytes)
   int bj;        // low 16 bits: i0 - j0, high 16 bits: j0 (both signed)
@@ -159,7 +167,7 @@ struct TcGeoP {  // packed geometry of one angle (16 bytes)
 };
 
 struct TcBars {
-  uint64_t geo_full[kTcNBB], full_b[kTcNBB], empty_b[kTcNBB], full_a[kTcNA], empty_a[kTcNA], done;
+  uint64_t geo_full[kTcMaxNBB], full[kTcMaxNBB], empty[kTcMaxNBB], done;
   uint32_t tmem;
   int abort;
 };
@@ -181,15 +189,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 // shared memory: [A: NA x S x 16 KB][B: NBB x S x N*64 B][geo ring][barriers]
-template <class TS>
+template <class TS, int kTcS2>
 __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int N = a.N;
   const int bBytes = N * kTcRowBytes;  // B bytes per angle
   unsigned char* Abuf = smem;
-  unsigned char* Bbuf = smem + kTcNA * kTcS2 * kTcAngleA;
-  TcGeoP* geo = reinterpret_cast<TcGeoP*>(Bbuf + kTcNBB * kTcS2 * bBytes);  // angle th -> geo[th % 64]
+  const int NA = a.na, NBB = a.nbb;  // ring depths (stages)
+  unsigned char* Bbuf = smem + NA * kTcS2 * kTcAngleA;
+  TcGeoP* geo = reinterpret_cast<TcGeoP*>(Bbuf + NBB * kTcS2 * bBytes);  // angle th -> geo[th % 64]
   TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcGeoRing);
   volatile int* abort = &bars->abort;
 
@@ -209,14 +218,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
 
   if (tid == 0) {
     bars->abort = 0;
-    for (int i = 0; i < kTcNBB; ++i) {
+    for (int i = 0; i < NBB; ++i) {
       mbar_init(smem_u32(&bars->geo_full[i]), 1);
-      mbar_init(smem_u32(&bars->full_b[i]), 1);
-      mbar_init(smem_u32(&bars->empty_b[i]), 1);
-    }
-    for (int i = 0; i < kTcNA; ++i) {
-      mbar_init(smem_u32(&bars->full_a[i]), kTcBuilders);
-      mbar_init(smem_u32(&bars->empty_a[i]), 1);
+      mbar_init(smem_u32(&bars->full[i]), kTcBuilders + 1);
+      mbar_init(smem_u32(&bars->empty[i]), 1);
     }
     mbar_init(smem_u32(&bars->done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -236,12 +241,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   if (live_tile) {
     if (warp == kTcBuilders) {
       // ---- producer.  Ring slot th % 64 of chunk c (angles 32c .. 32c+31)
-      // is rewritten only after empty_b of stage 16c - kTcNBB completed, which
-      // is after the builders finished every stage of chunk c - 2.
+      // is rewritten only after empty of stage 32c / S - NBB completed,
+      // which is after the builders finished every stage of chunk c - 2.
       constexpr int kStagesPerChunk = 32 / kTcS2;
+      int ib = 0;
+      uint32_t ph = 0;  // phase of slot ib for this pass over the ring
       for (int s = 0; s < nstages; ++s) {
-        const int ib = s % kTcNBB, kb = s / kTcNBB;
-        if (s >= kTcNBB && !wait_or_abort(smem_u32(&bars->empty_b[ib]), (kb - 1) & 1, abort, a.err)) break;
+        if (s >= NBB && !wait_or_abort(smem_u32(&bars->empty[ib]), ph ^ 1u, abort, a.err)) break;
         if (s % kStagesPerChunk == 0) {
           const int th = s * kTcS2 + lane;
           if (th < a.ntheta) {
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
         const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         if (lane == 0) {
           mbar_arrive(smem_u32(&bars->geo_full[ib]));
-          const uint32_t fb = smem_u32(&bars->full_b[ib]);
+          const uint32_t fb = smem_u32(&bars->full[ib]);
           mbar_expect_tx(fb, (uint32_t)(nt * bBytes));
           for (int t = 0; t < nt; ++t) {
             const int th = s * kTcS2 + t;
@@ -271,29 +277,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
           }
         }
         __syncwarp();
+        if (++ib == NBB) {
+          ib = 0;
+          ph ^= 1u;
+        }
       }
     } else if (warp == kTcBuilders + 1) {
-      // ---- MMA issuer
+      // ---- MMA issuer.  One thread issues every MMA, so its own instruction
+      // count per MMA bounds the tensor pipe: the descriptors are built once
+      // and advanced by adding byte offsets / 16 to their start-address
+      // field, and consecutive MMAs alternate between the two accumulators so
+      // that no MMA waits for the previous one's accumulation.
       if (lane == 0) {
+        const uint64_t dA0 = sw64_desc(smem_u32(Abuf)), dB0 = sw64_desc(smem_u32(Bbuf));
+        const uint32_t bStage = (uint32_t)(kTcS2 * bBytes) >> 4, bAngle = (uint32_t)bBytes >> 4;
+        int ia = 0, ib = 0;
+        uint32_t ph = 0;
         for (int s = 0; s < nstages; ++s) {
-          const int ia = s % kTcNA, ib = s % kTcNBB;
-          if (!wait_or_abort(smem_u32(&bars->full_a[ia]), (s / kTcNA) & 1, abort, a.err)) break;
-          if (!wait_or_abort(smem_u32(&bars->full_b[ib]), (s / kTcNBB) & 1, abort, a.err)) break;
+          if (!wait_or_abort(smem_u32(&bars->full[ib]), ph, abort, a.err)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int nt = min(kTcS2, a.ntheta - s * kTcS2);
-          for (int t = 0; t < nt; ++t) {
-            const uint32_t aa = smem_u32(Abuf + (ia * kTcS2 + t) * kTcAngleA);
-            const uint32_t bb = smem_u32(Bbuf + (ib * kTcS2 + t) * bBytes);
+          const uint64_t dA = dA0 + (uint64_t)((uint32_t)(ia * kTcS2 * kTcAngleA) >> 4);
+          const uint64_t dB = dB0 + (uint64_t)((uint32_t)ib * bStage);
 #pragma unroll
-            for (int h = 0; h < kTcH; ++h)
+          for (int t = 0; t < kTcS2; ++t) {
+            if (t < nt) {
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk)
-                mma_f16(tmem_d + (uint32_t)(h * N), sw64_desc(aa + h * kTcHalfA + 32 * kk), sw64_desc(bb + 32 * kk),
-                        a.idesc, (s | t | kk) ? 1u : 0u);
+#pragma unroll
+                for (int h = 0; h < kTcH; ++h)
+                  mma_f16(tmem_d + (uint32_t)(h * N), dA + (uint32_t)((t * kTcAngleA + h * kTcHalfA + 32 * kk) >> 4),
+                          dB + (uint32_t)(t * bAngle + ((32 * kk) >> 4)), a.idesc, (s | t | kk) ? 1u : 0u);
+            }
           }
-          mma_commit(smem_u32(&bars->empty_a[ia]));
-          mma_commit(smem_u32(&bars->empty_b[ib]));
+          mma_commit(smem_u32(&bars->empty[ib]));
           ++mma_stages;
+          if (++ia == NA) ia = 0;
+          if (++ib == NBB) {
+            ib = 0;
+            ph ^= 1u;
+          }
         }
         // every issued MMA completes before `done` arrives
         mma_commit(smem_u32(&bars->done));
@@ -304,10 +327,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
       const int h = warp >> 2, m = tid & (kTcM - 1);
       const float fdx = (float)(ox + (m & 15)), fdy = (float)(oy + 8 * h + (m >> 4));
       const int swz = (m & 7) >> 1;
+      int ia = 0, ib = 0, ie = NBB - NA;  // ie: ring slot of stage s - NA
+      uint32_t ph = 0, phe = 1;           // phases of slots ib and ie
       for (int s = 0; s < nstages; ++s) {
-        const int ia = s % kTcNA, ib = s % kTcNBB;
-        if (!wait_or_abort(smem_u32(&bars->geo_full[ib]), (s / kTcNBB) & 1, abort, a.err)) break;
-        if (s >= kTcNA && !wait_or_abort(smem_u32(&bars->empty_a[ia]), (s / kTcNA - 1) & 1, abort, a.err)) break;
+        if (!wait_or_abort(smem_u32(&bars->geo_full[ib]), ph, abort, a.err)) break;
+        if (s >= NA && !wait_or_abort(smem_u32(&bars->empty[ie]), phe, abort, a.err)) break;
         const int nt = min(kTcS2, a.ntheta - s * kTcS2);
         for (int t = 0; t < nt; ++t) {
           const TcGeoP g = geo[(s * kTcS2 + t) % kTcGeoRing];
@@ -329,7 +353,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars->full_a[ia]));
+        if (lane == 0) mbar_arrive(smem_u32(&bars->full[ib]));
+        if (++ia == NA) ia = 0;
+        if (++ib == NBB) {
+          ib = 0;
+          ph ^= 1u;
+        }
+        if (++ie == NBB) {
+          ie = 0;
+          phe ^= 1u;
+        }
       }
     }
   }
@@ -399,9 +432,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t tc_smem_bytes(int N) {
-  return 1024 + (size_t)kTcNA * kTcS2 * kTcAngleA + (size_t)kTcNBB * kTcS2 * N * kTcRowBytes +
-         (size_t)kTcGeoRing * sizeof(TcGeoP) + sizeof(TcBars);
+size_t tc_smem_bytes(int N, int S, int na, int nbb) {
+  return 1024 + (size_t)na * S * kTcAngleA + (size_t)nbb * S * N * kTcRowBytes + (size_t)kTcGeoRing * sizeof(TcGeoP) +
+         sizeof(TcBars);
+}
+
+// Ring depths for N slices and S angles per stage: NA = 3 (S = 1) or 2
+// (S = 2) weight buffers, then as many B buffers as fit (at most the
+// geometry ring's bound).
+void tc_rings(int N, int S, int* na, int* nbb) {
+  *na = S == 1 ? 3 : 2;
+  const size_t fixed = tc_smem_bytes(N, S, *na, 0);
+  const size_t per = (size_t)S * N * kTcRowBytes;
+  const size_t avail = kTcSmemLimit > fixed ? kTcSmemLimit - fixed : 0;
+  *nbb = (int)std::min<size_t>((size_t)tc_max_nbb(S), avail / per);
+  if (*na > *nbb) *na = *nbb;  // the builders wait on the empty barrier of stage s - NA
 }
 
 int tc_slices(int64_t nz) {
@@ -418,7 +463,7 @@ bool tc_eligible(const View3& sino) {
 }
 
 tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                                 float scale, cudaStream_t st) {
+                                 float scale, int theta_stage, cudaStream_t st) {
   if (!tc_eligible(sino)) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: sinogram not eligible");
   const int nz = (int)sino.d0, nt = (int)sino.d1, nd = (int)sino.d2, n = (int)vol.d1;
   if (nz == 0 || n == 0) return TCP_OK;
@@ -455,9 +500,13 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   a.err = device_error_word();
   a.check = checked_mode() ? 1 : 0;
-  const size_t smem = tc_smem_bytes(N);
+  const int S = theta_stage == 1 ? 1 : 2;
+  tc_rings(N, S, &a.na, &a.nbb);
+  if (a.nbb < 2) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
+  const size_t smem = tc_smem_bytes(N, S, a.na, a.nbb);
   void (*k)(const CUtensorMap, TcArgs) =
-      sino.dtype == TCP_F16 ? k_backproject_tc<__half> : k_backproject_tc<__nv_bfloat16>;
+      sino.dtype == TCP_F16 ? (S == 1 ? k_backproject_tc<__half, 1> : k_backproject_tc<__half, 2>)
+                            : (S == 1 ? k_backproject_tc<__nv_bfloat16, 1> : k_backproject_tc<__nv_bfloat16, 2>);
   TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 7) / 8;
   dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 8), (unsigned)((nz + N - 1) / N));

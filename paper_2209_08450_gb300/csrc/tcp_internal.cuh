@@ -174,7 +174,7 @@ struct BpWork {
 
 bool tc_eligible(const View3& sino);
 tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                                 float scale, cudaStream_t st);
+                                 float scale, int theta_stage, cudaStream_t st);
 
 BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol, float scale = 1.0f);
 int bp_threads(const tcp_bp_config& c);

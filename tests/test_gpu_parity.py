@@ -347,29 +347,35 @@ def test_fbp_fp16_many_angles_keeps_filtered_values_in_range():
 
 # ------------------------------------------------- tensor-core backprojector --
 
+@pytest.mark.parametrize("stage", [1, 2])
 @pytest.mark.parametrize("sdt", [torch.float16, torch.bfloat16])
 @pytest.mark.parametrize("nz,nt,nd,n,center", [
-    (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (16, 13, 64, 100, 31.7), (40, 129, 200, 160, 99.2)])
-def test_backproject_tensor_cores(sdt, nz, nt, nd, n, center):
+    (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (16, 13, 64, 100, 31.7), (40, 129, 200, 160, 99.2),
+    (1, 70, 40, 48, 19.5)])
+def test_backproject_tensor_cores(sdt, nz, nt, nd, n, center, stage):
+    # stage = angles per pipeline stage (the B ring then holds as many stages
+    # as shared memory allows); 129 angles leave a ragged last stage
     q, theta, c = _bp_case(nz, nt, nd, n, center, nz + nt + nd)
     qd = to_dev(q, sdt)
     ref = oracle.backproject(host(qd), theta, c, n)
     try:
-        tcp.set_backproject_config(8, 16, 4, kernel=1)
+        tcp.set_backproject_config(8, stage, 4, kernel=1)
         got = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
+        tcp.set_backproject_config(8, 16, 4, kernel=0)
+        cuda_core = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
     finally:
         tcp.set_backproject_config(None)
-    cuda_core = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
     assert rel(got, ref) <= 5e-3
     assert rel(got, cuda_core) <= 5e-3
 
 
-def test_backproject_tensor_cores_256_slices_and_scale():
+@pytest.mark.parametrize("stage", [1, 2])
+def test_backproject_tensor_cores_256_slices_and_scale(stage):
     # one full 256-slice block plus a ragged second block, 16-bit volume
     q, theta, c = _bp_case(300, 24, 64, 64, 32.4, 1)
     qd = to_dev(q, torch.float16)
     try:
-        tcp.set_backproject_config(8, 16, 4, kernel=1)
+        tcp.set_backproject_config(8, stage, 4, kernel=1)
         got = host(tcp.backproject(qd, theta, c, n=64, dtype=torch.float16, scale=0.5))
     finally:
         tcp.set_backproject_config(None)
