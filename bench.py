@@ -189,6 +189,45 @@ def run_reference(args):
 
 # ------------------------------------------------------- other hot-path rows --
 
+def _peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def bp_roofline(tcp, dev, dtype, nz, nt, n, ms) -> dict:
+    """Roofline of the backprojector launch that runs for this dtype and chunk.
+
+    CUDA-core kernels are bound by the shared-memory pipe: per 32
+    interpolations a warp needs 2 wavefronts (FP32 samples) or 1 (16-bit
+    sample pairs), i.e. 16 or 32 interpolations per clock per SM.  The
+    tensor-core kernel is bound by the tensor pipe: each interpolation is one
+    row x column entry of a dense 128 x 32 x N product, 32 multiply-adds =
+    64 flops (30 of the 32 weights in a row are zero), against the measured
+    dense bf16 peak (FP16 runs at the same rate)."""
+    import torch
+    pk = _peaks()
+    clk_max = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    interps = nz * n * n * nt
+    kernel = tcp.get_backproject_config(nz, nt, n, n, dtype, dtype)[3]
+    name = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}[dtype]
+    if kernel == 1:
+        peak = float(pk.get("bf16_tflops", 1900.0))
+        ach = interps * 64 / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" % name,
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "ms_per_launch": ms, "interps_per_launch": interps, "ginterp_s": interps / (ms * 1e-3) / 1e9,
+                "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; 64 MMA flops per interp"}
+    per_clk = 16 if dtype == torch.float32 else 32
+    peak = sms * per_clk * clk_max * 1e6
+    return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % name,
+            "achieved": interps / (ms * 1e-3) / 1e9, "peak": peak / 1e9, "unit": "Ginterp/s",
+            "frac": interps / (ms * 1e-3) / peak, "traffic": None, "ms_per_launch": ms, "interps_per_launch": interps,
+            "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
+
+
 def measure_rows(dev) -> dict:
     """Differentiable least-squares pair (512 x 512 x 64, 720 angles, 512-pixel
     detector) and the uneven batch (6 stacks, one persistent graph replay)."""
@@ -396,23 +435,8 @@ def main():
     nf_ms = time_kernel(lambda: tcp.normalize_filter(raw[:, z0:z0 + kc], dm[z0:z0 + kc], fm[z0:z0 + kc], center,
                                                      out=s_chunk))
     interps = kc * n * n * nt
-    clk_max = 2070.0
-    try:
-        clk_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
-    except Exception:
-        pass
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    per_clk = 16 if args.dtype == "f32" else 32  # shared-memory wavefronts: 2 (FP32) or 1 (16-bit pair) per 32 interps
-    bp_peak = sms * per_clk * clk_max * 1e6
-    roofline = {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % args.dtype, "achieved": interps / (bp_ms * 1e-3) / 1e9,
-                "peak": bp_peak / 1e9, "unit": "Ginterp/s", "frac": interps / (bp_ms * 1e-3) / bp_peak,
-                "traffic": None, "ms_per_launch": bp_ms, "interps_per_launch": interps,
-                "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
-    hbm = 6767.4
-    try:
-        hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
-    except Exception:
-        pass
+    roofline = bp_roofline(tcp, dev, hdt, kc, nt, n, bp_ms)
+    hbm = float(_peaks().get("hbm_gbs", 6767.4))
     nf_bytes = nt * kc * n * 2 + kc * nt * n * s_chunk.element_size()
     secondary = {"normalize_filter": {"bound": "hbm", "achieved": nf_bytes / (nf_ms * 1e-3) / 1e9, "peak": hbm,
                                       "unit": "GB/s", "frac": nf_bytes / (nf_ms * 1e-3) / 1e9 / hbm,
@@ -426,7 +450,15 @@ def main():
         vv = torch.empty((nz, n, n), dtype=dt, device=dev)
         vms = run_steps(dt, args.variant_steps, 1, vv)
         variants[name] = {"value": world * nz * n * n / (vms * 1e-3) / 1e9, "ms_per_step": vms,
-                          "speedup_vs_headline": ms / vms}
+                          "speedup_vs_headline": ms / vms, "chunk_nz": chunk_for(dt)}
+        # the variant's backprojector alone, on one filtered chunk of its own launch shape
+        vc = min(chunk_for(dt), nz)
+        vz = max(0, min(z0, nz - vc))
+        sv = torch.empty((vc, nt, n), dtype=dt, device=dev)
+        tcp.normalize_filter(raw[:, vz:vz + vc], dm[vz:vz + vc], fm[vz:vz + vc], center, out=sv)
+        vms_k = time_kernel(lambda: tcp.backproject(sv, theta, n / 2.0, out=vv[:vc]))
+        variants[name]["roofline"] = bp_roofline(tcp, dev, dt, vc, nt, n, vms_k)
+        del sv
         if rank == 0 and zs:
             variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
         del vv

@@ -182,9 +182,12 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
   const uint64_t twkey = ((uint64_t)(uint32_t)dev << 32) | (uint64_t)npad;
   auto tit = g_tw.find(twkey);
   if (tit == g_tw.end()) {
-    std::vector<float2> tw((size_t)npad);
-    for (int64_t m = 0; m < npad; ++m) {
-      const double ang = -2.0 * M_PI * (double)m / (double)npad;
+    // two-level table: 64 low powers, then the powers of W^64
+    const int64_t nhi = std::max<int64_t>(1, npad / 64);
+    std::vector<float2> tw((size_t)(64 + nhi));
+    for (int64_t m = 0; m < 64 + nhi; ++m) {
+      const double e = m < 64 ? (double)m : 64.0 * (double)(m - 64);
+      const double ang = -2.0 * M_PI * e / (double)npad;
       tw[(size_t)m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
     float2* d = nullptr;

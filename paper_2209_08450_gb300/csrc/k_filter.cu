@@ -122,8 +122,15 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
 // stride-16 stores of the first radix-16 pass fall in distinct banks.
 __device__ __forceinline__ int pi16(int i) { return i + (i >> 4); }
 
+// W^m (forward sign) from the two-level table in shared memory: entry m % 64
+// times entry 64 + m / 64, both rounded from FP64 (about 1.5 ulp).
+__device__ __forceinline__ float2 tw2(const float2* tw, int m) { return cmul(tw[m & 63], tw[64 + (m >> 6)]); }
+
 // Stockham pass of radix R: in -> out, sub-transform size Ns, by the gs
-// threads of one group (group-local index gt).
+// threads of one group (group-local index gt).  The R - 1 twiddles W^(r k
+// step) of a butterfly: for R = 16 the powers r = 1, 2, 4, 8 come from the
+// table and the others are products of at most three of them; for smaller R
+// every power comes from the table.
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int N, int Ns, const float2* tw,
                                               int gt, int gs) {
@@ -135,11 +142,27 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
     for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
     const int k = b & (Ns - 1);
     if (Ns > 1) {
+      float2 w[R];
+      const int m1 = k * step;
+      if constexpr (R == 16) {
+        w[1] = tw2(tw, m1);
+        w[2] = tw2(tw, 2 * m1);
+        w[4] = tw2(tw, 4 * m1);
+        w[8] = tw2(tw, 8 * m1);
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[r] = tw2(tw, r * m1);
+      }
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(tw + r * k * step);
-        if (INV) w.y = -w.y;
-        v[r] = cmul(v[r], w);
+        if (INV) w[r].y = -w[r].y;
+        v[r] = cmul(v[r], w[r]);
       }
     }
     dft<R, INV>(v);
@@ -189,8 +212,9 @@ struct FiltArgs {
   int nd, npad, log2n, left;
   int gs;           // threads per row pair
   int pad_zero;
+  int vec4;         // raw rows and means allow 4-sample vector loads
   const float2* resp;
-  const float2* tw;
+  const float2* tw;  // two-level twiddle table (global; copied to shared memory)
 };
 
 template <bool RAW, class TIn>
@@ -213,7 +237,11 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
   const int G = blockDim.x / gs;
   const int g = threadIdx.x / gs, gt = threadIdx.x - g * gs;
   const int plen = a.npad + a.npad / 16;  // padded buffer length
-  float2* bufA = smem + (size_t)g * 2 * plen;
+  // [two-level twiddle table][G x (bufA, bufB)]
+  const int ntw = 64 + max(1, a.npad / 64);
+  float2* tw = smem;
+  for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = __ldg(a.tw + i);
+  float2* bufA = smem + ntw + (size_t)g * 2 * plen;
   float2* bufB = bufA + plen;
   const int64_t npairs = (a.rows + 1) / 2;
   for (int64_t p0 = (int64_t)blockIdx.x * G; p0 < npairs; p0 += (int64_t)gridDim.x * G) {
@@ -224,12 +252,51 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
     const int64_t z0 = r0 / a.d1, t0 = r0 - z0 * a.d1;
     const int64_t z1 = has1 ? r1 / a.d1 : z0, t1 = has1 ? r1 - z1 * a.d1 : t0;
     if (active) {
-      // real samples (unrolled so that several loads are in flight)
+      if constexpr (RAW) {
+        // uint16 projections: 4 samples per load where the rows allow it;
+        // the two rows of a pair share one slice (and its dark/flat means)
+        // unless the pair straddles two slices
+        const uint16_t* ra = reinterpret_cast<const uint16_t*>(a.src) + t0 * a.s0 + z0 * a.s1;
+        const uint16_t* rb = reinterpret_cast<const uint16_t*>(a.src) + t1 * a.s0 + z1 * a.s1;
+        const float* d0 = a.dark + z0 * a.dm;
+        const float* f0 = a.flat + z0 * a.fm;
+        const float* d1 = a.dark + z1 * a.dm;
+        const float* f1 = a.flat + z1 * a.fm;
+        const bool vec = a.vec4;
+        const int nd4 = vec ? a.nd / 4 : 0;
+#pragma unroll 2
+        for (int q = gt; q < nd4; q += gs) {
+          const uint2 ua = __ldg(reinterpret_cast<const uint2*>(ra) + q);
+          const uint2 ub = has1 ? __ldg(reinterpret_cast<const uint2*>(rb) + q) : make_uint2(0, 0);
+          const float4 da = __ldg(reinterpret_cast<const float4*>(d0) + q);
+          const float4 fa = __ldg(reinterpret_cast<const float4*>(f0) + q);
+          float4 db = da, fb = fa;
+          if (has1 && z1 != z0) {
+            db = __ldg(reinterpret_cast<const float4*>(d1) + q);
+            fb = __ldg(reinterpret_cast<const float4*>(f1) + q);
+          }
+          const float va[4] = {(float)(ua.x & 0xffff), (float)(ua.x >> 16), (float)(ua.y & 0xffff), (float)(ua.y >> 16)};
+          const float vb[4] = {(float)(ub.x & 0xffff), (float)(ub.x >> 16), (float)(ub.y & 0xffff), (float)(ub.y >> 16)};
+          const float dA[4] = {da.x, da.y, da.z, da.w}, fA[4] = {fa.x, fa.y, fa.z, fa.w};
+          const float dB[4] = {db.x, db.y, db.z, db.w}, fB[4] = {fb.x, fb.y, fb.z, fb.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            bufA[pi16(a.left + 4 * q + e)] =
+                make_float2(neglog_ratio(va[e], dA[e], fA[e]), has1 ? neglog_ratio(vb[e], dB[e], fB[e]) : 0.f);
+        }
+        for (int j = 4 * nd4 + gt; j < a.nd; j += gs) {
+          const float re = neglog_ratio((float)__ldg(ra + j), __ldg(d0 + j), __ldg(f0 + j));
+          const float im = has1 ? neglog_ratio((float)__ldg(rb + j), __ldg(d1 + j), __ldg(f1 + j)) : 0.f;
+          bufA[pi16(a.left + j)] = make_float2(re, im);
+        }
+      } else {
+        // real samples (unrolled so that several loads are in flight)
 #pragma unroll 4
-      for (int j = gt; j < a.nd; j += gs) {
-        const float re = load_sample<RAW, TIn>(a, z0, t0, j);
-        const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
-        bufA[pi16(a.left + j)] = make_float2(re, im);
+        for (int j = gt; j < a.nd; j += gs) {
+          const float re = load_sample<RAW, TIn>(a, z0, t0, j);
+          const float im = has1 ? load_sample<RAW, TIn>(a, z1, t1, j) : 0.f;
+          bufA[pi16(a.left + j)] = make_float2(re, im);
+        }
       }
       // padding: zeros or the edge samples (each thread evaluates the edges once)
       float2 lo = make_float2(0.f, 0.f), hi = lo;
@@ -245,7 +312,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       }
     }
     __syncthreads();
-    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, a.tw, gt, gs, active);
+    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, tw, gt, gs, active);
     const int half = a.npad / 2;
     if (active) {
       for (int k = gt; k < a.npad; k += gs) {
@@ -255,7 +322,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       }
     }
     __syncthreads();
-    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, a.tw, gt, gs, active);
+    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, tw, gt, gs, active);
     if (active) {
       TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
       TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
@@ -291,7 +358,8 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
   a.gs = std::max(32, std::min(256, a.npad / 16));
   const int threads = 256;
-  const size_t smem = (size_t)(threads / a.gs) * 2 * (size_t)(a.npad + a.npad / 16) * sizeof(float2);
+  const size_t smem = ((size_t)(threads / a.gs) * 2 * (size_t)(a.npad + a.npad / 16) + 64 + std::max(1, a.npad / 64)) *
+                      sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
@@ -307,7 +375,7 @@ tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_
     auto it = grid_cache.find(key);
     if (it == grid_cache.end()) {
       TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(2 * (8192 + 512) * sizeof(float2))));
+                                        (int)((2 * (8192 + 512) + 64 + 128) * sizeof(float2))));
       int per_sm = 1, sms = 0;
       TCP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
       TCP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -335,6 +403,7 @@ tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode,
   a.t1 = sino.s1;
   a.dark = a.flat = nullptr;
   a.dm = a.fm = 0;
+  a.vec4 = 0;
   a.d1 = (int)sino.d1;
   a.rows = sino.d0 * sino.d1;
   a.nd = (int)sino.d2;
@@ -365,6 +434,9 @@ tcp_status launch_normalize_filter(const View3& raw, const View3& dark, const Vi
   a.d1 = (int)sino.d1;
   a.rows = sino.d0 * sino.d1;
   a.nd = (int)sino.d2;
+  // 8-byte raw loads and 16-byte mean loads need aligned row starts
+  a.vec4 = ((uintptr_t)raw.p % 8 == 0) && (raw.s0 % 4 == 0) && (raw.s1 % 4 == 0) && ((uintptr_t)dark.p % 16 == 0) &&
+           ((uintptr_t)flat.p % 16 == 0) && (dark.s1 % 4 == 0) && (flat.s1 % 4 == 0);
   return run(pick_out<true, uint16_t>(sino.dtype), a, ft, pad_mode, st);
 }
 

@@ -117,7 +117,10 @@ tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out);
 
 struct FilterTable {
   const float2* response = nullptr;  // npad/2+1 complex factors (incl. 1/npad)
-  const float2* twiddle = nullptr;   // npad twiddles exp(-2 pi i m / npad)
+  // Two-level twiddles: [0, 64): exp(-2 pi i l / npad), l < 64; then
+  // [64, 64 + max(1, npad / 64)): exp(-2 pi i 64 h / npad).  W^m is the
+  // product of entries m % 64 and 64 + m / 64.
+  const float2* twiddle = nullptr;
   int npad = 0;
 };
 // weight multiplies the response (pi/N_theta for FBP; any value > 0).
