@@ -172,30 +172,152 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
   }
 }
 
-// Transform the data in `a` (scratch `b`); returns the buffer with the result.
-// Radix-16 passes while 16 divides the remaining length, then one pass of 8,
-// 4 or 2 for the remainder.  Every thread of the block takes part in the
-// barriers; groups without a row pair (active == false) skip the arithmetic.
-template <bool INV>
-__device__ float2* fft(float2* a, float2* b, int N, int log2N, const float2* tw, int gt, int gs, bool active) {
-  int Ns = 1;
-  int rem = log2N;
-  while (rem > 0) {
-    const int lg = rem >= 4 ? 4 : rem;
-    if (active) {
-      if (lg == 4) stockham_pass<16, INV>(a, b, N, Ns, tw, gt, gs);
-      else if (lg == 3) stockham_pass<8, INV>(a, b, N, Ns, tw, gt, gs);
-      else if (lg == 2) stockham_pass<4, INV>(a, b, N, Ns, tw, gt, gs);
-      else stockham_pass<2, INV>(a, b, N, Ns, tw, gt, gs);
+// Response factor for frequency index k (Hermitian: F[N - k] = conj F[k]).
+__device__ __forceinline__ float2 response_at(const float2* resp, int k, int N) {
+  const int half = N >> 1;
+  float2 F = __ldg(resp + (k <= half ? k : N - k));
+  if (k > half) F.y = -F.y;
+  return F;
+}
+
+// The forward transform's last pass (radix R, Ns = N / R), the response and
+// the inverse transform's first pass (radix R, Ns = 1) in registers: the
+// forward butterfly b produces X[b + r N/R], which are exactly the inputs of
+// inverse butterfly b, so the spectrum never returns to shared memory.
+template <int R>
+__device__ __forceinline__ void fused_turn(const float2* in, float2* out, int N, const float2* tw, const float2* resp,
+                                           int gt, int gs) {
+  const int nb = N / R;
+  for (int b = gt; b < nb; b += gs) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
+    if (nb > 1) {  // forward twiddles W^(r b), step 1
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw2(tw, r * b));
     }
+    dft<R, false>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = cmul(v[r], response_at(resp, b + r * nb, N));
+    dft<R, true>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[pi16(b * R + r)] = v[r];
+  }
+}
+
+// The inverse transform's last pass (radix 16, Ns = N / 16) with the result
+// stored straight to the two output rows: butterfly b yields y[b + r N/16].
+template <class TOut>
+__device__ __forceinline__ void last_to_rows(const float2* in, int N, const float2* tw, int gt, int gs, int left,
+                                             int nd, TOut* o0, TOut* o1, bool has1) {
+  constexpr int R = 16;
+  const int nb = N / R;
+  for (int b = gt; b < nb; b += gs) {
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
+    float2 w[R];
+    w[1] = tw2(tw, b);
+    w[2] = tw2(tw, 2 * b);
+    w[4] = tw2(tw, 4 * b);
+    w[8] = tw2(tw, 8 * b);
+    w[3] = cmul(w[1], w[2]);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      w[r].y = -w[r].y;
+      v[r] = cmul(v[r], w[r]);
+    }
+    dft<R, true>(v);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int j = b + r * nb - left;
+      if (j >= 0 && j < nd) {
+        Store<TOut>::put(o0 + j, v[r].x);
+        if (has1) Store<TOut>::put(o1 + j, v[r].y);
+      }
+    }
+  }
+}
+
+// Transforms of N <= 16: one butterfly holds the whole row.
+template <int R, class TOut>
+__device__ __forceinline__ void single_pass(const float2* in, const float2* resp, int gt, int left, int nd, TOut* o0,
+                                            TOut* o1, bool has1) {
+  if (gt != 0) return;
+  float2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = in[pi16(r)];
+  dft<R, false>(v);
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = cmul(v[r], response_at(resp, r, R));
+  dft<R, true>(v);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j = r - left;
+    if (j >= 0 && j < nd) {
+      Store<TOut>::put(o0 + j, v[r].x);
+      if (has1) Store<TOut>::put(o1 + j, v[r].y);
+    }
+  }
+}
+
+// Filter the row pair held in `a` (padded, N = 2^log2N): forward transform
+// with radices 16, ..., 16, Rl (Rl = 2^(log2N mod 4), or 16), the inverse
+// with the same radices reversed so that its first pass meets the forward
+// last pass in registers, and its last pass writes the rows.  Every thread of
+// the block takes part in the barriers; groups without a row pair (active ==
+// false) skip the arithmetic.  On return the shared buffers may be reused
+// after a barrier.
+template <class TOut>
+__device__ void filter_pair(float2* a, float2* b, int N, int log2N, const float2* tw, const float2* resp, int gt,
+                            int gs, bool active, int left, int nd, TOut* o0, TOut* o1, bool has1) {
+  if (log2N <= 4) {
+    if (active) {
+      if (log2N == 4) single_pass<16>(a, resp, gt, left, nd, o0, o1, has1);
+      else if (log2N == 3) single_pass<8>(a, resp, gt, left, nd, o0, o1, has1);
+      else if (log2N == 2) single_pass<4>(a, resp, gt, left, nd, o0, o1, has1);
+      else single_pass<2>(a, resp, gt, left, nd, o0, o1, has1);
+    }
+    return;
+  }
+  const int rl = (log2N & 3) ? (log2N & 3) : 4;  // log2 of the last forward radix
+  const int n16 = (log2N - rl) / 4;             // radix-16 passes on each side
+  int Ns = 1;
+  for (int i = 0; i < n16; ++i) {
+    if (active) stockham_pass<16, false>(a, b, N, Ns, tw, gt, gs);
     __syncthreads();
     float2* t = a;
     a = b;
     b = t;
-    Ns <<= lg;
-    rem -= lg;
+    Ns <<= 4;
   }
-  return a;
+  if (active) {
+    if (rl == 4) fused_turn<16>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 3) fused_turn<8>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 2) fused_turn<4>(a, b, N, tw, resp, gt, gs);
+    else fused_turn<2>(a, b, N, tw, resp, gt, gs);
+  }
+  __syncthreads();
+  {
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  Ns = 1 << rl;
+  for (int i = 0; i + 1 < n16; ++i) {
+    if (active) stockham_pass<16, true>(a, b, N, Ns, tw, gt, gs);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns <<= 4;
+  }
+  if (active) last_to_rows<TOut>(a, N, tw, gt, gs, left, nd, o0, o1, has1);
 }
 
 struct FiltArgs {
@@ -312,26 +434,9 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
       }
     }
     __syncthreads();
-    float2* x = fft<false>(bufA, bufB, a.npad, a.log2n, tw, gt, gs, active);
-    const int half = a.npad / 2;
-    if (active) {
-      for (int k = gt; k < a.npad; k += gs) {
-        float2 F = __ldg(a.resp + (k <= half ? k : a.npad - k));
-        if (k > half) F.y = -F.y;
-        x[pi16(k)] = cmul(x[pi16(k)], F);
-      }
-    }
-    __syncthreads();
-    float2* y = fft<true>(x, x == bufA ? bufB : bufA, a.npad, a.log2n, tw, gt, gs, active);
-    if (active) {
-      TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
-      TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
-      for (int j = gt; j < a.nd; j += gs) {
-        const float2 v = y[pi16(a.left + j)];
-        Store<TOut>::put(o0 + j, v.x);
-        if (has1) Store<TOut>::put(o1 + j, v.y);
-      }
-    }
+    TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
+    TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
+    filter_pair<TOut>(bufA, bufB, a.npad, a.log2n, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1);
     __syncthreads();
   }
 }
