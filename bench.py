@@ -196,33 +196,49 @@ def _peaks() -> dict:
         return {}
 
 
-def bp_roofline(tcp, dev, dtype, nz, nt, n, ms) -> dict:
-    """Roofline of the backprojector launch that runs for this dtype and chunk.
+# Reconstruction paths: volume dtype, sinogram storage (None: the library's
+# choice), default chunk.  "f32" is FP32 volumes from FP16 hi/lo sinogram pairs
+# (tensor cores, FP32-accurate), "f32_cuda" FP32 sinograms on the CUDA cores.
+PATHS = {
+    "f32": ("float32", None, 256),
+    "f16": ("float16", None, 256),
+    "bf16": ("bfloat16", None, 256),
+    "f32_cuda": ("float32", "float32", 32),
+}
+
+
+def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
+    """Roofline of the backprojector launch of this path and chunk.
 
     CUDA-core kernels are bound by the shared-memory pipe: per 32
     interpolations a warp needs 2 wavefronts (FP32 samples) or 1 (16-bit
     sample pairs), i.e. 16 or 32 interpolations per clock per SM.  The
     tensor-core kernel is bound by the tensor pipe: each interpolation is one
     row x column entry of a dense 128 x 32 x N product, 32 multiply-adds =
-    64 flops (30 of the 32 weights in a row are zero), against the measured
-    dense bf16 peak (FP16 runs at the same rate)."""
+    64 flops (30 of the 32 weights in a row are zero), three such products in
+    split mode (hi*hi + hi*lo + lo*hi), against the measured dense bf16 peak
+    (FP16 runs at the same rate)."""
     import torch
     pk = _peaks()
     clk_max = float(pk.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     interps = nz * n * n * nt
-    kernel = tcp.get_backproject_config(nz, nt, n, n, dtype, dtype)[3]
-    name = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}[dtype]
+    vdt, sdt, _ = PATHS[path]
+    split = path == "f32"
+    sd = "f16x2" if split else getattr(torch, sdt or vdt)
+    kernel = tcp.get_backproject_config(nz, nt, n, n, sd, getattr(torch, vdt))[3]
     if kernel == 1:
+        fl = 192 if split else 64
         peak = float(pk.get("bf16_tflops", 1900.0))
-        ach = interps * 64 / (ms * 1e-3) / 1e12
-        return {"bound": "tensor", "kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" % name,
+        ach = interps * fl / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" %
+                ("FP16 hi/lo pairs, 3 products" if split else path),
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "ms_per_launch": ms, "interps_per_launch": interps, "ginterp_s": interps / (ms * 1e-3) / 1e9,
-                "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; 64 MMA flops per interp"}
-    per_clk = 16 if dtype == torch.float32 else 32
+                "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; %d MMA flops per interp" % fl}
+    per_clk = 16 if (sdt or vdt) == "float32" else 32
     peak = sms * per_clk * clk_max * 1e6
-    return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % name,
+    return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
             "achieved": interps / (ms * 1e-3) / 1e9, "peak": peak / 1e9, "unit": "Ginterp/s",
             "frac": interps / (ms * 1e-3) / peak, "traffic": None, "ms_per_launch": ms, "interps_per_launch": interps,
             "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
@@ -322,10 +338,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=0, help="slices (default: size); a small case of the same launches")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"], help="storage of the headline path")
-    ap.add_argument("--chunk", type=int, default=32, help="slices per chunk for FP32")
-    ap.add_argument("--chunk16", type=int, default=256, help="slices per chunk for 16-bit storage")
-    ap.add_argument("--variants", default="f32,f16,bf16")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "f32_cuda"],
+                    help="headline path (f32: FP32 volume from FP16 hi/lo sinogram pairs on the tensor cores)")
+    ap.add_argument("--chunk", type=int, default=0, help="slices per chunk (0: the path's default)")
+    ap.add_argument("--variants", default="f32,f16,bf16,f32_cuda")
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=4)
@@ -361,17 +377,24 @@ def main():
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     raw_bytes = raw.numel() * 2
-    hdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
+    def vdt_of(path):
+        return getattr(torch, PATHS[path][0])
 
-    def chunk_for(dtype):  # FP32: --chunk; 16-bit: --chunk16 (the tensor-core backprojector's N)
-        return args.chunk if dtype == torch.float32 else args.chunk16
-    nchunks = (nz + chunk_for(hdt) - 1) // chunk_for(hdt)
+    def sdt_of(path):
+        return None if PATHS[path][1] is None else getattr(torch, PATHS[path][1])
 
-    def run_steps(dtype, steps, warmup, out):
+    def chunk_for(path):
+        return args.chunk or PATHS[path][2]
+    hp = args.dtype
+    hdt = vdt_of(hp)
+    nchunks = (nz + chunk_for(hp) - 1) // chunk_for(hp)
+
+    def run_steps(path, steps, warmup, out):
         stream = torch.cuda.current_stream()
 
         def step():
-            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(dtype), stream=stream)
+            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(path), sino_dtype=sdt_of(path),
+                    stream=stream)
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
@@ -388,7 +411,7 @@ def main():
     # ---- headline: FP32 storage and arithmetic (unless --dtype says otherwise)
     vol = torch.empty((nz, n, n), dtype=hdt, device=dev)
     with ClockSampler(local) as clk:
-        ms = run_steps(hdt, args.steps, args.warmup, vol)
+        ms = run_steps(hp, args.steps, args.warmup, vol)
     clocks = clk.summary()
     value = world * nz * n * n / (ms * 1e-3) / 1e9
 
@@ -413,12 +436,7 @@ def main():
     par = {args.dtype: parity(vol, zs)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
-    kc = min(chunk_for(hdt), nz)
-    s_chunk = torch.empty((kc, nt, n), dtype=hdt, device=dev)
-    v_chunk = vol[:kc]
     dm, fm = tcp.frame_mean(dark), tcp.frame_mean(flat)
-    z0 = max(0, nz // 2 - kc)
-    tcp.normalize_filter(raw[:, z0:z0 + kc], dm[z0:z0 + kc], fm[z0:z0 + kc], center, out=s_chunk)
 
     def time_kernel(fn, reps=5):
         fn()
@@ -431,34 +449,49 @@ def main():
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    bp_ms = time_kernel(lambda: tcp.backproject(s_chunk, theta, n / 2.0, out=v_chunk))
-    nf_ms = time_kernel(lambda: tcp.normalize_filter(raw[:, z0:z0 + kc], dm[z0:z0 + kc], fm[z0:z0 + kc], center,
-                                                     out=s_chunk))
+    def path_kernels(path, out_vol):
+        """(backprojector ms, fused normalise+filter ms, filter bytes) on one
+        chunk, with the sinogram in the form the path's pipeline stores."""
+        c = min(chunk_for(path), nz)
+        zc = max(0, nz // 2 - c)
+        vdt, sdt = vdt_of(path), sdt_of(path)
+        if sdt is None:  # scaled storage: ramp x 2^10, pi/ntheta/2^10 at the voxel store
+            sd = "f16x2" if vdt == torch.float32 else vdt
+            w, sc = 1024.0, np.pi / nt / 1024.0
+        else:
+            sd, w, sc = sdt, None, 1.0
+        nf = lambda: tcp.normalize_filter(raw[:, zc:zc + c], dm[zc:zc + c], fm[zc:zc + c], center, dtype=sd,
+                                          weight=w)
+        sino = nf()
+        ms_bp = time_kernel(lambda: tcp.backproject(sino, theta, n / 2.0, out=out_vol[:c], scale=sc))
+        holder = {}
+
+        def nf_into():
+            holder["s"] = tcp.normalize_filter(raw[:, zc:zc + c], dm[zc:zc + c], fm[zc:zc + c], center,
+                                               out=sino, weight=w)
+        ms_nf = time_kernel(nf_into)
+        nbytes = nt * c * n * 2 + sino.numel() * sino.element_size()
+        del sino, holder
+        return c, ms_bp, ms_nf, nbytes
+
+    kc, bp_ms, nf_ms, nf_bytes = path_kernels(hp, vol)
     interps = kc * n * n * nt
-    roofline = bp_roofline(tcp, dev, hdt, kc, nt, n, bp_ms)
+    roofline = bp_roofline(tcp, dev, hp, kc, nt, n, bp_ms)
     hbm = float(_peaks().get("hbm_gbs", 6767.4))
-    nf_bytes = nt * kc * n * 2 + kc * nt * n * s_chunk.element_size()
     secondary = {"normalize_filter": {"bound": "hbm", "achieved": nf_bytes / (nf_ms * 1e-3) / 1e9, "peak": hbm,
                                       "unit": "GB/s", "frac": nf_bytes / (nf_ms * 1e-3) / 1e9 / hbm,
                                       "ms_per_launch": nf_ms}}
-    del s_chunk
 
-    # ---- 16-bit storage variants (FP32 accumulation)
+    # ---- other paths: 16-bit storage, FP32 sinograms on the CUDA cores
     variants = {}
-    for name in [v for v in args.variants.split(",") if v and v != args.dtype]:
-        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[name]
-        vv = torch.empty((nz, n, n), dtype=dt, device=dev)
-        vms = run_steps(dt, args.variant_steps, 1, vv)
+    for name in [v for v in args.variants.split(",") if v and v != hp]:
+        vv = torch.empty((nz, n, n), dtype=vdt_of(name), device=dev)
+        vms = run_steps(name, args.variant_steps, 1, vv)
         variants[name] = {"value": world * nz * n * n / (vms * 1e-3) / 1e9, "ms_per_step": vms,
-                          "speedup_vs_headline": ms / vms, "chunk_nz": chunk_for(dt)}
-        # the variant's backprojector alone, on one filtered chunk of its own launch shape
-        vc = min(chunk_for(dt), nz)
-        vz = max(0, min(z0, nz - vc))
-        sv = torch.empty((vc, nt, n), dtype=dt, device=dev)
-        tcp.normalize_filter(raw[:, vz:vz + vc], dm[vz:vz + vc], fm[vz:vz + vc], center, out=sv)
-        vms_k = time_kernel(lambda: tcp.backproject(sv, theta, n / 2.0, out=vv[:vc]))
-        variants[name]["roofline"] = bp_roofline(tcp, dev, dt, vc, nt, n, vms_k)
-        del sv
+                          "speedup_vs_headline": ms / vms, "chunk_nz": chunk_for(name),
+                          "sino_storage": "f16x2" if name == "f32" else (PATHS[name][1] or PATHS[name][0])}
+        vc, vms_k, _, _ = path_kernels(name, vv)
+        variants[name]["roofline"] = bp_roofline(tcp, dev, name, vc, nt, n, vms_k)
         if rank == 0 and zs:
             variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
         del vv
@@ -476,7 +509,8 @@ def main():
         stream = torch.cuda.current_stream()
 
         def e2e_step():
-            tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=chunk_for(hdt), stream=stream)
+            tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=chunk_for(hp), sino_dtype=sdt_of(hp),
+                    stream=stream)
         e2e_step()
         torch.cuda.synchronize()
         barrier(world, local)
@@ -508,14 +542,16 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": "GVoxel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": args.dtype, "data": DATA,
+            "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": "f32" if hp.startswith("f32") else hp,
+            "path": hp, "data": DATA,
             "config": {"workload": "%dx%d^2 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
-                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, chunk_for(hdt)),
-                       "n": n, "nz": nz, "ntheta": nt, "chunk_nz": chunk_for(hdt),
+                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, chunk_for(hp)),
+                       "n": n, "nz": nz, "ntheta": nt, "chunk_nz": chunk_for(hp),
+                       "sino_storage": "f16x2" if hp == "f32" else (PATHS[hp][1] or PATHS[hp][0]),
                        "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-            "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f16": 5e-3, "bf16": 5e-3},
+            "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f32_cuda": 1e-5, "f16": 5e-3, "bf16": 5e-3},
             "variants": variants, "rows": rows, "input_generation_s": t_gen,
         }
         print(json.dumps(out), flush=True)

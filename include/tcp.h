@@ -74,7 +74,17 @@ typedef enum {
   TCP_ERR_ALIAS = 10        /* input and output overlap where they must not */
 } tcp_status;
 
-typedef enum { TCP_U16 = 0, TCP_F16 = 1, TCP_BF16 = 2, TCP_F32 = 3 } tcp_dtype;
+/* TCP_F16X2: an FP32 value v kept as two FP16 planes, hi = fp16(v) and
+ * lo = fp16(v - hi), so that |v - hi - lo| <= 2^-22 |v| while lo is a normal
+ * FP16 number (|v| >= 2^-3; below that the error is at most 2^-25 absolute).
+ * A tensor of this dtype is 4-d [2][nz][ntheta][ndet] FP16: plane 0 = hi,
+ * plane 1 = lo, stride[0] = distance between the planes.  Only the fused
+ * normalise + filter writes it and only the backprojector reads it; products
+ * hi*hi + hi*lo + lo*hi of the split samples and split weights, accumulated in
+ * FP32 on the tensor cores, reproduce the FP32 backprojection.  Scale the
+ * values into [2^-3, 65504] with `weight` (the pipeline stores the ramp-
+ * filtered -log times 2^10 and applies pi/N_theta/2^10 when writing voxels). */
+typedef enum { TCP_U16 = 0, TCP_F16 = 1, TCP_BF16 = 2, TCP_F32 = 3, TCP_F16X2 = 4 } tcp_dtype;
 
 /* Filters of Sec. 2.2 ("Shepp-Logan, Parzen or other").  Every ramp is the
  * band-limited Ram-Lak response on the padded period; SHEPP multiplies it by
@@ -181,8 +191,9 @@ tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_
  * after filtering only (rounding the unfiltered sinogram to BF16 loses
  * accuracy to the ramp's removal of its low-frequency content, Sec. 2.1).
  * raw: U16 [ntheta][nz][ndet]; dark, flat: F32 means [nz][ndet] or U16 frames
- * [nf][nz][ndet]; sino: F32/F16/BF16 [nz][ntheta][ndet], must not overlap raw.
- * ndet <= 4096. */
+ * [nf][nz][ndet]; sino: F32/F16/BF16 [nz][ntheta][ndet] or F16X2
+ * [2][nz][ntheta][ndet] (hi and lo FP16 planes of the FP32 result), must not
+ * overlap raw.  ndet <= 4096. */
 tcp_status tcp_normalize_filter(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
                                 tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode,
                                 void* stream);
@@ -205,7 +216,9 @@ tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark
  * linear interpolation, zero outside the detector.  The FBP weight pi/ntheta
  * belongs to tcp_filter, so this is the plain sum (the transpose of
  * tcp_project).  Output is overwritten, not accumulated.
- * sino:  F32/F16/BF16 [nz][ntheta][ndet]; theta: HOST FP64 [ntheta];
+ * sino:  F32/F16/BF16 [nz][ntheta][ndet], or F16X2 [2][nz][ntheta][ndet]
+ *        (always on the tensor cores; planes, slices and rows must start on
+ *        16-byte boundaries, else TCP_ERR_ALIGN); theta: HOST FP64 [ntheta];
  * vol:   F32/F16/BF16 [nz][n][n] (n is taken from vol), accumulation in FP32.
  * The ray coordinate is formed from an FP64 origin per 32x32 voxel tile and
  * FP32 in-tile offsets (|error| < 1e-5 px). */
@@ -231,9 +244,10 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4).
  * kernel: 0 = FP32 pipes (every dtype); 1 = tensor cores (tcgen05.mma with
  * TMEM accumulators, FP16/BF16 sinograms whose row and slice strides are
- * multiples of 8 elements; other inputs fall back to kernel 0, and the
- * other fields are ignored).  The automatic choice is kernel 1 for 16-bit
- * sinograms with at least 32 slices. */
+ * multiples of 8 elements; other inputs fall back to kernel 0; theta_stage 1
+ * or 2 sets the angles per pipeline stage, the other fields are ignored).
+ * The automatic choice is kernel 1 for 16-bit sinograms with at least 32
+ * slices.  F16X2 sinograms always use the tensor cores. */
 typedef struct {
   int32_t k_slices;
   int32_t theta_stage;
@@ -250,8 +264,10 @@ tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, 
 /* ------------------------------------------------------------- pipeline -- */
 
 typedef struct {
-  int32_t chunk_nz;     /* slices per chunk (<= 0: 256 for 16-bit sinograms, 32 for FP32) */
-  int32_t sino_dtype;   /* storage of the intermediate sinogram chunk */
+  int32_t chunk_nz;     /* slices per chunk (<= 0: 256 for 16-bit and F16X2 sinograms, 32 for FP32) */
+  int32_t sino_dtype;   /* storage of the intermediate sinogram chunk: F32, F16, BF16 or F16X2;
+                           any other value: F16X2 for an FP32 volume when ndet % 8 == 0 (else
+                           F32), the volume's dtype for 16-bit volumes */
   int32_t filter;       /* tcp_filter_kind */
   int32_t pad_mode;     /* tcp_pad_mode */
   int32_t n_buffers;    /* device ring depth, 2 or 3 (default 2) */
@@ -265,7 +281,7 @@ typedef struct {
  * a ring of device buffers while the previous chunk computes on `stream`; host
  * outputs are copied back on a third stream.  dark/flat: U16 frames or F32
  * means, on the device or the host.  The intermediate sinogram holds the
- * ramp-filtered -log times 2^10 for FP16 storage (times 1 otherwise); the
+ * ramp-filtered -log times 2^10 for FP16 and F16X2 storage (times 1 otherwise); the
  * pi/ntheta weight and the inverse storage scale are applied by the
  * backprojector, so small values never fall into the FP16 subnormal range.  Returns after queueing the work; the
  * result is complete when `stream` is.  Device buffers of the ring are taken

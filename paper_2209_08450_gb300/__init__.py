@@ -72,16 +72,22 @@ def normalize_filter(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, 
     """Fused normalise + filter: raw uint16 [theta][z][j] -> filtered sinogram
     [z][theta][j] in `dtype`, -log computed in FP32 in shared memory and the
     result rounded once (the 16-bit-safe order of the two steps).  `weight`
-    replaces the pi/ntheta factor (see backproject(scale=...))."""
+    replaces the pi/ntheta factor (see backproject(scale=...)).  dtype="f16x2"
+    returns [2][z][theta][j] float16: hi and lo planes of the FP32 result (use a
+    weight such as 1024 so that values stay above 2^-3)."""
     raw = _as_u16(raw)
     nt, nz, nd = raw.shape
     if out is None:
-        out = torch.empty((nz, nt, nd), dtype=_lib.DTYPES[dtype], device=raw.device)
+        if dtype == _lib.SPLIT:  # FP16 hi/lo planes of the FP32 result
+            out = torch.empty((2, nz, nt, nd), dtype=torch.float16, device=raw.device)
+        else:
+            out = torch.empty((nz, nt, nd), dtype=_lib.DTYPES[dtype], device=raw.device)
 
     def dd(x):
         return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
 
-    r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
+    r, d, f = _lib.desc(raw, _lib.U16), dd(dark), dd(flat)
+    o = _lib.desc(out, _lib.F16X2 if _lib.is_split(out) else None)
     _lib.call("tcp_normalize_filter_ex", _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.FILTERS[filter],
               float(center), _lib.PADS[pad], float(weight or 0.0), _lib.stream_ptr(stream))
     return out
@@ -98,13 +104,17 @@ def filter_(sino: torch.Tensor, center: float, filter: str = "shepp", pad: str =
 
 def backproject(sino: torch.Tensor, theta, center: float, n: int | None = None,
                 out: torch.Tensor | None = None, dtype=None, scale: float = 1.0, stream=None) -> torch.Tensor:
-    """LineRec backprojection sino[z][theta][j] -> vol[z][n][n]: scale x (sum over angles)."""
+    """LineRec backprojection sino[z][theta][j] -> vol[z][n][n]: scale x (sum over angles).
+    A [2][z][theta][j] float16 sinogram is an F16X2 hi/lo pair (FP32-accurate,
+    tensor cores; the default output dtype is then float32)."""
     th = _lib.theta_array(theta)
-    nz, nt, nd = sino.shape
+    split = _lib.is_split(sino)
+    nz, nt, nd = sino.shape[1:] if split else sino.shape
     if out is None:
         n = nd if n is None else n
-        out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype or sino.dtype], device=sino.device)
-    a, b = _lib.desc(sino), _lib.desc(out)
+        odt = _lib.DTYPES[dtype] if dtype is not None else (torch.float32 if split else sino.dtype)
+        out = torch.empty((nz, n, n), dtype=odt, device=sino.device)
+    a, b = _lib.desc(sino, _lib.F16X2 if split else None), _lib.desc(out)
     _lib.call("tcp_backproject_ex", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
               float(scale), _lib.stream_ptr(stream))
     return out
@@ -152,8 +162,8 @@ def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, r
 
 def get_backproject_config(nz, ntheta, ndet, n, sino_dtype=torch.float32, vol_dtype=torch.float32) -> tuple:
     c = _lib.BpConfig()
-    _lib.call("tcp_get_backproject_config", nz, ntheta, ndet, n, _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype]],
-              _lib._TORCH_DTYPE[_lib.DTYPES[vol_dtype]], ctypes.byref(c))
+    _lib.call("tcp_get_backproject_config", nz, ntheta, ndet, n, _lib.dtype_code(sino_dtype),
+              _lib.dtype_code(vol_dtype), ctypes.byref(c))
     return (c.k_slices, c.theta_stage, c.rows_per_thread, c.kernel)
 
 
@@ -181,7 +191,8 @@ def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center
 
     opts = _lib.FbpOpts()
     opts.chunk_nz = chunk_nz
-    opts.sino_dtype = _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype or out.dtype]]
+    # None: the library's choice (F16X2 pairs for FP32 volumes when ndet % 8 == 0)
+    opts.sino_dtype = -1 if sino_dtype is None else _lib.dtype_code(sino_dtype)
     opts.filter = _lib.FILTERS[filter]
     opts.pad_mode = _lib.PADS[pad]
     opts.n_buffers = n_buffers

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtcp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "tcp.h")
 
-U16, F16, BF16, F32 = 0, 1, 2, 3
+U16, F16, BF16, F32, F16X2 = 0, 1, 2, 3, 4
 FILTERS = {"shepp": 0, "parzen": 1, "ramp": 2, "none": 3}
 PADS = {"edge": 0, "zero": 1}
 
@@ -27,6 +27,19 @@ if hasattr(torch, "uint16"):
     _TORCH_DTYPE[torch.uint16] = U16
 DTYPES = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16,
           torch.float32: torch.float32, torch.float16: torch.float16, torch.bfloat16: torch.bfloat16}
+SPLIT = "f16x2"  # FP32 values as FP16 hi + lo planes: a [2][nz][ntheta][ndet] float16 tensor
+
+
+def is_split(t: torch.Tensor) -> bool:
+    """A [2][nz][ntheta][ndet] float16 tensor is an F16X2 sinogram."""
+    return t.dim() == 4 and t.dtype == torch.float16 and t.shape[0] == 2
+
+
+def dtype_code(dt) -> int:
+    """tcp_dtype code of a torch dtype or name (including "f16x2")."""
+    if dt == SPLIT:
+        return F16X2
+    return _TORCH_DTYPE[DTYPES[dt]]
 
 
 class TcpError(RuntimeError):

@@ -242,7 +242,7 @@ static tcp_status cache_clear() {
 
 static int dtype_size(int dt) {
   switch (dt) {
-    case TCP_U16: case TCP_F16: case TCP_BF16: return 2;
+    case TCP_U16: case TCP_F16: case TCP_BF16: case TCP_F16X2: return 2;
     case TCP_F32: return 4;
   }
   return 0;
@@ -318,6 +318,41 @@ static bool overlap(const tcp_tensor* a, const tcp_tensor* b) {
 }
 
 static bool is_float(int dt) { return dt == TCP_F32 || dt == TCP_F16 || dt == TCP_BF16; }
+
+// A sinogram argument: 3-d F32/F16/BF16 [nz][ntheta][ndet], or (where
+// `split_ok`) a 4-d TCP_F16X2 [2][nz][ntheta][ndet] pair of FP16 planes.
+static tcp_status check_sino(const tcp_tensor* t, const char* name, bool split_ok) {
+  if (t && t->dtype == TCP_F16X2) {
+    if (!split_ok) return fail(TCP_ERR_DTYPE, std::string(name) + ": F16X2 is accepted only by normalize_filter and backproject");
+    tcp_status s = check_tensor(t, name, 4, 4);
+    if (s != TCP_OK) return s;
+    if (t->shape[0] != 2) return fail(TCP_ERR_SHAPE, std::string(name) + ": F16X2 must be [2][nz][ntheta][ndet]");
+    const int64_t span = (t->shape[1] - 1) * t->stride[1] + (t->shape[2] - 1) * t->stride[2] + t->shape[3];
+    if (numel(t) > 0 && (t->stride[1] < 0 || t->stride[2] < 0 || t->stride[0] < span))
+      return fail(TCP_ERR_ALIGN, std::string(name) + ": F16X2 planes must not overlap (stride[0] >= one plane)");
+    return TCP_OK;
+  }
+  tcp_status s = check_tensor(t, name, 3, 3);
+  if (s != TCP_OK) return s;
+  if (!is_float(t->dtype)) return fail(TCP_ERR_DTYPE, std::string(name) + ": sino must be F32, F16 or BF16");
+  return TCP_OK;
+}
+
+// [nz][ntheta][ndet] view of a sinogram (the hi plane plus the plane offset
+// for F16X2).
+static View3 sino_view(const tcp_tensor* t) {
+  if (t->dtype != TCP_F16X2) return view3(t);
+  View3 v;
+  v.p = t->data;
+  v.dtype = TCP_F16X2;
+  v.d0 = t->shape[1];
+  v.d1 = t->shape[2];
+  v.d2 = t->shape[3];
+  v.s0 = t->stride[1];
+  v.s1 = t->stride[2];
+  v.plane = t->stride[0];
+  return v;
+}
 
 static tcp_bp_config g_bp_override{0, 0, 0, 0};
 
@@ -397,14 +432,14 @@ tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark
   if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
   if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
   if (!std::isfinite(weight)) return fail(TCP_ERR_ARG, "weight must be finite");
-  if (sino && sino->ndim == 3 && sino->shape[2] > 4096)
-    return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
   FilterTable ft;
   tcp_status s;
-  if (raw && sino && raw->ndim == 3 && sino->ndim == 3 && numel(sino) > 0 && numel(raw) > 0) {
-    if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
-    const double w = weight > 0 ? weight : M_PI / (double)sino->shape[1];
-    if ((s = get_filter_table(sino->shape[2], filter, w, center, &ft)) != TCP_OK) return s;
+  if ((s = check_sino(sino, "sino", true)) != TCP_OK) return s;
+  const View3 sv = sino_view(sino);
+  if (sv.d2 > 4096) return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
+  if (raw && raw->ndim == 3 && numel(sino) > 0 && numel(raw) > 0) {
+    const double w = weight > 0 ? weight : M_PI / (double)sv.d1;
+    if ((s = get_filter_table(sv.d2, filter, w, center, &ft)) != TCP_OK) return s;
   } else {
     ft.npad = 0;
   }
@@ -422,11 +457,11 @@ static tcp_status normalize_impl(const tcp_tensor* raw, const tcp_tensor* dark, 
   if ((s = check_tensor(raw, "raw", 3, 3)) != TCP_OK) return s;
   if ((s = check_tensor(dark, "dark", 2, 3)) != TCP_OK) return s;
   if ((s = check_tensor(flat, "flat", 2, 3)) != TCP_OK) return s;
-  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+  if ((s = check_sino(sino, "sino", ft != nullptr)) != TCP_OK) return s;
   if (raw->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "raw must be U16");
-  if (!is_float(sino->dtype)) return fail(TCP_ERR_DTYPE, "sino must be F32, F16 or BF16");
   const int64_t nt = raw->shape[0], nz = raw->shape[1], nd = raw->shape[2];
-  if (sino->shape[0] != nz || sino->shape[1] != nt || sino->shape[2] != nd)
+  const View3 sview = sino_view(sino);
+  if (sview.d0 != nz || sview.d1 != nt || sview.d2 != nd)
     return fail(TCP_ERR_SHAPE, "sino must be [nz][ntheta][ndet] of raw [ntheta][nz][ndet]");
   for (const tcp_tensor* df : {dark, flat}) {
     if (df->ndim == 2) {
@@ -464,8 +499,8 @@ static tcp_status normalize_impl(const tcp_tensor* raw, const tcp_tensor* dark, 
       fv = m;
     }
   }
-  s = ft ? launch_normalize_filter(view3(raw), dv, fv, view3(sino), *ft, pad_mode, st)
-         : launch_normalize(view3(raw), dv, fv, view3(sino), st);
+  s = ft ? launch_normalize_filter(view3(raw), dv, fv, sview, *ft, pad_mode, st)
+         : launch_normalize(view3(raw), dv, fv, sview, st);
   if (scratch) {
     cudaError_t e = cudaFreeAsync(scratch, st);
     if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
@@ -521,20 +556,21 @@ tcp_status tcp_backproject_ex(const tcp_tensor* sino, const double* theta, doubl
                               double scale, void* stream) {
   tcp_status s;
   if (!std::isfinite(scale)) return fail(TCP_ERR_ARG, "scale must be finite");
-  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
+  if ((s = check_sino(sino, "sino", true)) != TCP_OK) return s;
   if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
-  if (!is_float(sino->dtype) || !is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "sino/vol must be F32, F16 or BF16");
-  if (vol->shape[0] != sino->shape[0]) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
+  if (!is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "vol must be F32, F16 or BF16");
+  const View3 sv = sino_view(sino);
+  if (vol->shape[0] != sv.d0) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
   if (vol->shape[1] != vol->shape[2]) return fail(TCP_ERR_SHAPE, "vol slices must be square [n][n]");
   if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
-  const int64_t nt = sino->shape[1];
+  const int64_t nt = sv.d1;
   if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "theta is null");
   for (int64_t i = 0; i < nt; ++i)
     if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "theta must be finite");
   if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (numel(vol) == 0) return TCP_OK;
-  if (nt == 0 || sino->shape[2] == 0) {  // no rays: the sum is zero
+  if (nt == 0 || sv.d2 == 0) {  // no rays: the sum is zero
     for (int64_t z = 0; z < vol->shape[0]; ++z)
       TCP_CUDA_TRY(cudaMemset2DAsync((char*)vol->data + z * vol->stride[0] * dtype_size(vol->dtype),
                                      vol->stride[1] * dtype_size(vol->dtype), 0,
@@ -544,8 +580,8 @@ tcp_status tcp_backproject_ex(const tcp_tensor* sino, const double* theta, doubl
   TrigTable trig;
   if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
   tcp_bp_config cfg;
-  tcp_get_backproject_config(sino->shape[0], nt, sino->shape[2], vol->shape[1], sino->dtype, vol->dtype, &cfg);
-  return launch_backproject(view3(sino), trig, center, view3(vol), cfg, st, (float)scale);
+  tcp_get_backproject_config(sv.d0, nt, sv.d2, vol->shape[1], sino->dtype, vol->dtype, &cfg);
+  return launch_backproject(sv, trig, center, view3(vol), cfg, st, (float)scale);
 }
 
 tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {

@@ -553,12 +553,15 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
   // 16-bit sinograms with enough slices to fill the MMA's N dimension go to
   // the tensor cores (inputs whose strides do not suit TMA fall back).
   if ((sdt == TCP_F16 || sdt == TCP_BF16) && nz >= 32) c.kernel = 1;
+  if (sdt == TCP_F16X2) c.kernel = 1;  // split FP16 pairs exist only on the tensor cores
   return c;
 }
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st, float scale) {
-  if (cfg.kernel == 1 && tc_eligible(sino)) {
+  if (sino.dtype == TCP_F16X2 || (cfg.kernel == 1 && tc_eligible(sino))) {
+    if (!tc_eligible(sino))
+      return fail(TCP_ERR_ALIGN, "backproject: F16X2 sinograms need 16-byte aligned planes, slices and rows");
     if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
     return launch_backproject_tc(sino, trig, center, vol, scale, cfg.theta_stage, st);
   }

@@ -30,6 +30,18 @@
 // The ray coordinate and the weights come from the same canonical geometry as
 // the CUDA-core backprojector (FP64 tile origin + FP32 in-tile offsets), the
 // weights rounded to the sinogram's 16-bit type.
+//
+// Split mode (TCP_F16X2 sinograms, FP32 accuracy): every sample is stored as
+// FP16 hi + lo and every weight is split the same way, so each angle runs
+// three products per accumulator, A_hi B_hi + A_hi B_lo + A_lo B_hi (the
+// dropped A_lo B_lo is below 2^-22 of the term); the FP16 x FP16 products are
+// exact, but the tensor core's accumulation into TMEM does not round to
+// nearest: its error grows linearly with the number of accumulation steps
+// (measured: 1.2e-4 relative after 2048 angles).  Split mode therefore
+// accumulates segments of kTcSeg angles on the tensor cores and adds each
+// segment into FP32 running sums held in TMEM next to the accumulators, with
+// round-to-nearest FP32 adds on the CUDA cores (N <= 128 leaves room for
+// both: 2N accumulator columns + 2N sum columns).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -153,6 +165,7 @@ __device__ __forceinline__ void put(void* base, int64_t off, float v) {
 //                     builders (A slot s % NA free once stage s - NA is
 //                     consumed; NA <= NBB)
 // Stage s waits the phase (s / NBB) & 1 of its ring slot.
+constexpr int kTcSeg = 32;      // split mode: angles per tensor-core accumulation segment
 constexpr int kTcMaxNA = 4;     // A stage buffers (at most)
 constexpr int kTcMaxNBB = 32;   // B stage buffers (at most)
 constexpr int kTcGeoRing = 64;  // geometry ring (two chunks of 32 angles)
@@ -168,6 +181,7 @@ struct TcGeoP {  // packed geometry of one angle (16 bytes)
 
 struct TcBars {
   uint64_t geo_full[kTcMaxNBB], full[kTcMaxNBB], empty[kTcMaxNBB], done;
+  uint64_t seg_done, seg_free;  // split mode: segment accumulated / accumulators read
   uint32_t tmem;
   int abort;
 };
@@ -188,17 +202,41 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// shared memory: [A: NA x S x 16 KB][B: NBB x S x N*64 B][geo ring][barriers]
-template <class TS, int kTcS2>
-__global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+// 16 consecutive TMEM columns of this warp's 32 lanes (one per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+// shared memory: [A: NA x S x P x 16 KB][B: NBB x S x P x N*64 B][geo ring]
+// [barriers], P = 2 planes (hi, lo) in split mode, else 1.
+template <class TS, int kTcS2, bool SPLIT>
+__global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_constant__ CUtensorMap tmap,
+                                                                   const __grid_constant__ CUtensorMap tmap_lo,
+                                                                   TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kParts = SPLIT ? 2 : 1;
   const int N = a.N;
-  const int bBytes = N * kTcRowBytes;  // B bytes per angle
+  const int bBytes = N * kTcRowBytes;  // B bytes per angle and plane
+  const int angleB = kParts * bBytes;  // B bytes per angle
+  constexpr int angleA = kParts * kTcAngleA;
   unsigned char* Abuf = smem;
   const int NA = a.na, NBB = a.nbb;  // ring depths (stages)
-  unsigned char* Bbuf = smem + NA * kTcS2 * kTcAngleA;
-  TcGeoP* geo = reinterpret_cast<TcGeoP*>(Bbuf + NBB * kTcS2 * bBytes);  // angle th -> geo[th % 64]
+  unsigned char* Bbuf = smem + NA * kTcS2 * angleA;
+  TcGeoP* geo = reinterpret_cast<TcGeoP*>(Bbuf + NBB * kTcS2 * angleB);  // angle th -> geo[th % 64]
   TcBars* bars = reinterpret_cast<TcBars*>(geo + kTcGeoRing);
   volatile int* abort = &bars->abort;
 
@@ -213,7 +251,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   const bool live_tile = sub_x < a.nsub_x && sub_y < a.nsub_y;
   const int gx = sub_x >> 1, gy = sub_y >> 1;
   const int ox = (sub_x & 1) * 16, oy = (sub_y & 1) * 16;
-  const uint32_t tmem_cols = kTcH * N <= 32 ? 32 : (kTcH * N <= 64 ? 64 : (kTcH * N <= 128 ? 128 : (kTcH * N <= 256 ? 256 : 512)));
+  // columns: [accumulator half 0][half 1], then in split mode [sum 0][sum 1]
+  const int ncols = (SPLIT ? 2 : 1) * kTcH * N;
+  const uint32_t tmem_cols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
   const int nstages = (a.ntheta + kTcS2 - 1) / kTcS2;
 
   if (tid == 0) {
@@ -224,6 +264,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
       mbar_init(smem_u32(&bars->empty[i]), 1);
     }
     mbar_init(smem_u32(&bars->done), 1);
+    mbar_init(smem_u32(&bars->seg_done), 1);
+    mbar_init(smem_u32(&bars->seg_free), kTcBuilders);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -269,11 +311,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
         if (lane == 0) {
           mbar_arrive(smem_u32(&bars->geo_full[ib]));
           const uint32_t fb = smem_u32(&bars->full[ib]);
-          mbar_expect_tx(fb, (uint32_t)(nt * bBytes));
+          mbar_expect_tx(fb, (uint32_t)(nt * angleB));
           for (int t = 0; t < nt; ++t) {
             const int th = s * kTcS2 + t;
-            tma_load_3d(smem_u32(Bbuf + (ib * kTcS2 + t) * bBytes), &tmap, fb, geo[th % kTcGeoRing].bj >> 16, th,
-                        z0);
+            const int jb = geo[th % kTcGeoRing].bj >> 16;
+            unsigned char* dst = Bbuf + (ib * kTcS2 + t) * angleB;
+            tma_load_3d(smem_u32(dst), &tmap, fb, jb, th, z0);
+            if (SPLIT) tma_load_3d(smem_u32(dst + bBytes), &tmap_lo, fb, jb, th, z0);
           }
         }
         __syncwarp();
@@ -290,14 +334,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
       // that no MMA waits for the previous one's accumulation.
       if (lane == 0) {
         const uint64_t dA0 = sw64_desc(smem_u32(Abuf)), dB0 = sw64_desc(smem_u32(Bbuf));
-        const uint32_t bStage = (uint32_t)(kTcS2 * bBytes) >> 4, bAngle = (uint32_t)bBytes >> 4;
+        const uint32_t bStage = (uint32_t)(kTcS2 * angleB) >> 4, bAngle = (uint32_t)angleB >> 4;
+        const uint32_t bPlane = (uint32_t)bBytes >> 4;
         int ia = 0, ib = 0;
         uint32_t ph = 0;
         for (int s = 0; s < nstages; ++s) {
           if (!wait_or_abort(smem_u32(&bars->full[ib]), ph, abort, a.err)) break;
+          // split mode: a new segment overwrites the accumulators once the
+          // builders have added the previous segment into the sums
+          const bool seg0 = SPLIT ? (s % kTcSeg == 0) : (s == 0);
+          if (SPLIT && s > 0 && seg0 &&
+              !wait_or_abort(smem_u32(&bars->seg_free), (uint32_t)((s / kTcSeg - 1) & 1), abort, a.err))
+            break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int nt = min(kTcS2, a.ntheta - s * kTcS2);
-          const uint64_t dA = dA0 + (uint64_t)((uint32_t)(ia * kTcS2 * kTcAngleA) >> 4);
+          const uint64_t dA = dA0 + (uint64_t)((uint32_t)(ia * kTcS2 * angleA) >> 4);
           const uint64_t dB = dB0 + (uint64_t)((uint32_t)ib * bStage);
 #pragma unroll
           for (int t = 0; t < kTcS2; ++t) {
@@ -305,12 +356,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-                for (int h = 0; h < kTcH; ++h)
-                  mma_f16(tmem_d + (uint32_t)(h * N), dA + (uint32_t)((t * kTcAngleA + h * kTcHalfA + 32 * kk) >> 4),
-                          dB + (uint32_t)(t * bAngle + ((32 * kk) >> 4)), a.idesc, (s | t | kk) ? 1u : 0u);
+                for (int pr = 0; pr < (SPLIT ? 3 : 1); ++pr)  // (A_hi,B_hi), (A_hi,B_lo), (A_lo,B_hi)
+#pragma unroll
+                  for (int h = 0; h < kTcH; ++h)
+                    mma_f16(tmem_d + (uint32_t)(h * N),
+                            dA + (uint32_t)((t * angleA + (pr == 2 ? kTcAngleA : 0) + h * kTcHalfA + 32 * kk) >> 4),
+                            dB + (uint32_t)(t * bAngle + (pr == 1 ? bPlane : 0u) + ((32 * kk) >> 4)), a.idesc,
+                            (seg0 && (t | kk | pr) == 0) ? 0u : 1u);
             }
           }
           mma_commit(smem_u32(&bars->empty[ib]));
+          if (SPLIT && (s + 1) % kTcSeg == 0 && s + 1 < nstages) mma_commit(smem_u32(&bars->seg_done));
           ++mma_stages;
           if (++ia == NA) ia = 0;
           if (++ib == NBB) {
@@ -344,16 +400,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
             idx = 0;
           }
           unsigned char* row =
-              Abuf + (ia * kTcS2 + t) * kTcAngleA + h * kTcHalfA + (m >> 3) * 512 + (m & 7) * kTcRowBytes;
+              Abuf + (ia * kTcS2 + t) * angleA + h * kTcHalfA + (m >> 3) * 512 + (m & 7) * kTcRowBytes;
+          const int k1 = idx + 1;
+          const int o0 = (((idx >> 3) ^ swz) << 4) + (idx & 7) * 2, o1 = (((k1 >> 3) ^ swz) << 4) + (k1 & 7) * 2;
 #pragma unroll
           for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(row + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
-          const int k1 = idx + 1;
-          *reinterpret_cast<uint16_t*>(row + (((idx >> 3) ^ swz) << 4) + (idx & 7) * 2) = weight_bits<TS>(1.f - w);
-          *reinterpret_cast<uint16_t*>(row + (((k1 >> 3) ^ swz) << 4) + (k1 & 7) * 2) = weight_bits<TS>(w);
+          if (SPLIT) {
+            // FP16 hi/lo of both weights; the lo matrix sits one plane later
+            const float u = 1.f - w;
+            const __half uh = __float2half_rn(u), wh = __float2half_rn(w);
+            const __half ul = __float2half_rn(u - __half2float(uh)), wl = __float2half_rn(w - __half2float(wh));
+            unsigned char* lrow = row + kTcAngleA;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) *reinterpret_cast<uint4*>(lrow + ((c ^ swz) << 4)) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint16_t*>(row + o0) = __half_as_ushort(uh);
+            *reinterpret_cast<uint16_t*>(row + o1) = __half_as_ushort(wh);
+            *reinterpret_cast<uint16_t*>(lrow + o0) = __half_as_ushort(ul);
+            *reinterpret_cast<uint16_t*>(lrow + o1) = __half_as_ushort(wl);
+          } else {
+            *reinterpret_cast<uint16_t*>(row + o0) = weight_bits<TS>(1.f - w);
+            *reinterpret_cast<uint16_t*>(row + o1) = weight_bits<TS>(w);
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->full[ib]));
+        if (SPLIT && s > 0 && s % kTcSeg == 0) {
+          // segment k = s / kTcSeg - 1 is complete: sums (+)= accumulators,
+          // round-to-nearest FP32 on the CUDA cores
+          const int k = s / kTcSeg - 1;
+          if (!wait_or_abort(smem_u32(&bars->seg_done), (uint32_t)(k & 1), abort, a.err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+          for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t acc[16], sum[16];
+            tmem_ld16(tmem_d + lanes + (uint32_t)(h * N + c0), acc);
+            if (k > 0) tmem_ld16(tmem_d + lanes + (uint32_t)(kTcH * N + h * N + c0), sum);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              sum[q] = k > 0 ? __float_as_uint(__fadd_rn(__uint_as_float(sum[q]), __uint_as_float(acc[q]))) : acc[q];
+            tmem_st16(tmem_d + lanes + (uint32_t)(kTcH * N + h * N + c0), sum);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bars->seg_free));
+        }
         if (++ia == NA) ia = 0;
         if (++ib == NBB) {
           ib = 0;
@@ -377,15 +470,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
       const int h = warp >> 2, m = tid & (kTcM - 1);
       const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + 8 * h + (m >> 4);
       const bool inside = ix < a.n && iy < a.n;
+      // split mode: segments 0 .. nseg-2 are in the sums, the last one in the accumulators
+      const bool add_sums = SPLIT && (nstages + kTcSeg - 1) / kTcSeg > 1;
       for (int c0 = 0; c0 < N; c0 += 16) {
         uint32_t r[16];
         const uint32_t taddr = tmem_d + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * N + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
+        tmem_ld16(taddr, r);
+        if (add_sums) {
+          uint32_t sm[16];
+          tmem_ld16(taddr + (uint32_t)(kTcH * N), sm);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) r[q] = __float_as_uint(__fadd_rn(__uint_as_float(sm[q]), __uint_as_float(r[q])));
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (inside) {
 #pragma unroll
@@ -432,32 +529,33 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t tc_smem_bytes(int N, int S, int na, int nbb) {
-  return 1024 + (size_t)na * S * kTcAngleA + (size_t)nbb * S * N * kTcRowBytes + (size_t)kTcGeoRing * sizeof(TcGeoP) +
-         sizeof(TcBars);
+size_t tc_smem_bytes(int N, int S, int parts, int na, int nbb) {
+  return 1024 + (size_t)na * S * parts * kTcAngleA + (size_t)nbb * S * parts * N * kTcRowBytes +
+         (size_t)kTcGeoRing * sizeof(TcGeoP) + sizeof(TcBars);
 }
 
 // Ring depths for N slices and S angles per stage: NA = 3 (S = 1) or 2
 // (S = 2) weight buffers, then as many B buffers as fit (at most the
 // geometry ring's bound).
-void tc_rings(int N, int S, int* na, int* nbb) {
-  *na = S == 1 ? 3 : 2;
-  const size_t fixed = tc_smem_bytes(N, S, *na, 0);
-  const size_t per = (size_t)S * N * kTcRowBytes;
+void tc_rings(int N, int S, int parts, int* na, int* nbb) {
+  *na = (S == 1 && parts == 1) ? 3 : 2;
+  const size_t fixed = tc_smem_bytes(N, S, parts, *na, 0);
+  const size_t per = (size_t)S * parts * N * kTcRowBytes;
   const size_t avail = kTcSmemLimit > fixed ? kTcSmemLimit - fixed : 0;
   *nbb = (int)std::min<size_t>((size_t)tc_max_nbb(S), avail / per);
   if (*na > *nbb) *na = *nbb;  // the builders wait on the empty barrier of stage s - NA
 }
 
-int tc_slices(int64_t nz) {
+int tc_slices(int64_t nz, bool split) {
   const int64_t r = ((nz + 15) / 16) * 16;
-  return (int)std::min<int64_t>(256, std::max<int64_t>(16, r));
+  return (int)std::min<int64_t>(split ? 128 : 256, std::max<int64_t>(16, r));
 }
 
 bool tc_eligible(const View3& sino) {
-  if (sino.dtype != TCP_F16 && sino.dtype != TCP_BF16) return false;
+  if (sino.dtype != TCP_F16 && sino.dtype != TCP_BF16 && sino.dtype != TCP_F16X2) return false;
   if ((uintptr_t)sino.p % 16 != 0) return false;
   if ((sino.s1 * 2) % 16 != 0 || (sino.s0 * 2) % 16 != 0) return false;
+  if (sino.dtype == TCP_F16X2 && (sino.plane * 2) % 16 != 0) return false;
   if (sino.d1 < 1 || sino.d2 < 1 || sino.d0 < 1) return false;
   return encode_fn() != nullptr;
 }
@@ -467,17 +565,22 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   if (!tc_eligible(sino)) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: sinogram not eligible");
   const int nz = (int)sino.d0, nt = (int)sino.d1, nd = (int)sino.d2, n = (int)vol.d1;
   if (nz == 0 || n == 0) return TCP_OK;
-  const int N = tc_slices(nz);
-  CUtensorMap map;
+  const bool split = sino.dtype == TCP_F16X2;
+  const int N = tc_slices(nz, split);
+  CUtensorMap map, map_lo;
   const cuuint64_t dims[3] = {(cuuint64_t)nd, (cuuint64_t)nt, (cuuint64_t)nz};
   const cuuint64_t strides[2] = {(cuuint64_t)sino.s1 * 2, (cuuint64_t)sino.s0 * 2};
   const cuuint32_t box[3] = {(cuuint32_t)kTcK, 1u, (cuuint32_t)N};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode_fn()(&map, sino.dtype == TCP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                                 3, sino.p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(TCP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  const CUtensorMapDataType tdt = sino.dtype == TCP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  for (int pl = 0; pl < (split ? 2 : 1); ++pl) {
+    void* base = pl == 0 ? sino.p : (void*)((__half*)sino.p + sino.plane);
+    const CUresult r = encode_fn()(pl == 0 ? &map : &map_lo, tdt, 3, base, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TCP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  }
+  if (!split) map_lo = map;
   TcArgs a;
   a.nz = nz;
   a.ntheta = nt;
@@ -496,22 +599,26 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   a.half_n = 0.5 * (double)n;
   a.scale = scale;
   // instruction descriptor: D FP32, A/B F16 or BF16, K-major, N >> 3, M >> 4
-  const uint32_t fmt = sino.dtype == TCP_F16 ? 0u : 1u;
+  const uint32_t fmt = sino.dtype == TCP_BF16 ? 1u : 0u;
   a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   a.err = device_error_word();
   a.check = checked_mode() ? 1 : 0;
-  const int S = theta_stage == 1 ? 1 : 2;
-  tc_rings(N, S, &a.na, &a.nbb);
+  // split mode: one angle per stage (its A and B are twice as large)
+  const int S = (split || theta_stage == 1) ? 1 : 2;
+  const int parts = split ? 2 : 1;
+  tc_rings(N, S, parts, &a.na, &a.nbb);
   if (a.nbb < 2) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
-  const size_t smem = tc_smem_bytes(N, S, a.na, a.nbb);
-  void (*k)(const CUtensorMap, TcArgs) =
-      sino.dtype == TCP_F16 ? (S == 1 ? k_backproject_tc<__half, 1> : k_backproject_tc<__half, 2>)
-                            : (S == 1 ? k_backproject_tc<__nv_bfloat16, 1> : k_backproject_tc<__nv_bfloat16, 2>);
+  const size_t smem = tc_smem_bytes(N, S, parts, a.na, a.nbb);
+  void (*k)(const CUtensorMap, const CUtensorMap, TcArgs) =
+      split ? k_backproject_tc<__half, 1, true>
+      : sino.dtype == TCP_F16
+          ? (S == 1 ? k_backproject_tc<__half, 1, false> : k_backproject_tc<__half, 2, false>)
+          : (S == 1 ? k_backproject_tc<__nv_bfloat16, 1, false> : k_backproject_tc<__nv_bfloat16, 2, false>);
   TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 7) / 8;
   dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 8), (unsigned)((nz + N - 1) / N));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");
-  k<<<grid, kTcThreads, smem, st>>>(map, a);
+  k<<<grid, kTcThreads, smem, st>>>(map, map_lo, a);
   TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
 }

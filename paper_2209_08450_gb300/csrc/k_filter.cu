@@ -19,6 +19,7 @@
 // lose accuracy: the ramp removes its large low-frequency content and keeps
 // the rounding noise (the large-minus-small hazard of Sec. 2.1).
 #include <map>
+#include <type_traits>
 #include <mutex>
 #include <tuple>
 
@@ -172,6 +173,21 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
   }
 }
 
+// Store one filtered sample.  With `plane` != 0 (TCP_F16X2, TOut = __half) the
+// value is split: hi = fp16(v) at p[j], lo = fp16(v - hi) at p[j + plane].
+template <class TOut>
+__device__ __forceinline__ void put_sample(TOut* p, int j, float v, int64_t plane) {
+  if constexpr (std::is_same<TOut, __half>::value) {
+    if (plane) {
+      const __half hi = __float2half_rn(v);
+      p[j] = hi;
+      p[j + plane] = __float2half_rn(v - __half2float(hi));
+      return;
+    }
+  }
+  Store<TOut>::put(p + j, v);
+}
+
 // Response factor for frequency index k (Hermitian: F[N - k] = conj F[k]).
 __device__ __forceinline__ float2 response_at(const float2* resp, int k, int N) {
   const int half = N >> 1;
@@ -209,7 +225,7 @@ __device__ __forceinline__ void fused_turn(const float2* in, float2* out, int N,
 // stored straight to the two output rows: butterfly b yields y[b + r N/16].
 template <class TOut>
 __device__ __forceinline__ void last_to_rows(const float2* in, int N, const float2* tw, int gt, int gs, int left,
-                                             int nd, TOut* o0, TOut* o1, bool has1) {
+                                             int nd, TOut* o0, TOut* o1, bool has1, int64_t plane) {
   constexpr int R = 16;
   const int nb = N / R;
   for (int b = gt; b < nb; b += gs) {
@@ -237,8 +253,8 @@ __device__ __forceinline__ void last_to_rows(const float2* in, int N, const floa
     for (int r = 0; r < R; ++r) {
       const int j = b + r * nb - left;
       if (j >= 0 && j < nd) {
-        Store<TOut>::put(o0 + j, v[r].x);
-        if (has1) Store<TOut>::put(o1 + j, v[r].y);
+        put_sample<TOut>(o0, j, v[r].x, plane);
+        if (has1) put_sample<TOut>(o1, j, v[r].y, plane);
       }
     }
   }
@@ -247,7 +263,7 @@ __device__ __forceinline__ void last_to_rows(const float2* in, int N, const floa
 // Transforms of N <= 16: one butterfly holds the whole row.
 template <int R, class TOut>
 __device__ __forceinline__ void single_pass(const float2* in, const float2* resp, int gt, int left, int nd, TOut* o0,
-                                            TOut* o1, bool has1) {
+                                            TOut* o1, bool has1, int64_t plane) {
   if (gt != 0) return;
   float2 v[R];
 #pragma unroll
@@ -260,8 +276,8 @@ __device__ __forceinline__ void single_pass(const float2* in, const float2* resp
   for (int r = 0; r < R; ++r) {
     const int j = r - left;
     if (j >= 0 && j < nd) {
-      Store<TOut>::put(o0 + j, v[r].x);
-      if (has1) Store<TOut>::put(o1 + j, v[r].y);
+      put_sample<TOut>(o0, j, v[r].x, plane);
+      if (has1) put_sample<TOut>(o1, j, v[r].y, plane);
     }
   }
 }
@@ -275,13 +291,13 @@ __device__ __forceinline__ void single_pass(const float2* in, const float2* resp
 // after a barrier.
 template <class TOut>
 __device__ void filter_pair(float2* a, float2* b, int N, int log2N, const float2* tw, const float2* resp, int gt,
-                            int gs, bool active, int left, int nd, TOut* o0, TOut* o1, bool has1) {
+                            int gs, bool active, int left, int nd, TOut* o0, TOut* o1, bool has1, int64_t plane) {
   if (log2N <= 4) {
     if (active) {
-      if (log2N == 4) single_pass<16>(a, resp, gt, left, nd, o0, o1, has1);
-      else if (log2N == 3) single_pass<8>(a, resp, gt, left, nd, o0, o1, has1);
-      else if (log2N == 2) single_pass<4>(a, resp, gt, left, nd, o0, o1, has1);
-      else single_pass<2>(a, resp, gt, left, nd, o0, o1, has1);
+      if (log2N == 4) single_pass<16>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      else if (log2N == 3) single_pass<8>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      else if (log2N == 2) single_pass<4>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      else single_pass<2>(a, resp, gt, left, nd, o0, o1, has1, plane);
     }
     return;
   }
@@ -317,7 +333,7 @@ __device__ void filter_pair(float2* a, float2* b, int N, int log2N, const float2
     b = t;
     Ns <<= 4;
   }
-  if (active) last_to_rows<TOut>(a, N, tw, gt, gs, left, nd, o0, o1, has1);
+  if (active) last_to_rows<TOut>(a, N, tw, gt, gs, left, nd, o0, o1, has1, plane);
 }
 
 struct FiltArgs {
@@ -335,6 +351,7 @@ struct FiltArgs {
   int gs;           // threads per row pair
   int pad_zero;
   int vec4;         // raw rows and means allow 4-sample vector loads
+  int64_t plane;    // TCP_F16X2 output: elements from the hi to the lo plane (else 0)
   const float2* resp;
   const float2* tw;  // two-level twiddle table (global; copied to shared memory)
 };
@@ -436,7 +453,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
     __syncthreads();
     TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
     TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
-    filter_pair<TOut>(bufA, bufB, a.npad, a.log2n, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1);
+    filter_pair<TOut>(bufA, bufB, a.npad, a.log2n, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1, a.plane);
     __syncthreads();
   }
 }
@@ -447,6 +464,7 @@ void (*pick_out(int dt))(FiltArgs) {
     case TCP_F32: return k_filter<RAW, TIn, float>;
     case TCP_F16: return k_filter<RAW, TIn, __half>;
     case TCP_BF16: return k_filter<RAW, TIn, __nv_bfloat16>;
+    case TCP_F16X2: return k_filter<RAW, TIn, __half>;
   }
   return nullptr;
 }
@@ -509,6 +527,7 @@ tcp_status launch_filter(const View3& sino, const FilterTable& ft, int pad_mode,
   a.dark = a.flat = nullptr;
   a.dm = a.fm = 0;
   a.vec4 = 0;
+  a.plane = 0;
   a.d1 = (int)sino.d1;
   a.rows = sino.d0 * sino.d1;
   a.nd = (int)sino.d2;
@@ -539,6 +558,7 @@ tcp_status launch_normalize_filter(const View3& raw, const View3& dark, const Vi
   a.d1 = (int)sino.d1;
   a.rows = sino.d0 * sino.d1;
   a.nd = (int)sino.d2;
+  a.plane = sino.dtype == TCP_F16X2 ? sino.plane : 0;
   // 8-byte raw loads and 16-byte mean loads need aligned row starts
   a.vec4 = ((uintptr_t)raw.p % 8 == 0) && (raw.s0 % 4 == 0) && (raw.s1 % 4 == 0) && ((uintptr_t)dark.p % 16 == 0) &&
            ((uintptr_t)flat.p % 16 == 0) && (dark.s1 % 4 == 0) && (flat.s1 % 4 == 0);

@@ -29,7 +29,7 @@ Where where(const void* p) {
   }
 }
 
-int esize(int dt) { return dt == TCP_F32 ? 4 : 2; }
+int esize(int dt) { return (dt == TCP_F32 || dt == TCP_F16X2) ? 4 : 2; }  // F16X2: both planes
 
 // Everything created for one call; released in stream order at the end.
 struct Scope {
@@ -143,10 +143,14 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "fbp: ndet > 4096");
   tcp_fbp_opts o{};
   if (opts) o = *opts;
-  const int sdt = (o.sino_dtype == TCP_F32 || o.sino_dtype == TCP_F16 || o.sino_dtype == TCP_BF16) ? o.sino_dtype
-                                                                                                   : vol->dtype;
+  // Sinogram storage: as requested, else FP16 hi/lo pairs for an FP32 volume
+  // (FP32-accurate on the tensor cores; needs ndet % 8 == 0 for 16-byte rows,
+  // FP32 otherwise) and the volume's own type for 16-bit volumes.
+  int sdt = o.sino_dtype;
+  if (sdt != TCP_F32 && sdt != TCP_F16 && sdt != TCP_BF16 && sdt != TCP_F16X2)
+    sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 ? TCP_F16X2 : TCP_F32);
   // default chunk: 256 slices for 16-bit sinograms (the tensor-core
-  // backprojector's N), 32 otherwise
+  // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel)
   const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : (sdt == TCP_F32 ? 32 : 256);
   if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
   if (o.pad_mode != TCP_PAD_EDGE && o.pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
@@ -244,6 +248,7 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
     fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
     View3 sv;
     sv.p = sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    sv.plane = sdt == TCP_F16X2 ? cz * nt * nd : 0;
     TRY_S(launch_normalize_filter(rv, dv, fv, sv, ft, o.pad_mode, st));
     if (host_raw) {
       TCP_CUDA_TRY(cudaEventRecord(raw_free[b], st));

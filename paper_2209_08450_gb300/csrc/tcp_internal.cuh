@@ -129,7 +129,7 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
 // Storage scale of a sinogram that the library writes in `dtype` and reads
 // back itself (pipeline, batch): FP16 keeps a 2^10 headroom so that filtered
 // values stay out of the subnormal range (|filtered -log| <= 6.9 < 65504/2^10).
-inline double storage_scale(int dtype) { return dtype == TCP_F16 ? 1024.0 : 1.0; }
+inline double storage_scale(int dtype) { return (dtype == TCP_F16 || dtype == TCP_F16X2) ? 1024.0 : 1.0; }
 
 int64_t padded_length(int64_t ndet);
 
@@ -139,6 +139,7 @@ struct View3 {  // [d0][d1][d2] with element strides s0, s1 (s2 == 1)
   int dtype;
   int64_t d0, d1, d2;
   int64_t s0, s1;
+  int64_t plane = 0;  // TCP_F16X2: elements from the hi plane to the lo plane
 };
 
 tcp_status launch_frame_mean(const View3& frames, const View3& mean, cudaStream_t st);

@@ -95,6 +95,27 @@ def test_host_side_argument_checks(lib):
     assert _status(lib, "tcp_set_backproject_config", ctypes.byref(c)) == 9
 
 
+def test_split_sinogram_descriptor_checks(lib):
+    # F16X2 must be 4-d [2][nz][ntheta][ndet] with non-overlapping planes;
+    # rejected before any device work
+    raw = _t(_lib.U16, (10, 4, 32), ptr=1 << 20)
+    dark = _t(_lib.F32, (4, 32), ptr=1 << 21)
+    flat = _t(_lib.F32, (4, 32), ptr=1 << 22)
+    bad3 = _t(_lib.F16X2, (4, 10, 32), ptr=1 << 23)
+    assert _status(lib, "tcp_normalize_filter", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat),
+                   ctypes.byref(bad3), 0, 16.0, 0, None) == 2
+    three = _t(_lib.F16X2, (3, 4, 10, 32), ptr=1 << 23)
+    assert _status(lib, "tcp_normalize_filter", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat),
+                   ctypes.byref(three), 0, 16.0, 0, None) == 2
+    ovl = _t(_lib.F16X2, (2, 4, 10, 32), ptr=1 << 23)
+    ovl.stride[0] = 16  # planes overlap
+    assert _status(lib, "tcp_normalize_filter", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat),
+                   ctypes.byref(ovl), 0, 16.0, 0, None) == 4
+    pair = _t(_lib.F16X2, (2, 4, 10, 32), ptr=1 << 23)
+    assert _status(lib, "tcp_normalize", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat),
+                   ctypes.byref(pair), None) == 3  # only the fused normalise + filter writes pairs
+
+
 def test_default_config_query(lib):
     c = _lib.BpConfig()
     assert lib.tcp_get_backproject_config(64, 2048, 2048, 2048, 3, 3, ctypes.byref(c)) == 0

@@ -96,7 +96,7 @@ def test_batch_of_one_equals_fbp_and_fp32_sinogram():
     b.run()
     torch.cuda.synchronize()
     for d in ds:
-        ref = tcp.fbp(d["raw"], d["dark"], d["flat"], d["theta"], d["center"])
+        ref = tcp.fbp(d["raw"], d["dark"], d["flat"], d["theta"], d["center"], sino_dtype=torch.float32)
         torch.cuda.synchronize()
         assert torch.allclose(d["vol"], ref, rtol=0, atol=1e-6 * float(ref.abs().max()))
         _check_sampled(d, z=4, tol=1e-5)

@@ -381,3 +381,66 @@ def test_backproject_tensor_cores_256_slices_and_scale(stage):
         tcp.set_backproject_config(None)
     ref = 0.5 * oracle.backproject(host(qd), theta, c, 64)
     assert rel(got, ref) <= 5e-3
+
+
+# ------------------------------- FP32-accurate split FP16 (F16X2) sinograms --
+
+def _split(q, scale):
+    """hi = fp16(q * scale), lo = fp16(q * scale - hi) as a [2][...] tensor."""
+    v = to_dev(q) * scale
+    hi = v.half()
+    lo = (v - hi.float()).half()
+    return torch.stack([hi, lo])
+
+
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (300, 24, 64, 64, 32.4), (1, 70, 40, 48, 19.5),
+    (40, 129, 200, 160, 99.2)])
+def test_backproject_split_fp16_pairs_reach_fp32_tolerance(nz, nt, nd, n, center):
+    # three FP16 products per weight/sample pair, accumulated in FP32 on the
+    # tensor cores: held to the FP32 tolerance, not the 16-bit one
+    q, theta, c = _bp_case(nz, nt, nd, n, center, 7 * nz + nt)
+    ref = oracle.backproject(q, theta, c, n)
+    got = host(tcp.backproject(_split(q, 1024.0), theta, c, n=n, scale=1.0 / 1024.0))
+    assert rel(got, ref) <= 1e-5
+    fp32 = host(tcp.backproject(to_dev(q), theta, c, n=n))
+    assert rel(got, fp32) <= 1e-5
+
+
+def test_normalize_filter_split_planes_carry_the_fp32_result():
+    ds = synth.shepp_logan_dataset(ntheta=64, ndet=128, nz=5, center=63.2, seed=6)
+    raw, dark, flat = u16(ds.raw), u16(ds.dark), u16(ds.flat)
+    f32 = tcp.normalize_filter(raw, dark, flat, ds.center, dtype=torch.float32, weight=1024.0)
+    sp = tcp.normalize_filter(raw, dark, flat, ds.center, dtype="f16x2", weight=1024.0)
+    torch.cuda.synchronize()
+    assert sp.shape == (2, 5, 64, 128) and sp.dtype == torch.float16
+    v = f32.double()
+    pair = sp[0].double() + sp[1].double()
+    # |v - hi - lo| <= 2^-22 |v| while lo is normal (|v| >= 2^-3), else <= 2^-25
+    bound = torch.clamp(v.abs() * 2.0 ** -22, min=2.0 ** -25) * 1.01
+    assert bool(((pair - v).abs() <= bound).all())
+    assert bool((sp[0].double() == v.half().double()).all())  # hi is fp16(v)
+
+
+def test_fbp_default_fp32_volume_uses_split_pairs_and_matches_fp32_sinograms():
+    ds = synth.shepp_logan_dataset(ntheta=90, ndet=104, nz=7, center=51.6, seed=8)
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp")
+    raw, dark, flat = u16(ds.raw), u16(ds.dark), u16(ds.flat)
+    assert tcp.get_backproject_config(7, 90, 104, 104, "f16x2")[3] == 1
+    a = tcp.fbp(raw, dark, flat, ds.theta, ds.center)  # default: F16X2 chunks
+    b = tcp.fbp(raw, dark, flat, ds.theta, ds.center, sino_dtype="f16x2", chunk_nz=3)
+    c = tcp.fbp(raw, dark, flat, ds.theta, ds.center, sino_dtype=torch.float32)
+    torch.cuda.synchronize()
+    for v in (a, b, c):
+        assert rel(host(v), ref) <= 1e-5
+    # two FP32-accurate paths with different rounding orders: the FP32 tolerance
+    assert rel(host(a), host(c)) <= 1e-5
+    assert torch.equal(a, b)  # slices are independent of the chunking
+
+
+def test_split_sinogram_rejections():
+    q = torch.zeros((2, 4, 10, 36), dtype=torch.float16, device=DEV)  # rows of 72 bytes: not 16-byte aligned
+    with pytest.raises(tcp.TcpError):
+        tcp.backproject(q, np.linspace(0, np.pi, 10), 18.0, n=36)
+    with pytest.raises(tcp.TcpError):  # the in-place filter does not take pairs
+        tcp.filter_(torch.zeros((2, 4, 10, 32), dtype=torch.float16, device=DEV), 16.0)
