@@ -207,6 +207,23 @@ PATHS = {
 }
 
 
+# DRAM bytes (read + write) per backprojector launch from ncu captures of these
+# exact launch shapes (slices, angles, n) -> bytes, file under profiles/.  Set
+# an entry to None when its kernel changes.
+PROFILED_TRAFFIC = {
+    "f32": ((256, 2048, 2048), 593.1e9 + 4.31e9, "profiles/k_backproject_tc_split_f32_2048sq_256slices.md"),
+    "f16": ((256, 2048, 2048), 559.1e9 + 2.15e9, "profiles/k_backproject_tc_f16_2048sq_256slices.md"),
+    "f32_cuda": ((32, 2048, 2048), 8.09e9 + 0.53e9, "profiles/k_backproject_f32_2048sq_32slices.md"),
+}
+
+
+def _traffic(path, nz, nt, n):
+    e = PROFILED_TRAFFIC.get(path)
+    if e and e[0] == (nz, nt, n):
+        return e[1], e[2]
+    return None, None
+
+
 def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     """Roofline of the backprojector launch of this path and chunk.
 
@@ -225,6 +242,7 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     interps = nz * n * n * nt
     vdt, sdt, _ = PATHS[path]
     split = path == "f32"
+    traffic, tsrc = _traffic(path, nz, nt, n)
     sd = "f16x2" if split else getattr(torch, sdt or vdt)
     kernel = tcp.get_backproject_config(nz, nt, n, n, sd, getattr(torch, vdt))[3]
     if kernel == 1:
@@ -233,14 +251,15 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
         ach = interps * fl / (ms * 1e-3) / 1e12
         return {"bound": "tensor", "kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" %
                 ("FP16 hi/lo pairs, 3 products" if split else path),
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "ms_per_launch": ms, "interps_per_launch": interps, "ginterp_s": interps / (ms * 1e-3) / 1e9,
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                "traffic_source": tsrc, "ms_per_launch": ms, "interps_per_launch": interps, "ginterp_s": interps / (ms * 1e-3) / 1e9,
                 "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; %d MMA flops per interp" % fl}
     per_clk = 16 if (sdt or vdt) == "float32" else 32
     peak = sms * per_clk * clk_max * 1e6
     return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
             "achieved": interps / (ms * 1e-3) / 1e9, "peak": peak / 1e9, "unit": "Ginterp/s",
-            "frac": interps / (ms * 1e-3) / peak, "traffic": None, "ms_per_launch": ms, "interps_per_launch": interps,
+            "frac": interps / (ms * 1e-3) / peak, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
+            "interps_per_launch": interps,
             "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
 
 
