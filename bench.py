@@ -344,6 +344,17 @@ def measure_rows(dev) -> dict:
         "config": info["config"], "tuned_ms": info["tuned_ms"], "grid_blocks": info["grid_blocks"],
         "work_units": info["work_units"]}
     b.close()
+    del ds
+    # f2: multi-centre "try" reconstruction of one 2048^2 slice, 64 candidate axes
+    raw, dark, flat, th, c, mu = sgpu.porous_frames(2048, 2048, 2048, seed=3, device=dev, slices=np.array([1024]))
+    centers = c + 0.25 * (np.arange(64) - 32)
+    vol = torch.empty((64, 2048, 2048), dtype=torch.float32, device=dev)
+    tms = ev_time(lambda: tcp.try_centers(raw, dark, flat, th, centers, slice=0, out=vol), 3)
+    out["f2_try_centers"] = {
+        "workload": "one 2048^2 slice of the porous workload, 2048 angles, 64 candidate centres (step 0.25 px), "
+                    "FP32 volume from FP16 hi/lo pairs",
+        "ms": tms, "gvoxel_s": 64 * 2048 * 2048 / tms / 1e6}
+    del raw, dark, flat, vol
     return out
 
 

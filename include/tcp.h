@@ -290,6 +290,21 @@ tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tens
                    const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
                    void* stream);
 
+/* Multi-centre "try" reconstruction (Sec. 2.4, --reconstruction-type try):
+ * slice `slice` of the projections reconstructed about each of `ncenters`
+ * candidate rotation axes (Sec. 2.4: one image per centre, from which the
+ * axis is picked before the full reconstruction).  Each candidate's shift is
+ * applied in its own filter pass (the axis moves to ndet/2), and one
+ * backprojection launch reconstructs the stack of candidates as if they were
+ * slices.  raw: U16 [ntheta][nz][ndet], host or device; dark/flat as for
+ * tcp_fbp; theta: HOST FP64 [ntheta]; centers: HOST FP64 [ncenters];
+ * vol: DEVICE F32/F16/BF16 [ncenters][n][n], overwritten (FP32 volumes are
+ * reconstructed from FP16 hi/lo pairs when ndet % 8 == 0, as tcp_fbp does).
+ * slice outside [0, nz) or a non-finite centre: TCP_ERR_ARG. */
+tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, const tcp_tensor* dark, const tcp_tensor* flat,
+                           const double* theta, const double* centers, int64_t ncenters, tcp_tensor* vol,
+                           int32_t filter, void* stream);
+
 /* Time every instantiated backprojector configuration on these tensors (the
  * output is overwritten) and keep the fastest for later calls with the same
  * shapes and dtypes (an explicit tcp_set_backproject_config still wins).

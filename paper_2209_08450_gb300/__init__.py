@@ -203,3 +203,32 @@ def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center
 
 
 __all__.append("fbp")
+
+
+def try_centers(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, centers,
+                slice: int | None = None, n: int | None = None, out: torch.Tensor | None = None,
+                dtype=torch.float32, filter: str = "shepp", stream=None) -> torch.Tensor:
+    """Multi-centre "try" reconstruction (Sec. 2.4): slice `slice` (default the
+    middle one) reconstructed about every candidate axis in `centers`; returns
+    [len(centers)][n][n] on the device of `raw` (CUDA)."""
+    raw = _as_u16(raw)
+    nt, nz, nd = raw.shape
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
+    if slice is None:
+        slice = nz // 2
+    if out is None:
+        n = nd if n is None else n
+        out = torch.empty((c.shape[0], n, n), dtype=_lib.DTYPES[dtype], device="cuda")
+    th = _lib.theta_array(theta)
+
+    def dd(x):
+        return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
+
+    r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
+    _lib.call("tcp_try_centers", _lib.ref(r), int(slice), _lib.ref(d), _lib.ref(f), th.ctypes.data_as(ctypes.c_void_p),
+              c.ctypes.data_as(ctypes.c_void_p), int(c.shape[0]), _lib.ref(o), _lib.FILTERS[filter],
+              _lib.stream_ptr(stream))
+    return out
+
+
+__all__.append("try_centers")

@@ -295,3 +295,94 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   }
   return TCP_OK;
 }
+
+// Multi-centre "try" reconstruction (Sec. 2.4, --reconstruction-type try): one
+// slice reconstructed about every candidate rotation axis.  Each candidate's
+// shift lives in its own filter pass (the Fourier phase that moves the axis to
+// ndet/2), so the filtered rows of all candidates form a stack that ONE
+// backprojection launch reconstructs about ndet/2, candidates in place of
+// slices.
+extern "C" tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, const tcp_tensor* dark,
+                                      const tcp_tensor* flat, const double* theta, const double* centers,
+                                      int64_t ncenters, tcp_tensor* vol, int32_t filter, void* stream) {
+  if (!raw || !dark || !flat || !vol) return fail(TCP_ERR_ARG, "try_centers: null tensor");
+  if (raw->ndim != 3 || raw->dtype != TCP_U16)
+    return fail(TCP_ERR_DTYPE, "try_centers: raw must be U16 [ntheta][nz][ndet]");
+  if (vol->ndim != 3 || (vol->dtype != TCP_F32 && vol->dtype != TCP_F16 && vol->dtype != TCP_BF16))
+    return fail(TCP_ERR_DTYPE, "try_centers: vol must be F32/F16/BF16 [ncenters][n][n]");
+  const int64_t nt = raw->shape[0], nz = raw->shape[1], nd = raw->shape[2], n = vol->shape[1];
+  if (ncenters < 0 || vol->shape[0] != ncenters || vol->shape[2] != n)
+    return fail(TCP_ERR_SHAPE, "try_centers: vol must be [ncenters][n][n]");
+  if (slice < 0 || slice >= nz) return fail(TCP_ERR_ARG, "try_centers: slice outside [0, nz)");
+  if (raw->stride[2] != 1 || vol->stride[2] != 1) return fail(TCP_ERR_ALIGN, "try_centers: innermost stride must be 1");
+  for (const tcp_tensor* df : {dark, flat}) {
+    const bool ok = (df->ndim == 2 && df->dtype == TCP_F32 && df->shape[0] == nz && df->shape[1] == nd) ||
+                    (df->ndim == 3 && df->dtype == TCP_U16 && df->shape[0] >= 1 && df->shape[1] == nz &&
+                     df->shape[2] == nd);
+    if (!ok) return fail(TCP_ERR_SHAPE, "try_centers: dark/flat must be F32 [nz][ndet] or U16 [nf][nz][ndet]");
+  }
+  if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "try_centers: unknown filter");
+  if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "try_centers: ndet > 4096");
+  if (ncenters > 0 && !centers) return fail(TCP_ERR_ARG, "try_centers: centers is null");
+  for (int64_t k = 0; k < ncenters; ++k)
+    if (!std::isfinite(centers[k])) return fail(TCP_ERR_ARG, "try_centers: centers must be finite");
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "try_centers: theta is null");
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "try_centers: theta must be finite");
+  if (ncenters == 0 || n == 0) return TCP_OK;
+  if (nt == 0 || nd == 0) return fail(TCP_ERR_SHAPE, "try_centers: empty projections for a non-empty volume");
+  if (where(vol->data) != kDevice) return fail(TCP_ERR_ARG, "try_centers: vol must be device memory");
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // storage of the candidate stack: as tcp_fbp chooses for this volume dtype
+  const int sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 ? TCP_F16X2 : TCP_F32);
+  const double sscale = storage_scale(sdt);
+  TrigTable trig;
+  tcp_status s;
+  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  Scope sc;
+  sc.st = st;
+  View3 dm, fm;
+  if ((s = device_means(dark, nz, nd, sc, &dm)) != TCP_OK) return s;
+  if ((s = device_means(flat, nz, nd, sc, &fm)) != TCP_OK) return s;
+  // the slice's raw rows [ntheta][1][ndet], on the device
+  View3 rv;
+  rv.dtype = TCP_U16;
+  rv.d0 = nt; rv.d1 = 1; rv.d2 = nd;
+  if (where(raw->data) == kDevice) {
+    rv.p = (uint16_t*)raw->data + slice * raw->stride[1];
+    rv.s0 = raw->stride[0]; rv.s1 = raw->stride[1];
+  } else {
+    void* d = nullptr;
+    TRY_S(sc.alloc(&d, (size_t)nt * nd * 2));
+    TCP_CUDA_TRY(cudaMemcpy2DAsync(d, (size_t)nd * 2, (const uint16_t*)raw->data + slice * raw->stride[1],
+                                   (size_t)raw->stride[0] * 2, (size_t)nd * 2, (size_t)nt, cudaMemcpyHostToDevice, st));
+    rv.p = d; rv.s0 = nd; rv.s1 = nd;
+  }
+  View3 dv = dm, fv = fm;
+  dv.p = (float*)dm.p + slice * dm.s1; dv.d1 = 1;
+  fv.p = (float*)fm.p + slice * fm.s1; fv.d1 = 1;
+  void* sino = nullptr;
+  TRY_S(sc.alloc(&sino, (size_t)ncenters * nt * nd * esize(sdt)));
+  const int64_t plane = ncenters * nt * nd;
+  for (int64_t k = 0; k < ncenters; ++k) {
+    FilterTable ft;
+    if ((s = get_filter_table(nd, filter, sscale, centers[k], &ft)) != TCP_OK) return s;
+    View3 sv;
+    sv.dtype = sdt;
+    sv.p = (char*)sino + (size_t)k * nt * nd * (sdt == TCP_F32 ? 4 : 2);
+    sv.d0 = 1; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    sv.plane = sdt == TCP_F16X2 ? plane : 0;
+    TRY_S(launch_normalize_filter(rv, dv, fv, sv, ft, TCP_PAD_EDGE, st));
+  }
+  View3 stack;
+  stack.p = sino; stack.dtype = sdt;
+  stack.d0 = ncenters; stack.d1 = nt; stack.d2 = nd; stack.s0 = nt * nd; stack.s1 = nd;
+  stack.plane = sdt == TCP_F16X2 ? plane : 0;
+  View3 vv;
+  vv.p = vol->data; vv.dtype = vol->dtype; vv.d0 = ncenters; vv.d1 = n; vv.d2 = n;
+  vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
+  tcp_bp_config cfg;
+  tcp_get_backproject_config(ncenters, nt, nd, n, sdt, vol->dtype, &cfg);
+  return launch_backproject(stack, trig, 0.5 * (double)nd, vv, cfg, st, (float)(M_PI / (double)nt / sscale));
+}

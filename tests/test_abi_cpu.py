@@ -116,6 +116,22 @@ def test_split_sinogram_descriptor_checks(lib):
                    ctypes.byref(pair), None) == 3  # only the fused normalise + filter writes pairs
 
 
+def test_try_centers_argument_checks(lib):
+    raw = _t(_lib.U16, (10, 4, 32), ptr=1 << 20)
+    dark = _t(_lib.F32, (4, 32), ptr=1 << 21)
+    flat = _t(_lib.F32, (4, 32), ptr=1 << 22)
+    vol = _t(_lib.F32, (2, 32, 32), ptr=1 << 23)
+    th = (ctypes.c_double * 10)(*[0.1 * i for i in range(10)])
+    cs = (ctypes.c_double * 2)(16.0, 17.0)
+    bad = (ctypes.c_double * 2)(16.0, float("inf"))
+    assert _status(lib, "tcp_try_centers", ctypes.byref(raw), 4, ctypes.byref(dark), ctypes.byref(flat), th, cs, 2,
+                   ctypes.byref(vol), 0, None) == 1  # slice outside [0, nz)
+    assert _status(lib, "tcp_try_centers", ctypes.byref(raw), 1, ctypes.byref(dark), ctypes.byref(flat), th, bad, 2,
+                   ctypes.byref(vol), 0, None) == 1  # non-finite centre
+    assert _status(lib, "tcp_try_centers", ctypes.byref(raw), 1, ctypes.byref(dark), ctypes.byref(flat), th, cs, 3,
+                   ctypes.byref(vol), 0, None) == 2  # vol is not [ncenters][n][n]
+
+
 def test_default_config_query(lib):
     c = _lib.BpConfig()
     assert lib.tcp_get_backproject_config(64, 2048, 2048, 2048, 3, 3, ctypes.byref(c)) == 0
