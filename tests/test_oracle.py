@@ -67,10 +67,13 @@ def test_ramp_response_closed_form():
     s = sum(1.0 / (np.pi ** 2 * m * m) for m in (1, 3, 5, 7))
     assert abs(r[0] - (0.25 - 2 * s)) < 1e-15
     assert abs(r[-1] - (0.25 + 2 * s)) < 1e-15
-    for npad in (16, 256, 4096):
+    for npad in (16, 256, 4096, 48, 3072):  # 3 x 2^k periods of the smooth padding too
         r = oracle.filter_response("ramp", npad)
         nu = np.arange(npad // 2 + 1) / npad
         assert np.max(np.abs(r - nu)) < 1.0 / npad
+    r = oracle.filter_response("ramp", 48)
+    s = sum(1.0 / (np.pi ** 2 * m * m) for m in range(1, 24, 2))
+    assert abs(r[0] - (0.25 - 2 * s)) < 1e-15
         assert r[0] > 0
 
 
@@ -86,14 +89,15 @@ def test_window_special_values():
     assert np.all(oracle.filter_response("none", n) == 1.0)
 
 
-def _brute_filter(row, center, kind, pad, ntheta):
+def _brute_filter(row, center, kind, pad, ntheta, npad=None):
     """Brute-force reference: explicit padding, impulse response by a direct
     inverse DFT sum over the full Hermitian spectrum, then a direct circular
     convolution, then the crop."""
     nd = row.shape[0]
-    npad = 1
-    while npad < 2 * nd:
-        npad *= 2
+    if npad is None:
+        npad = 1
+        while npad < 2 * nd:
+            npad *= 2
     left = (npad - nd) // 2
     right = npad - nd - left
     if pad == "edge":
@@ -123,6 +127,28 @@ def test_filter_equals_direct_convolution(nd, center, kind, pad):
     row = rng.normal(size=nd)
     got = oracle.filter_sino(row[None, :], center, kind, pad, ntheta=7)[0]
     ref = _brute_filter(row, center, kind, pad, 7)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_smooth_padded_lengths():
+    # the smaller of the next 2^k and the next 3 * 2^k (>= 48) at or above 2 ndet
+    cases = {12: 32, 20: 48, 24: 48, 40: 96, 100: 256, 200: 512, 300: 768, 1024: 2048, 1536: 3072, 2560: 6144,
+             2048: 4096, 4096: 8192}
+    for nd, n in cases.items():
+        assert oracle.padded_length(nd, "smooth") == n, nd
+        assert oracle.padded_length(nd) == 1 << (2 * nd - 1).bit_length()
+
+
+@pytest.mark.parametrize("nd,center,kind,pad", [
+    (20, 11.25, "shepp", "edge"), (24, 12.0, "parzen", "zero"), (40, 17.6, "ramp", "edge")])
+def test_filter_on_smooth_padding_equals_direct_convolution(nd, center, kind, pad):
+    # padded lengths 48, 48 and 96 (3 x 2^k): the same definition, other period
+    rng = np.random.default_rng(nd + 1)
+    row = rng.normal(size=nd)
+    npad = oracle.padded_length(nd, "smooth")
+    assert npad % 3 == 0
+    got = oracle.filter_sino(row[None, :], center, kind, pad, ntheta=5, rule="smooth")[0]
+    ref = _brute_filter(row, center, kind, pad, 5, npad=npad)
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
