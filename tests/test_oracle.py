@@ -71,10 +71,10 @@ def test_ramp_response_closed_form():
         r = oracle.filter_response("ramp", npad)
         nu = np.arange(npad // 2 + 1) / npad
         assert np.max(np.abs(r - nu)) < 1.0 / npad
+        assert r[0] > 0
     r = oracle.filter_response("ramp", 48)
     s = sum(1.0 / (np.pi ** 2 * m * m) for m in range(1, 24, 2))
     assert abs(r[0] - (0.25 - 2 * s)) < 1e-15
-        assert r[0] > 0
 
 
 def test_window_special_values():
