@@ -32,10 +32,17 @@ def _as_u16(t: torch.Tensor) -> torch.Tensor:
     raise TypeError("raw/dark/flat frames must be uint16 (or int16 holding the same bits)")
 
 
-def padded_length(ndet: int) -> int:
+def padded_length(ndet: int, smooth: bool = False) -> int:
+    """Padded row length of the filter: the next power of two >= 2 ndet; with
+    `smooth`, the smaller of that and the next 3 * 2^k >= 2 ndet (from 48 on)."""
     n = 1
     while n < 2 * ndet:
         n *= 2
+    if smooth:
+        m = 3
+        while m < 2 * ndet or m < 48:
+            m *= 2
+        n = min(n, m)
     return n
 
 

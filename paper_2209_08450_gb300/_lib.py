@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "tcp.h")
 
 U16, F16, BF16, F32, F16X2 = 0, 1, 2, 3, 4
 FILTERS = {"shepp": 0, "parzen": 1, "ramp": 2, "none": 3}
-PADS = {"edge": 0, "zero": 1}
+PADS = {"edge": 0, "zero": 1, "edge_smooth": 2, "zero_smooth": 3}  # _smooth: 3 * 2^k padded lengths allowed
 
 _TORCH_DTYPE = {torch.int16: U16, torch.float16: F16, torch.bfloat16: BF16, torch.float32: F32}
 if hasattr(torch, "uint16"):

@@ -93,9 +93,14 @@ tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out) {
   return TCP_OK;
 }
 
-int64_t padded_length(int64_t ndet) {
+int64_t padded_length(int64_t ndet, bool smooth) {
   int64_t n = 1;
   while (n < 2 * ndet) n *= 2;
+  if (smooth) {  // the next 3 * 2^k >= 2 ndet, counted from 48 on
+    int64_t m = 3;
+    while (m < 2 * ndet || m < 48) m *= 2;
+    n = std::min(n, m);
+  }
   return n;
 }
 
@@ -138,7 +143,19 @@ static std::vector<double> filter_response(int64_t npad, int32_t filter) {
     const double m = (double)(npad / 2);
     h[(size_t)(npad / 2)] = -1.0 / (M_PI * M_PI * m * m);
   }
-  fft64(h);
+  if ((npad & (npad - 1)) == 0) {
+    fft64(h);
+  } else {
+    // 3 * 2^k periods: the same DFT as a direct cosine sum (h is real and even)
+    std::vector<double> r((size_t)npad / 2 + 1);
+    for (int64_t k = 0; k <= npad / 2; ++k) {
+      double acc = 0.25;
+      for (int64_t m = 1; m < npad / 2; m += 2)
+        acc += 2.0 * h[(size_t)m].real() * std::cos(2.0 * M_PI * (double)((k * m) % npad) / (double)npad);
+      r[(size_t)k] = acc;
+    }
+    for (int64_t k = 0; k <= npad / 2; ++k) h[(size_t)k] = r[(size_t)k];
+  }
   for (int64_t k = 0; k <= npad / 2; ++k) {
     const double nu = (double)k / (double)npad;
     double w = 1.0;
@@ -165,10 +182,11 @@ struct FiltKeyHash {
 static std::unordered_map<FiltKey, float2*, FiltKeyHash> g_resp;
 static std::unordered_map<uint64_t, float2*> g_tw;  // (dev << 32) | npad
 
-tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out) {
+tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out,
+                            bool smooth) {
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
-  const int64_t npad = padded_length(ndet);
+  const int64_t npad = padded_length(ndet, smooth);
   FiltKey key;
   std::memset(&key, 0, sizeof(key));
   key.dev = dev;
@@ -183,7 +201,7 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
   auto tit = g_tw.find(twkey);
   if (tit == g_tw.end()) {
     // two-level table: 64 low powers, then the powers of W^64
-    const int64_t nhi = std::max<int64_t>(1, npad / 64);
+    const int64_t nhi = (npad + 63) / 64;
     std::vector<float2> tw((size_t)(64 + nhi));
     for (int64_t m = 0; m < 64 + nhi; ++m) {
       const double e = m < 64 ? (double)m : 64.0 * (double)(m - 64);
@@ -429,7 +447,7 @@ tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark
                                    tcp_tensor* sino, int32_t filter, double center, int32_t pad_mode, double weight,
                                    void* stream) {
   if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "unknown filter");
-  if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
+  if (!valid_pad_mode(pad_mode)) return fail(TCP_ERR_ARG, "unknown pad mode");
   if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
   if (!std::isfinite(weight)) return fail(TCP_ERR_ARG, "weight must be finite");
   FilterTable ft;
@@ -439,7 +457,7 @@ tcp_status tcp_normalize_filter_ex(const tcp_tensor* raw, const tcp_tensor* dark
   if (sv.d2 > 4096) return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
   if (raw && raw->ndim == 3 && numel(sino) > 0 && numel(raw) > 0) {
     const double w = weight > 0 ? weight : M_PI / (double)sv.d1;
-    if ((s = get_filter_table(sv.d2, filter, w, center, &ft)) != TCP_OK) return s;
+    if ((s = get_filter_table(sv.d2, filter, w, center, &ft, pad_smooth(pad_mode))) != TCP_OK) return s;
   } else {
     ft.npad = 0;
   }
@@ -514,14 +532,15 @@ tcp_status tcp_filter_ex(tcp_tensor* sino, int32_t filter, double center, int32_
   if ((s = check_tensor(sino, "sino", 2, 3)) != TCP_OK) return s;
   if (!is_float(sino->dtype)) return fail(TCP_ERR_DTYPE, "sino must be F32, F16 or BF16");
   if (filter < TCP_FILTER_SHEPP || filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "unknown filter");
-  if (pad_mode != TCP_PAD_EDGE && pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "unknown pad mode");
+  if (!valid_pad_mode(pad_mode)) return fail(TCP_ERR_ARG, "unknown pad mode");
   if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
   View3 v = view3(sino);
   if (v.d2 > 4096) return fail(TCP_ERR_UNSUPPORTED, "filter: ndet > 4096 (padded length > 8192)");
   const int64_t nt = ntheta > 0 ? ntheta : v.d1;
   if (numel(sino) == 0) return TCP_OK;
   FilterTable ft;
-  if ((s = get_filter_table(v.d2, filter, M_PI / (double)nt, center, &ft)) != TCP_OK) return s;
+  if ((s = get_filter_table(v.d2, filter, M_PI / (double)nt, center, &ft, pad_smooth(pad_mode))) != TCP_OK)
+    return s;
   return launch_filter(v, ft, pad_mode, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -215,7 +215,7 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     if (!in.theta) { s = fail(TCP_ERR_ARG, tag + "theta is null"); break; }
     if (!std::isfinite(in.center)) { s = fail(TCP_ERR_ARG, tag + "center must be finite"); break; }
     if (in.filter < TCP_FILTER_SHEPP || in.filter > TCP_FILTER_NONE) { s = fail(TCP_ERR_ARG, tag + "unknown filter"); break; }
-    if (in.pad_mode != TCP_PAD_EDGE && in.pad_mode != TCP_PAD_ZERO) { s = fail(TCP_ERR_ARG, tag + "unknown pad mode"); break; }
+    if (!valid_pad_mode(in.pad_mode)) { s = fail(TCP_ERR_ARG, tag + "unknown pad mode"); break; }
     for (const void* p : {in.raw.data, in.vol.data, in.dark.data, in.flat.data})
       if (!p || !on_device(p)) { s = fail(TCP_ERR_ARG, tag + "raw, dark, flat and vol must be device buffers"); break; }
     if (s != TCP_OK) break;
@@ -249,7 +249,9 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     it.sino.p = w; it.sino.dtype = b->sdt; it.sino.d0 = nz; it.sino.d1 = nt; it.sino.d2 = nd;
     it.sino.s0 = nt * nd; it.sino.s1 = nd;
     if ((s = get_trig_table(in.theta, nt, &it.trig)) != TCP_OK) break;
-    if ((s = get_filter_table(nd, in.filter, storage_scale(b->sdt), in.center, &it.ft)) != TCP_OK) break;
+    if ((s = get_filter_table(nd, in.filter, storage_scale(b->sdt), in.center, &it.ft, pad_smooth(in.pad_mode))) !=
+        TCP_OK)
+      break;
     b->items.push_back(it);
   }
   if (s == TCP_OK) {

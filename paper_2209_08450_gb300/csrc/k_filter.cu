@@ -74,9 +74,24 @@ __device__ __forceinline__ float2 tw_const(float2 a, int e, int R) {
   return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
 }
 
+// 3-point DFT: X_q = sum_r v_r W3^(r q), W3 = exp(-+2 pi i/3) = -1/2 -+ i sqrt(3)/2.
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& v0, float2& v1, float2& v2) {
+  constexpr float S3 = 0.86602540378443865f;  // sqrt(3)/2
+  const float2 s = cadd(v1, v2), d = csub(v1, v2);
+  const float2 m = make_float2(v0.x - 0.5f * s.x, v0.y - 0.5f * s.y);
+  // (-+ i sqrt(3)/2) (v1 - v2)
+  const float2 r = INV ? make_float2(-S3 * d.y, S3 * d.x) : make_float2(S3 * d.y, -S3 * d.x);
+  v0 = cadd(v0, s);
+  v1 = cadd(m, r);
+  v2 = csub(m, r);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-  if constexpr (R == 2) {
+  if constexpr (R == 3) {
+    dft3<INV>(v[0], v[1], v[2]);
+  } else if constexpr (R == 2) {
     dft2<INV>(v[0], v[1]);
   } else if constexpr (R == 4) {
     dft4<INV>(v[0], v[1], v[2], v[3]);
@@ -132,7 +147,7 @@ __device__ __forceinline__ float2 tw2(const float2* tw, int m) { return cmul(tw[
 // step) of a butterfly: for R = 16 the powers r = 1, 2, 4, 8 come from the
 // table and the others are products of at most three of them; for smaller R
 // every power comes from the table.
-template <int R, bool INV>
+template <int R, bool INV, bool P2 = true>
 __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int N, int Ns, const float2* tw,
                                               int gt, int gs) {
   const int nb = N / R;
@@ -141,7 +156,7 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
-    const int k = b & (Ns - 1);
+    const int k = P2 ? (b & (Ns - 1)) : b % Ns;  // P2: Ns is a power of two (else 3 * 2^i)
     if (Ns > 1) {
       float2 w[R];
       const int m1 = k * step;
@@ -282,40 +297,72 @@ __device__ __forceinline__ void single_pass(const float2* in, const float2* resp
   }
 }
 
-// Filter the row pair held in `a` (padded, N = 2^log2N): forward transform
-// with radices 16, ..., 16, Rl (Rl = 2^(log2N mod 4), or 16), the inverse
-// with the same radices reversed so that its first pass meets the forward
-// last pass in registers, and its last pass writes the rows.  Every thread of
-// the block takes part in the barriers; groups without a row pair (active ==
-// false) skip the arithmetic.  On return the shared buffers may be reused
-// after a barrier.
+// One Stockham pass of runtime radix r (2, 3, 4, 8 or 16).
+template <bool INV>
+__device__ __forceinline__ void pass_r(int r, const float2* in, float2* out, int N, int Ns, const float2* tw, int gt,
+                                       int gs) {
+  if ((Ns & (Ns - 1)) == 0) {
+    switch (r) {
+      case 16: stockham_pass<16, INV>(in, out, N, Ns, tw, gt, gs); break;
+      case 8: stockham_pass<8, INV>(in, out, N, Ns, tw, gt, gs); break;
+      case 4: stockham_pass<4, INV>(in, out, N, Ns, tw, gt, gs); break;
+      case 3: stockham_pass<3, INV>(in, out, N, Ns, tw, gt, gs); break;
+      default: stockham_pass<2, INV>(in, out, N, Ns, tw, gt, gs); break;
+    }
+  } else {  // after the inverse radix-3 pass: Ns = 3 * 2^i
+    switch (r) {
+      case 16: stockham_pass<16, INV, false>(in, out, N, Ns, tw, gt, gs); break;
+      case 8: stockham_pass<8, INV, false>(in, out, N, Ns, tw, gt, gs); break;
+      case 4: stockham_pass<4, INV, false>(in, out, N, Ns, tw, gt, gs); break;
+      default: stockham_pass<2, INV, false>(in, out, N, Ns, tw, gt, gs); break;
+    }
+  }
+}
+
+// Filter the row pair held in `a` (padded to N = prod rad[i]): forward
+// transform with the radices rad[0..nrad) (16, ..., 16, then 2/4/8, then 3),
+// the inverse with the same radices reversed so that its first pass meets the
+// forward last pass in registers, and its last pass (radix 16) writes the rows.
+// nrad == 1: N <= 16, one butterfly.  Every thread of the block takes part in
+// the barriers; groups without a row pair (active == false) skip the
+// arithmetic.  On return the shared buffers may be reused after a barrier.
 template <class TOut>
-__device__ void filter_pair(float2* a, float2* b, int N, int log2N, const float2* tw, const float2* resp, int gt,
-                            int gs, bool active, int left, int nd, TOut* o0, TOut* o1, bool has1, int64_t plane) {
-  if (log2N <= 4) {
+__device__ void filter_pair(float2* a, float2* b, int N, const int* rad, int nrad, const float2* tw, const float2* resp,
+                            int gt, int gs, bool active, int left, int nd, TOut* o0, TOut* o1, bool has1,
+                            int64_t plane) {
+  if (nrad == 1) {
     if (active) {
-      if (log2N == 4) single_pass<16>(a, resp, gt, left, nd, o0, o1, has1, plane);
-      else if (log2N == 3) single_pass<8>(a, resp, gt, left, nd, o0, o1, has1, plane);
-      else if (log2N == 2) single_pass<4>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      if (N == 16) single_pass<16>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      else if (N == 8) single_pass<8>(a, resp, gt, left, nd, o0, o1, has1, plane);
+      else if (N == 4) single_pass<4>(a, resp, gt, left, nd, o0, o1, has1, plane);
       else single_pass<2>(a, resp, gt, left, nd, o0, o1, has1, plane);
     }
     return;
   }
-  const int rl = (log2N & 3) ? (log2N & 3) : 4;  // log2 of the last forward radix
-  const int n16 = (log2N - rl) / 4;             // radix-16 passes on each side
+  int r8[8];  // the radices in registers (compile-time indices below)
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r8[i] = i < nrad ? rad[i] : 1;
   int Ns = 1;
-  for (int i = 0; i < n16; ++i) {
-    if (active) stockham_pass<16, false>(a, b, N, Ns, tw, gt, gs);
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-    Ns <<= 4;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    if (i + 1 < nrad) {
+      if (active) pass_r<false>(r8[i], a, b, N, Ns, tw, gt, gs);
+      __syncthreads();
+      float2* t = a;
+      a = b;
+      b = t;
+      Ns *= r8[i];
+    }
   }
+  int rl = 1;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (i == nrad - 1) rl = r8[i];
   if (active) {
-    if (rl == 4) fused_turn<16>(a, b, N, tw, resp, gt, gs);
-    else if (rl == 3) fused_turn<8>(a, b, N, tw, resp, gt, gs);
-    else if (rl == 2) fused_turn<4>(a, b, N, tw, resp, gt, gs);
+    if (rl == 16) fused_turn<16>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 8) fused_turn<8>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 4) fused_turn<4>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 3) fused_turn<3>(a, b, N, tw, resp, gt, gs);
     else fused_turn<2>(a, b, N, tw, resp, gt, gs);
   }
   __syncthreads();
@@ -324,14 +371,17 @@ __device__ void filter_pair(float2* a, float2* b, int N, int log2N, const float2
     a = b;
     b = t;
   }
-  Ns = 1 << rl;
-  for (int i = 0; i + 1 < n16; ++i) {
-    if (active) stockham_pass<16, true>(a, b, N, Ns, tw, gt, gs);
-    __syncthreads();
-    float2* t = a;
-    a = b;
-    b = t;
-    Ns <<= 4;
+  Ns = rl;
+#pragma unroll
+  for (int i = 6; i >= 1; --i) {
+    if (i <= nrad - 2) {
+      if (active) pass_r<true>(r8[i], a, b, N, Ns, tw, gt, gs);
+      __syncthreads();
+      float2* t = a;
+      a = b;
+      b = t;
+      Ns *= r8[i];
+    }
   }
   if (active) last_to_rows<TOut>(a, N, tw, gt, gs, left, nd, o0, o1, has1, plane);
 }
@@ -351,6 +401,8 @@ struct FiltArgs {
   int gs;           // threads per row pair
   int pad_zero;
   int vec4;         // raw rows and means allow 4-sample vector loads
+  int nrad;         // FFT radices, forward order (see filter_pair)
+  int rad[8];
   int64_t plane;    // TCP_F16X2 output: elements from the hi to the lo plane (else 0)
   const float2* resp;
   const float2* tw;  // two-level twiddle table (global; copied to shared memory)
@@ -377,7 +429,7 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
   const int g = threadIdx.x / gs, gt = threadIdx.x - g * gs;
   const int plen = a.npad + a.npad / 16;  // padded buffer length
   // [two-level twiddle table][G x (bufA, bufB)]
-  const int ntw = 64 + max(1, a.npad / 64);
+  const int ntw = 64 + (a.npad + 63) / 64;
   float2* tw = smem;
   for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = __ldg(a.tw + i);
   float2* bufA = smem + ntw + (size_t)g * 2 * plen;
@@ -453,7 +505,8 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
     __syncthreads();
     TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
     TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
-    filter_pair<TOut>(bufA, bufB, a.npad, a.log2n, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1, a.plane);
+    filter_pair<TOut>(bufA, bufB, a.npad, a.rad, a.nrad, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1,
+                      a.plane);
     __syncthreads();
   }
 }
@@ -472,16 +525,36 @@ void (*pick_out(int dt))(FiltArgs) {
 tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_mode, cudaStream_t st) {
   a.npad = ft.npad;
   a.log2n = 0;
-  while ((1 << a.log2n) < a.npad) ++a.log2n;
+  // radices: N = 16^p 2^q (3 if N % 3 == 0), forward order 16, .., 16, 2^q, 3
+  {
+    const bool three = a.npad % 3 == 0;
+    int m = three ? a.npad / 3 : a.npad, l2 = 0;
+    while ((1 << l2) < m) ++l2;
+    a.log2n = l2;
+    a.nrad = 0;
+    if (!three && l2 <= 4) {
+      a.rad[a.nrad++] = a.npad;  // one butterfly
+    } else {
+      const int q = l2 % 4;
+      for (int i = 0; i < l2 / 4; ++i) a.rad[a.nrad++] = 16;
+      if (q) a.rad[a.nrad++] = 1 << q;
+      if (three) a.rad[a.nrad++] = 3;
+    }
+    if (a.nrad > 8 || (a.nrad > 1 && a.rad[0] != 16))
+      return fail(TCP_ERR_UNSUPPORTED, "filter: padded length " + std::to_string(a.npad) + " not supported");
+  }
   a.left = (a.npad - a.nd) / 2;
-  a.pad_zero = pad_mode == TCP_PAD_ZERO;
+  a.pad_zero = (pad_mode & TCP_PAD_ZERO) != 0;
   a.resp = ft.response;
   a.tw = ft.twiddle;
   if (a.rows == 0 || a.nd == 0) return TCP_OK;
   if (!k) return fail(TCP_ERR_DTYPE, "filter: sinogram dtype must be F32, F16 or BF16");
-  a.gs = std::max(32, std::min(256, a.npad / 16));
+  // threads per row pair: a power of two (so that groups tile the block),
+  // about one radix-16 butterfly each
+  a.gs = 32;
+  while (a.gs < 256 && 2 * a.gs <= a.npad / 16) a.gs *= 2;
   const int threads = 256;
-  const size_t smem = ((size_t)(threads / a.gs) * 2 * (size_t)(a.npad + a.npad / 16) + 64 + std::max(1, a.npad / 64)) *
+  const size_t smem = ((size_t)(threads / a.gs) * 2 * (size_t)(a.npad + a.npad / 16) + 64 + (a.npad + 63) / 64) *
                       sizeof(float2);
   const int64_t npairs = (a.rows + 1) / 2;
   int dev = 0;

@@ -153,7 +153,7 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel)
   const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : (sdt == TCP_F32 ? 32 : 256);
   if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
-  if (o.pad_mode != TCP_PAD_EDGE && o.pad_mode != TCP_PAD_ZERO) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
+  if (!valid_pad_mode(o.pad_mode)) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
   const int B = o.n_buffers == 3 ? 3 : 2;
   if (nz == 0 || n == 0 || nt == 0 || nd == 0) {
     if (nz * n * n > 0) return fail(TCP_ERR_SHAPE, "fbp: empty projections for a non-empty volume");
@@ -175,7 +175,7 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   // backprojector writes each voxel (Sec. 2.1: reorder so 16-bit values stay
   // in range).
   const double sscale = storage_scale(sdt);
-  if ((s = get_filter_table(nd, o.filter, sscale, center, &ft)) != TCP_OK) return s;
+  if ((s = get_filter_table(nd, o.filter, sscale, center, &ft, pad_smooth(o.pad_mode))) != TCP_OK) return s;
   const float bp_scale = (float)(M_PI / (double)nt / sscale);
   tcp_bp_config cfg;
   tcp_get_backproject_config(std::min(chunk, nz), nt, nd, n, sdt, vol->dtype, &cfg);

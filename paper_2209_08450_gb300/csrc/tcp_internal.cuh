@@ -124,14 +124,18 @@ struct FilterTable {
   int npad = 0;
 };
 // weight multiplies the response (pi/N_theta for FBP; any value > 0).
-tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out);
+tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out,
+                            bool smooth = false);
+// pad_mode: bit 0 zero padding (else edge), bit 1 smooth padded length
+inline bool valid_pad_mode(int32_t m) { return m >= 0 && m <= (TCP_PAD_ZERO | TCP_PAD_SMOOTH); }
+inline bool pad_smooth(int32_t m) { return (m & TCP_PAD_SMOOTH) != 0; }
 
 // Storage scale of a sinogram that the library writes in `dtype` and reads
 // back itself (pipeline, batch): FP16 keeps a 2^10 headroom so that filtered
 // values stay out of the subnormal range (|filtered -log| <= 6.9 < 65504/2^10).
 inline double storage_scale(int dtype) { return (dtype == TCP_F16 || dtype == TCP_F16X2) ? 1024.0 : 1.0; }
 
-int64_t padded_length(int64_t ndet);
+int64_t padded_length(int64_t ndet, bool smooth = false);
 
 // Launchers (argument checks are done by the API layer).
 struct View3 {  // [d0][d1][d2] with element strides s0, s1 (s2 == 1)

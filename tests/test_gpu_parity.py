@@ -444,3 +444,32 @@ def test_split_sinogram_rejections():
         tcp.backproject(q, np.linspace(0, np.pi, 10), 18.0, n=36)
     with pytest.raises(tcp.TcpError):  # the in-place filter does not take pairs
         tcp.filter_(torch.zeros((2, 4, 10, 32), dtype=torch.float16, device=DEV), 16.0)
+
+
+# ------------------------------------------ smooth (3 x 2^k) filter padding --
+
+@pytest.mark.parametrize("nd,pad", [(40, "edge"), (300, "zero"), (24, "edge"), (1536, "edge")])
+@pytest.mark.parametrize("dt", [torch.float32, torch.float16])
+def test_filter_on_smooth_padding(nd, pad, dt):
+    # padded lengths 96, 768, 48 and 3072 (radix-3 FFT pass), in place and fused
+    rng = np.random.default_rng(nd)
+    nz, nt = 3, 5 if nd > 1000 else 17
+    q = rng.normal(size=(nz, nt, nd))
+    c = nd / 2.0 + 1.37
+    ref = oracle.filter_sino(q, c, "shepp", pad, rule="smooth")
+    assert tcp.padded_length(nd, smooth=True) == oracle.padded_length(nd, "smooth")
+    got = tcp.filter_(to_dev(q, dt), c, "shepp", pad + "_smooth")
+    tol = 1e-5 if dt == torch.float32 else 2e-3
+    assert rel(host(got), ref) <= tol
+    # against the power-of-two padding the result differs (other period) but only slightly
+    pow2 = oracle.filter_sino(q, c, "shepp", pad)
+    assert rel(ref, pow2) < 0.05
+
+
+def test_fbp_with_smooth_padding_matches_oracle():
+    ds = synth.shepp_logan_dataset(ntheta=80, ndet=96, nz=3, center=47.1, seed=21)
+    ref = oracle.fbp(ds.raw, ds.dark, ds.flat, ds.theta, ds.center, "shepp", rule="smooth")
+    out = tcp.fbp(u16(ds.raw), u16(ds.dark), u16(ds.flat), ds.theta, ds.center, pad="edge_smooth")
+    torch.cuda.synchronize()
+    assert tcp.padded_length(96, smooth=True) == 192
+    assert rel(host(out), ref) <= 1e-5
