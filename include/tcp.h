@@ -170,8 +170,9 @@ tcp_status tcp_normalize_noalloc(const tcp_tensor* raw, const tcp_tensor* dark, 
 /* ---------------------------------------------------------------- filter -- */
 
 /* One-dimensional FBP filter of every detector row, in place (Sec. 2.2).
- * Per row: pad to npad = next power of two >= 2*ndet (L = (npad-ndet)/2 on the
- * left, edge-replicated), FFT, multiply bin k by
+ * Per row: pad to npad = next power of two >= 2*ndet, or the smooth length
+ * of tcp_pad_mode (L = (npad-ndet)/2 on the left, edge-replicated unless
+ * TCP_PAD_ZERO), FFT, multiply bin k by
  *   H(k) * pi/ntheta * exp(2 pi i (k/npad) (center - ndet/2))
  * (Hermitian: the Nyquist bin takes the real part), inverse FFT, crop
  * [L, L+ndet).  The phase factor moves the rotation axis from `center` to

@@ -7,11 +7,15 @@
 // because the filter response is Hermitian (F[N-k] = conj(F[k])), filtering z
 // filters a and b independently, so one complex FFT pair serves two rows
 // without a separation step.  The FFT is a Stockham auto-sort transform
-// (radix-16 register butterflies, one pass of 8, 4 or 2 for the rest of
-// log2 N) between two shared-memory buffers, one barrier per pass.  Twiddles and the response are
-// FP64-derived tables; the arithmetic is FP32.  The response folds in the
-// window, the pi/N_theta FBP weight, the 1/N of the inverse transform and the
-// phase that moves the rotation axis to ndet/2.
+// between two shared-memory buffers, one barrier per pass: radix-16 register
+// butterflies, then one pass of 8, 4 or 2 for the rest of the power of two,
+// then radix 3 for padded lengths 3 * 2^k.  The forward last pass, the
+// response and the inverse first pass run in registers (the inverse takes the
+// radices in reverse order), and the inverse last pass writes the output
+// rows.  Twiddles (a two-level table in shared memory) and the response are
+// FP64-derived; the arithmetic is FP32.  The response folds in the window, the
+// pi/N_theta FBP weight (or a caller's storage weight), the 1/N of the inverse
+// transform and the phase that moves the rotation axis to ndet/2.
 //
 // Fused mode reads uint16 projections and computes -ln((raw-dark)/(flat-dark))
 // in FP32 while filling shared memory, so an FP16/BF16 sinogram is rounded
