@@ -507,6 +507,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
     while (!mbar_try(smem_u32(&bars->done), 0) && clock64() - t0 < kTcBudget) {
     }
   }
+  // Also on an abort, sinogram copies the producer issued may still be
+  // landing in shared memory.  They complete only the stage barriers, which
+  // also wait for builder arrivals that an abort cancels, so the producer
+  // holds the block for a fixed interval (~50k cycles, far above a copy's
+  // latency) before the shared memory is given up.
+  if (live_tile && warp == kTcBuilders && lane == 0 && *abort) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < 50000) {
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)

@@ -473,3 +473,30 @@ def test_fbp_with_smooth_padding_matches_oracle():
     torch.cuda.synchronize()
     assert tcp.padded_length(96, smooth=True) == 192
     assert rel(host(out), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_tensor_core_window_check_stays_clean(split):
+    # checked mode: every weight index is checked against the 32-sample window
+    # and any violation is recorded in the device error word; angles over two
+    # turns, an axis off the middle, ragged tiles
+    rng = np.random.default_rng(31)
+    nz, nt, nd, n, c = 40, 96, 200, 184, 123.7
+    q = rng.normal(size=(nz, nt, nd))
+    theta = rng.uniform(-7.0, 7.0, nt)
+    ref = oracle.backproject(q, theta, c, n)
+    tcp.set_checked(True)
+    try:
+        if split:
+            got = tcp.backproject(_split(q, 1024.0), theta, c, n=n, scale=1.0 / 1024.0)
+            tol = 1e-5
+        else:
+            qd = to_dev(q, torch.float16)
+            got = tcp.backproject(qd, theta, c, n=n, dtype=torch.float32)
+            ref = oracle.backproject(host(qd), theta, c, n)
+            tol = 5e-3
+        torch.cuda.synchronize()
+        assert tcp.device_check() == 0
+    finally:
+        tcp.set_checked(False)
+    assert rel(host(got), ref) <= tol
