@@ -211,9 +211,9 @@ PATHS = {
 # exact launch shapes (slices, angles, n) -> bytes, file under profiles/.  Set
 # an entry to None when its kernel changes.
 PROFILED_TRAFFIC = {
-    "f32": ((256, 2048, 2048), 593.1e9 + 4.31e9, "profiles/k_backproject_tc_split_f32_2048sq_256slices.md"),
-    "f16": ((256, 2048, 2048), 559.1e9 + 2.15e9, "profiles/k_backproject_tc_f16_2048sq_256slices.md"),
-    "f32_cuda": ((32, 2048, 2048), 8.09e9 + 0.53e9, "profiles/k_backproject_f32_2048sq_32slices.md"),
+    "f32": ((256, 2048, 2048), 561.5e9 + 4.30e9, "profiles/k_backproject_tc_split_f32_2048sq_256slices.md"),
+    "f16": ((256, 2048, 2048), 622.5e9 + 2.15e9, "profiles/k_backproject_tc_f16_2048sq_256slices.md"),
+    "f32_cuda": ((32, 2048, 2048), 8.01e9 + 0.53e9, "profiles/k_backproject_f32_2048sq_32slices.md"),
 }
 
 

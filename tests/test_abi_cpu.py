@@ -132,6 +132,12 @@ def test_try_centers_argument_checks(lib):
                    ctypes.byref(vol), 0, None) == 2  # vol is not [ncenters][n][n]
 
 
+def test_detector_width_limit(lib):
+    # padded rows must fit shared memory: ndet <= 4096, checked before any device work
+    wide = _t(_lib.F32, (1, 2, 4097), ptr=1 << 20)
+    assert _status(lib, "tcp_filter", ctypes.byref(wide), 0, 2048.0, None) == 9
+
+
 def test_default_config_query(lib):
     c = _lib.BpConfig()
     assert lib.tcp_get_backproject_config(64, 2048, 2048, 2048, 3, 3, ctypes.byref(c)) == 0

@@ -351,7 +351,7 @@ def test_fbp_fp16_many_angles_keeps_filtered_values_in_range():
 @pytest.mark.parametrize("sdt", [torch.float16, torch.bfloat16])
 @pytest.mark.parametrize("nz,nt,nd,n,center", [
     (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (16, 13, 64, 100, 31.7), (40, 129, 200, 160, 99.2),
-    (1, 70, 40, 48, 19.5)])
+    (1, 70, 40, 48, 19.5), (3, 10, 16, 9, 4.2)])
 def test_backproject_tensor_cores(sdt, nz, nt, nd, n, center, stage):
     # stage = angles per pipeline stage (the B ring then holds as many stages
     # as shared memory allows); 129 angles leave a ragged last stage
@@ -395,7 +395,7 @@ def _split(q, scale):
 
 @pytest.mark.parametrize("nz,nt,nd,n,center", [
     (20, 37, 96, 96, 48.0), (3, 50, 72, 70, 35.3), (300, 24, 64, 64, 32.4), (1, 70, 40, 48, 19.5),
-    (40, 129, 200, 160, 99.2)])
+    (40, 129, 200, 160, 99.2), (2, 33, 16, 9, 4.2)])
 def test_backproject_split_fp16_pairs_reach_fp32_tolerance(nz, nt, nd, n, center):
     # three FP16 products per weight/sample pair, accumulated in FP32 on the
     # tensor cores: held to the FP32 tolerance, not the 16-bit one
