@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import TcpError, load  # noqa: F401
 
-__all__ = ["frame_mean", "normalize", "normalize_filter", "filter_", "backproject", "project", "device_check",
+__all__ = ["frame_mean", "normalize", "normalize_filter", "filter_", "backproject", "project", "fourierrec", "device_check",
            "set_checked", "cache_clear", "set_backproject_config", "get_backproject_config",
            "TcpError", "load", "padded_length"]
 
@@ -138,6 +138,24 @@ def project(vol: torch.Tensor, theta, center: float, ndet: int | None = None,
     a, b = _lib.desc(vol), _lib.desc(out)
     _lib.call("tcp_project", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
               _lib.stream_ptr(stream))
+    return out
+
+
+def fourierrec(sino: torch.Tensor, theta, center: float, n: int | None = None,
+               out: torch.Tensor | None = None, dtype=None, scale: float = 1.0, width: int = 0,
+               stream=None) -> torch.Tensor:
+    """FourierRec backprojection sino[z][theta][j] -> vol[z][n][n] (n even): scale x
+    (sum over angles of the trigonometric interpolant of each zero-padded row),
+    evaluated on an oversampled Cartesian frequency grid with a window of
+    `width` points (0: 7 for float32 output, 5 for 16-bit)."""
+    th = _lib.theta_array(theta)
+    nz, nt, nd = sino.shape
+    if out is None:
+        n = nd if n is None else n
+        out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype or sino.dtype], device=sino.device)
+    a, b = _lib.desc(sino), _lib.desc(out)
+    _lib.call("tcp_fourierrec", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
+              float(scale), int(width), _lib.stream_ptr(stream))
     return out
 
 

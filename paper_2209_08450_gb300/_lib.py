@@ -88,6 +88,7 @@ SIGNATURES = {
     "tcp_filter_ex": ([_T, _I32, _D, _I32, _I64, _P], _I32),
     "tcp_backproject": ([_T, _P, _D, _T, _P], _I32),
     "tcp_project": ([_T, _P, _D, _T, _P], _I32),
+    "tcp_fourierrec": ([_T, _P, _D, _T, _D, _I32, _P], _I32),
     "tcp_set_backproject_config": ([ctypes.POINTER(BpConfig)], _I32),
     "tcp_get_backproject_config": ([_I64, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(BpConfig)], _I32),
     "tcp_fbp": ([_T, _T, _T, _P, _D, _T, ctypes.POINTER(FbpOpts), _P], _I32),

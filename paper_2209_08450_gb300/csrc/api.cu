@@ -603,6 +603,39 @@ tcp_status tcp_backproject_ex(const tcp_tensor* sino, const double* theta, doubl
   return launch_backproject(sv, trig, center, view3(vol), cfg, st, (float)scale);
 }
 
+tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol,
+                          double scale, int32_t width, void* stream) {
+  tcp_status s;
+  if (!std::isfinite(scale)) return fail(TCP_ERR_ARG, "scale must be finite");
+  if ((s = check_tensor(sino, "sino", 3, 4)) != TCP_OK) return s;
+  if (!is_float(sino->dtype)) return fail(TCP_ERR_DTYPE, "fourierrec: sino must be F32, F16 or BF16");
+  if (sino->ndim != 3) return fail(TCP_ERR_SHAPE, "fourierrec: sino must be [nz][ntheta][ndet]");
+  if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
+  if (!is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "vol must be F32, F16 or BF16");
+  if (vol->shape[0] != sino->shape[0]) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
+  if (vol->shape[1] != vol->shape[2]) return fail(TCP_ERR_SHAPE, "vol slices must be square [n][n]");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  const int64_t nt = sino->shape[1], nd = sino->shape[2], n = vol->shape[1];
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "theta is null");
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "theta must be finite");
+  const int w = width == 0 ? fourierrec_default_width(vol->dtype, n) : width;
+  if ((s = fourierrec_check(nt, nd, n, w)) != TCP_OK) return s;
+  if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (numel(vol) == 0) return TCP_OK;
+  if (nt == 0 || nd == 0) {  // no rays: the sum is zero
+    for (int64_t z = 0; z < vol->shape[0]; ++z)
+      TCP_CUDA_TRY(cudaMemset2DAsync((char*)vol->data + z * vol->stride[0] * dtype_size(vol->dtype),
+                                     vol->stride[1] * dtype_size(vol->dtype), 0,
+                                     vol->shape[2] * dtype_size(vol->dtype), vol->shape[1], st));
+    return TCP_OK;
+  }
+  TrigTable trig;
+  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  return launch_fourierrec(view3(sino), trig, center, view3(vol), (float)scale, w, st);
+}
+
 tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {
   tcp_status s;
   if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;

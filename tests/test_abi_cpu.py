@@ -142,3 +142,22 @@ def test_default_config_query(lib):
     c = _lib.BpConfig()
     assert lib.tcp_get_backproject_config(64, 2048, 2048, 2048, 3, 3, ctypes.byref(c)) == 0
     assert c.k_slices in (1, 2, 4, 8, 16) and c.theta_stage in (8, 16, 32)
+
+
+def test_fourierrec_argument_checks(lib):
+    th = (ctypes.c_double * 4)(0, 0.5, 1.0, 1.5)
+    sino = _t(_lib.F32, (2, 4, 16))
+    vol = _t(_lib.F32, (2, 16, 16), ptr=1 << 20)
+    odd = _t(_lib.F32, (2, 15, 15), ptr=1 << 20)
+    assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, 8.0, ctypes.byref(odd), 1.0, 0, None) == 2
+    assert b"even" in lib.tcp_last_error()
+    for w in (1, 17):
+        assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, 8.0, ctypes.byref(vol), 1.0, w, None) == 1
+    pair = _t(_lib.F16X2, (2, 2, 4, 16))
+    assert _status(lib, "tcp_fourierrec", ctypes.byref(pair), th, 8.0, ctypes.byref(vol), 1.0, 0, None) == 3
+    wide = _t(_lib.F32, (2, 4, 8193))
+    assert _status(lib, "tcp_fourierrec", ctypes.byref(wide), th, 8.0, ctypes.byref(vol), 1.0, 0, None) == 2
+    tiny = _t(_lib.F32, (2, 2, 2), ptr=1 << 20)  # n = 2: grid L = 4 < width 5
+    assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, 8.0, ctypes.byref(tiny), 1.0, 5, None) == 1
+    assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, float("nan"), ctypes.byref(vol), 1.0, 0,
+                   None) == 1
