@@ -204,7 +204,11 @@ PATHS = {
     "f16": ("float16", None, 256),
     "bf16": ("bfloat16", None, 256),
     "f32_cuda": ("float32", "float32", 32),
+    "f32_frec": ("float32", "float32", 64),
+    "f16_frec": ("float16", "float16", 64),
 }
+# Paths reconstructed by FourierRec (Fourier-slice gridding) instead of LineRec.
+FOURIERREC = {"f32_frec": 7, "f16_frec": 5}  # path -> window width
 
 
 # DRAM bytes (read + write) per backprojector launch from ncu captures of these
@@ -240,6 +244,23 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     clk_max = float(pk.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     interps = nz * n * n * nt
+    if path in FOURIERREC:
+        # gridding work: every polar sample (ntheta x (M + 1) per slice pair)
+        # reaches W x W grid nodes with one complex-by-real multiply-add
+        # (4 flops); against the FP32 FMA peak of the CUDA cores
+        w = FOURIERREC[path]
+        m = 1
+        while m < 2 * n:
+            m *= 2
+        flops = ((nz + 1) // 2) * nt * (m + 1) * w * w * 4
+        peak = sms * 128 * 2 * clk_max * 1e6
+        ach = flops / (ms * 1e-3)
+        return {"bound": "alu", "kernel": "tcp_fourierrec (row FFT, gather, column and row inverse FFTs; "
+                                          "k_frec_gather is the dominant kernel)",
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "ms_per_launch": ms, "window_width": w,
+                "peak_basis": "FP32 FMA lanes: %d SMs x 128 x 2 flops x %.0f MHz (max SM clock); the time is the "
+                              "whole backprojector call, not the gather kernel alone" % (sms, clk_max)}
     vdt, sdt, _ = PATHS[path]
     split = path == "f32"
     traffic, tsrc = _traffic(path, nz, nt, n)
@@ -374,7 +395,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "f32_cuda"],
                     help="headline path (f32: FP32 volume from FP16 hi/lo sinogram pairs on the tensor cores)")
     ap.add_argument("--chunk", type=int, default=0, help="slices per chunk (0: the path's default)")
-    ap.add_argument("--variants", default="f32,f16,bf16,f32_cuda")
+    ap.add_argument("--variants", default="f32,f16,bf16,f32_cuda,f32_frec,f16_frec")
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=4)
@@ -427,6 +448,7 @@ def main():
 
         def step():
             tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(path), sino_dtype=sdt_of(path),
+                    algorithm="fourierrec" if path in FOURIERREC else "linerec", width=FOURIERREC.get(path, 0),
                     stream=stream)
         for _ in range(warmup):
             step()
@@ -449,18 +471,24 @@ def main():
     value = world * nz * n * n / (ms * 1e-3) / 1e9
 
     # ---- parity on sampled slices (oracle on the same uint16 frames)
-    def parity(v, zs):
+    def parity(v, zs, path=None):
         import oracle
+        from oracle import fourierrec as frc
         rng = np.random.default_rng(1)
         errs = []
+        frec = path in FOURIERREC
+        npts = 24 if frec else 2000  # the exact FourierRec sums cost ntheta x 2 ndet per voxel
         for z in zs:
             r = raw[:, z:z + 1].cpu().numpy().view(np.uint16)
             d = dark[:, z:z + 1].cpu().numpy().view(np.uint16)
             f = flat[:, z:z + 1].cpu().numpy().view(np.uint16)
             p = oracle.normalize(r, oracle.frame_mean(d), oracle.frame_mean(f))
             q = oracle.filter_sino(p, center, "shepp")[0]
-            ix, iy = rng.integers(0, n, 2000), rng.integers(0, n, 2000)
-            ref = oracle.backproject_points(q, theta, n / 2.0, n, ix, iy)
+            ix, iy = rng.integers(0, n, npts), rng.integers(0, n, npts)
+            if frec:
+                ref = frc.backproject_exact_points(q, theta, n / 2.0, n, ix, iy)
+            else:
+                ref = oracle.backproject_points(q, theta, n / 2.0, n, ix, iy)
             got = v[z].double().cpu().numpy()[iy, ix]
             errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         return float(max(errs))
@@ -496,7 +524,11 @@ def main():
         nf = lambda: tcp.normalize_filter(raw[:, zc:zc + c], dm[zc:zc + c], fm[zc:zc + c], center, dtype=sd,
                                           weight=w)
         sino = nf()
-        ms_bp = time_kernel(lambda: tcp.backproject(sino, theta, n / 2.0, out=out_vol[:c], scale=sc))
+        if path in FOURIERREC:
+            ms_bp = time_kernel(lambda: tcp.fourierrec(sino, theta, n / 2.0, out=out_vol[:c], scale=sc,
+                                                       width=FOURIERREC[path]))
+        else:
+            ms_bp = time_kernel(lambda: tcp.backproject(sino, theta, n / 2.0, out=out_vol[:c], scale=sc))
         holder = {}
 
         def nf_into():
@@ -522,11 +554,13 @@ def main():
         vms = run_steps(name, args.variant_steps, 1, vv)
         variants[name] = {"value": world * nz * n * n / (vms * 1e-3) / 1e9, "ms_per_step": vms,
                           "speedup_vs_headline": ms / vms, "chunk_nz": chunk_for(name),
-                          "sino_storage": "f16x2" if name == "f32" else (PATHS[name][1] or PATHS[name][0])}
+                          "sino_storage": "f16x2" if name == "f32" else (PATHS[name][1] or PATHS[name][0]),
+                          "algorithm": "fourierrec (window %d)" % FOURIERREC[name] if name in FOURIERREC
+                          else "linerec"}
         vc, vms_k, _, _ = path_kernels(name, vv)
         variants[name]["roofline"] = bp_roofline(tcp, dev, name, vc, nt, n, vms_k)
         if rank == 0 and zs:
-            variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs)
+            variants[name]["rel_l2_vs_fp64_oracle"] = parity(vv, zs, name)
         del vv
 
     # ---- end to end through the C ABI with host buffers
@@ -584,7 +618,8 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-            "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f32_cuda": 1e-5, "f16": 5e-3, "bf16": 5e-3},
+            "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f32_cuda": 1e-5, "f16": 5e-3, "bf16": 5e-3, "f32_frec": 1e-5,
+                          "f16_frec": 5e-3},
             "variants": variants, "rows": rows, "input_generation_s": t_gen,
         }
         print(json.dumps(out), flush=True)

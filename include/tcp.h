@@ -299,8 +299,17 @@ typedef struct {
   int32_t filter;       /* tcp_filter_kind */
   int32_t pad_mode;     /* tcp_pad_mode */
   int32_t n_buffers;    /* device ring depth, 2 or 3 (default 2) */
-  int32_t reserved[3];
+  int32_t algorithm;    /* tcp_algorithm: backprojector (0 = LineRec) */
+  int32_t width;        /* FourierRec window width (0: the tcp_fourierrec default) */
+  int32_t reserved[1];
 } tcp_fbp_opts;
+
+/* Backprojector of tcp_fbp (Sec. 3 names both): LineRec, the direct
+ * linear-interpolation sum (tcp_backproject), or FourierRec, the
+ * Fourier-slice evaluation with band-limited interpolation (tcp_fourierrec;
+ * F32/F16/BF16 sinogram chunks, the default F32 for FP32 volumes; chunk_nz
+ * <= 0 gives 64; n must be even). */
+typedef enum { TCP_ALG_LINEREC = 0, TCP_ALG_FOURIERREC = 1 } tcp_algorithm;
 
 /* Chunked FBP (Sec. 2.3): for each chunk of chunk_nz slices, copy the raw
  * z-slab in, normalise, filter (axis moved to ndet/2) and backproject into

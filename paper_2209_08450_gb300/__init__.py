@@ -195,14 +195,16 @@ def get_backproject_config(nz, ntheta, ndet, n, sino_dtype=torch.float32, vol_dt
 def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center: float,
         out: torch.Tensor | None = None, dtype=torch.float32, n: int | None = None, chunk_nz: int = 0,
         filter: str = "shepp", pad: str = "edge", sino_dtype=None, n_buffers: int = 2,
-        stream=None) -> torch.Tensor:
+        algorithm: str = "linerec", width: int = 0, stream=None) -> torch.Tensor:
     """Chunked FBP (normalise -> filter -> backproject per z-slab, Sec. 2.3).
 
     raw uint16 [theta][z][j] and the output may be CUDA tensors or host tensors
     (page-locked host memory lets the slab copies overlap compute).  dark/flat
     are uint16 frames [nf][z][j] or FP32 means [z][j].  The volume is
     reconstructed about the filtered axis ndet/2 with the `center` shift folded
-    into the filter.  Returns `out` once the work is queued on the stream."""
+    into the filter.  algorithm: "linerec" (direct sum, linear interpolation)
+    or "fourierrec" (Fourier-slice evaluation, window `width`; n even).
+    Returns `out` once the work is queued on the stream."""
     raw = _as_u16(raw)
     nt, nz, nd = raw.shape
     if out is None:
@@ -221,6 +223,8 @@ def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center
     opts.filter = _lib.FILTERS[filter]
     opts.pad_mode = _lib.PADS[pad]
     opts.n_buffers = n_buffers
+    opts.algorithm = _lib.ALGORITHMS[algorithm]
+    opts.width = width
     r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
     _lib.call("tcp_fbp", _lib.ref(r), _lib.ref(d), _lib.ref(f), th.ctypes.data_as(ctypes.c_void_p), float(center),
               _lib.ref(o), ctypes.byref(opts), _lib.stream_ptr(stream))

@@ -60,7 +60,11 @@ class BpConfig(ctypes.Structure):
 
 class FbpOpts(ctypes.Structure):
     _fields_ = [("chunk_nz", ctypes.c_int32), ("sino_dtype", ctypes.c_int32), ("filter", ctypes.c_int32),
-                ("pad_mode", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("pad_mode", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("algorithm", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+
+
+ALGORITHMS = {"linerec": 0, "fourierrec": 1}
 
 
 _lock = threading.Lock()

@@ -633,7 +633,7 @@ tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double ce
   }
   TrigTable trig;
   if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
-  return launch_fourierrec(view3(sino), trig, center, view3(vol), (float)scale, w, st);
+  return launch_fourierrec(view3(sino), theta, trig, center, view3(vol), (float)scale, w, st);
 }
 
 tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {

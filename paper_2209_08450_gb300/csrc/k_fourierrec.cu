@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kMaxLg = 14;  // M, L <= 16384 (128 KB of complex FP32 in shared memory)
 constexpr int kMaxTheta = 16384;
-constexpr size_t kBatchBytes = size_t(1) << 30;  // P + H workspace per batch
+constexpr size_t kBatchBytes = size_t(3) << 29;  // P + G + H workspace per batch (1.5 GiB)
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -110,16 +110,19 @@ __device__ void fft_dif(float2* a, int lg, int count, const float2* __restrict__
 
 // --------------------------------------------------------------- tables --
 
-// Per-call geometry: (L/M) cos theta and (L/M) sin theta as FP32 hi + lo
-// pairs (from the FP64 angle table), and the row phase factors
+// Per-call geometry in sorted-angle order: for sorted position u, meta[u] =
+// (original angle t, sign s) with theta' = theta_t - pi (1 - s)/2 in [0, pi);
+// geomS[u] = (L/M) s (cos theta_t, sin theta_t) as FP32 hi + lo pairs (from
+// the FP64 angle table).  Also the row phase factors
 // (w_k / M) e^{2 pi i k center / M}, k = -M/2 .. M/2, made in FP64.
-__global__ void k_frec_geom(const double2* __restrict__ trig, int nt, double ratio, float4* __restrict__ geom,
-                            double center, int M, float2* __restrict__ phase) {
+__global__ void k_frec_geom(const double2* __restrict__ trig, const int2* __restrict__ meta, int nt, double ratio,
+                            float4* __restrict__ geomS, double center, int M, float2* __restrict__ phase) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nt) {
-    const double cx = trig[i].x * ratio, sy = trig[i].y * ratio;
+    const int2 m = meta[i];
+    const double cx = trig[m.x].x * ratio * m.y, sy = trig[m.x].y * ratio * m.y;
     const float chi = (float)cx, shi = (float)sy;
-    geom[i] = make_float4(chi, (float)(cx - (double)chi), shi, (float)(sy - (double)shi));
+    geomS[i] = make_float4(chi, (float)(cx - (double)chi), shi, (float)(sy - (double)shi));
   }
   if (i <= M) {
     const double k = (double)(i - M / 2);
@@ -162,33 +165,6 @@ __global__ void __launch_bounds__(256) k_frec_rows(const TS* __restrict__ sino, 
 
 // ------------------------------------------------------------- kernel 2 --
 
-// Conservative k range of the samples of one angle whose window can reach
-// grid columns [lo, hi]: k * c in (lo - W/2, hi + W/2), widened by one on each
-// side (the exact column test is made per node), clipped to [-M/2, M/2].
-__device__ __forceinline__ void k_range(float c, float A, float B, int M, int* klo, int* khi) {
-  const float lim = (float)M;
-  if (fabsf(c) < 1e-30f) {
-    if (A < 0.f && B > 0.f) {
-      *klo = -M / 2;
-      *khi = M / 2;
-    } else {
-      *klo = 1;
-      *khi = 0;
-    }
-    return;
-  }
-  float qa = A / c, qb = B / c;
-  if (qa > qb) {
-    const float tmp = qa;
-    qa = qb;
-    qb = tmp;
-  }
-  qa = fminf(fmaxf(qa, -lim), lim);
-  qb = fminf(fmaxf(qb, -lim), lim);
-  *klo = max((int)floorf(qa) - 1, -M / 2);
-  *khi = min((int)ceilf(qb) + 1, M / 2);
-}
-
 // k * (hi + lo) as an integer part and a fraction accurate to ~1e-7.
 __device__ __forceinline__ void split_pos(float fk, float hi, float lo, int* gi, float* fr) {
   const float ph = fk * hi;
@@ -206,126 +182,241 @@ __device__ __forceinline__ void split_pos(float fk, float hi, float lo, int* gi,
   *fr = f;
 }
 
-template <int W>
-__device__ __forceinline__ float es_weight(float d, float beta) {
-  const float s = d * (2.f / (float)W);
-  const float z2 = s * s;
-  return z2 < 1.f ? expf(beta * (sqrtf(1.f - z2) - 1.f)) : 0.f;
+// Window weight at distance d (grid points): exp(beta (sqrt(1 - (2d/W)^2) - 1))
+// inside |d| < W/2, else 0.  The fast exponential and reciprocal square root
+// keep the weight within ~1e-6 relative, well inside the window's own error
+// at the default widths.
+__device__ __forceinline__ float es_weight(float d, float beta, float two_over_w) {
+  const float s = d * two_over_w;
+  const float z = 1.f - s * s;
+  return z > 0.f ? __expf(beta * (z * rsqrtf(z) - 1.f)) : 0.f;
 }
 
-// Exclusive scan of v[0..n) in place, v[n] = total; all threads take part.
-__device__ void block_scan(int* v, int n) {
-  __shared__ int warp_tot[32];
-  const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int per = (n + nthr - 1) / nthr;
-  const int b = min(n, tid * per), e = min(n, b + per);
-  int sum = 0;
-  for (int i = b; i < e; ++i) sum += v[i];
-  int inc = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
+// Intersect [klo, khi] with the integers k for which k * c lies in (A, B),
+// up to a margin of 2e-3 in k: the quotients carry a relative error of a few
+// 1e-7 (|k| <= 8192), and a sample that close to the window's edge has weight
+// below 2e-7 (e^-beta scale), far inside the window's own error.
+__device__ __forceinline__ void clip_k(float c, float A, float B, float lim, int* klo, int* khi) {
+  if (fabsf(c) < 1e-30f) {
+    if (!(A < 0.f && B > 0.f)) *khi = *klo - 1;
+    return;
   }
-  if (lane == 31) warp_tot[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = nthr >> 5;
-    int x = lane < nw ? warp_tot[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+  float qa = __fdividef(A, c), qb = __fdividef(B, c);
+  if (qa > qb) {
+    const float t = qa;
+    qa = qb;
+    qb = t;
+  }
+  *klo = max(*klo, (int)ceilf(fmaxf(qa, -lim) - 2e-3f));
+  *khi = min(*khi, (int)floorf(fminf(qb, lim) + 2e-3f));
+}
+
+// Sorted-angle index range [u0, u1) of the angles theta' in [lo, hi] (thS
+// ascending in [0, pi)).
+__device__ __forceinline__ void angle_range(const float* __restrict__ thS, int nt, float lo, float hi, int* u0,
+                                            int* u1) {
+  int a = 0, b = nt;  // first index with thS >= lo
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (__ldg(thS + m) < lo) a = m + 1; else b = m;
+  }
+  *u0 = a;
+  b = nt;  // first index with thS > hi
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (__ldg(thS + m) <= hi) a = m + 1; else b = m;
+  }
+  *u1 = a;
+}
+
+// Candidate angles for the nodes [bx0, bx0 + CW) x [by0, by0 + R): lines
+// through the origin at angle theta' reach a window of a node only if they
+// pass within hd + W/sqrt(2) of the block centre (hd: half diagonal).  Up to
+// two sorted-index ranges (the angle interval may wrap at pi).
+template <int R, int CW>
+__device__ __forceinline__ int block_angles(int W, int bx0, int by0, const float* __restrict__ thS, int nt, int2* rng) {
+  const float xc = bx0 + 0.5f * (CW - 1), yc = by0 + 0.5f * (R - 1);
+  const float rho = sqrtf(xc * xc + yc * yc);
+  const float reach = 0.5f * sqrtf((float)((CW - 1) * (CW - 1) + (R - 1) * (R - 1))) + 0.7072f * W + 0.5f;
+  if (reach >= rho) {
+    rng[0] = make_int2(0, nt);
+    return 1;
+  }
+  const float kPi = 3.14159265358979f;
+  const float alpha = asinf(reach / rho) + 1e-4f;
+  float phi = atan2f(yc, xc);
+  if (phi < 0.f) phi += kPi;
+  if (phi >= kPi) phi -= kPi;
+  const float lo = phi - alpha, hi = phi + alpha;
+  int u0, u1;
+  if (lo < 0.f) {
+    angle_range(thS, nt, 0.f, hi, &u0, &u1);
+    rng[0] = make_int2(u0, u1);
+    angle_range(thS, nt, lo + kPi, kPi, &u0, &u1);
+    rng[1] = make_int2(u0, u1);
+    return 2;
+  }
+  if (hi >= kPi) {
+    angle_range(thS, nt, lo, kPi, &u0, &u1);
+    rng[0] = make_int2(u0, u1);
+    angle_range(thS, nt, 0.f, hi - kPi, &u0, &u1);
+    rng[1] = make_int2(u0, u1);
+    return 2;
+  }
+  angle_range(thS, nt, lo, hi, &u0, &u1);
+  rng[0] = make_int2(u0, u1);
+  return 1;
+}
+
+// Adds to acc[r][c] the window-weighted samples of sorted angle u that reach
+// node (bx0 + c, by0 + r).
+template <int R, int CW>
+__device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, const float2* __restrict__ Pp, int ms,
+                                             int M, const float4* __restrict__ geomS, const int2* __restrict__ meta,
+                                             float beta, float2 (&acc)[R][CW]) {
+  const float tw = 2.f / (float)W;
+  const float4 g = __ldg(geomS + u);
+  int klo = -M / 2, khi = M / 2;
+  const float lim = (float)M;
+  clip_k(g.x, bx0 - 0.5f * W, bx0 + (CW - 1) + 0.5f * W, lim, &klo, &khi);
+  clip_k(g.z, by0 - 0.5f * W, by0 + (R - 1) + 0.5f * W, lim, &klo, &khi);
+  if (klo > khi) return;
+  const int2 m = __ldg(meta + u);  // original angle, sign of k
+  const float2* row = Pp + (int64_t)m.x * ms + M / 2;
+  for (int k = klo; k <= khi; ++k) {
+    const float fk = (float)k;
+    int gix, giy;
+    float frx, fry;
+    split_pos(fk, g.x, g.y, &gix, &frx);
+    split_pos(fk, g.z, g.w, &giy, &fry);
+    const float dx = (float)(gix - bx0) + frx, dy = (float)(giy - by0) + fry;
+    float wy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) wy[r] = es_weight(dy - (float)r, beta, tw);
+    const float2 v = __ldg(row + m.y * k);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      const float wx = es_weight(dx - (float)c, beta, tw);
+      const float2 vx = make_float2(v.x * wx, v.y * wx);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        acc[r][c].x = fmaf(vx.x, wy[r], acc[r][c].x);
+        acc[r][c].y = fmaf(vx.y, wy[r], acc[r][c].y);
+      }
     }
-    if (lane < nw) warp_tot[lane] = x;  // inclusive over warps
   }
-  __syncthreads();
-  int run = inc - sum + (wid > 0 ? warp_tot[wid - 1] : 0);
-  for (int i = b; i < e; ++i) {
-    const int c = v[i];
-    v[i] = run;
-    run += c;
-  }
-  if (tid == nthr - 1) v[n] = run;
-  __syncthreads();
 }
 
-template <int W>
-__global__ void __launch_bounds__(512) k_frec_spread(const float2* __restrict__ P, int64_t p_pair, int ms,
-                                                     const float4* __restrict__ geom, int nt, int M, int lgL,
-                                                     int cw, int n, const float2* __restrict__ twL,
-                                                     const float* __restrict__ dec, float beta,
-                                                     float2* __restrict__ H, int64_t h_pair) {
+// Gather: thread t owns a block of R x CW grid nodes (CW columns, R rows) in
+// a 64 x 64-node tile per CTA (warps: 8 x 4 blocks), with signed node
+// coordinates and their images shifted by -L (samples lie in [-L/2, L/2]),
+// and adds every sample whose window reaches the block -- no atomics, no
+// shared memory.  Warps with a block within kCoopRadius of the zero
+// frequency (where every angle contributes) take their blocks one at a time
+// and share each block's angles among the lanes, reducing with shuffles.
+// Output: the grid G[pair][gx][gy] (column-major), written from registers.
+constexpr float kCoopRadius = 384.f;
+constexpr int kTile = 64;  // nodes per CTA tile side
+
+template <int R, int CW>
+__global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __restrict__ P, int64_t p_pair, int ms,
+                                                     const float4* __restrict__ geomS, const int2* __restrict__ meta,
+                                                     const float* __restrict__ thS, int nt, int M, int lgL, float beta,
+                                                     float2* __restrict__ G, int64_t g_pair) {
+  const int L = 1 << lgL;
+  const int pb = blockIdx.z;
+  const float2* Pp = P + (int64_t)pb * p_pair;
+  float2* Gp = G + (int64_t)pb * g_pair;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // warp tile: 8 blocks across (8 CW columns), 4 blocks down (4 R rows)
+  constexpr int kWarpCols = 8 * CW, kWarpRows = 4 * R;
+  constexpr int kWarpsX = kTile / kWarpCols;
+  const int tx0 = blockIdx.x * kTile + (wid % kWarpsX) * kWarpCols;
+  const int ty0 = blockIdx.y * kTile + (wid / kWarpsX) * kWarpRows;
+  const int gx0 = tx0 + (lane & 7) * CW, gy0 = ty0 + (lane >> 3) * R;
+  const bool own = gx0 < L && gy0 < L;
+  auto reachable = [&](int b0, int ext) { return !(2 * (b0 + ext - 1) <= -L - W || 2 * b0 >= L + W); };
+  bool near = false;
+  if (own) {
+    for (int mx = 0; mx >= -1; --mx)
+      for (int my = 0; my >= -1; --my) {
+        const int bx0 = gx0 + mx * L, by0 = gy0 + my * L;
+        if (!reachable(bx0, CW) || !reachable(by0, R)) continue;
+        const float xc = bx0 + 0.5f * (CW - 1), yc = by0 + 0.5f * (R - 1);
+        near |= xc * xc + yc * yc < kCoopRadius * kCoopRadius;
+      }
+  }
+  float2 acc[R][CW];
+  if (!__any_sync(0xffffffffu, near)) {
+    if (!own) return;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < CW; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int mx = 0; mx >= -1; --mx)
+      for (int my = 0; my >= -1; --my) {
+        const int bx0 = gx0 + mx * L, by0 = gy0 + my * L;
+        if (!reachable(bx0, CW) || !reachable(by0, R)) continue;
+        int2 rng[2];
+        const int nr = block_angles<R, CW>(W, bx0, by0, thS, nt, rng);
+        for (int q = 0; q < nr; ++q)
+          for (int u = rng[q].x; u < rng[q].y; ++u)
+            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, beta, acc);
+      }
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+#pragma unroll
+      for (int r = 0; r < R; ++r) Gp[(int64_t)(gx0 + c) * L + gy0 + r] = acc[r][c];
+    return;
+  }
+  // cooperative: the warp's 32 blocks one at a time, angles split over lanes
+  for (int bi = 0; bi < 32; ++bi) {
+    const int bx = tx0 + (bi & 7) * CW, by = ty0 + (bi >> 3) * R;
+    if (bx >= L || by >= L) continue;  // uniform over the warp
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < CW; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int mx = 0; mx >= -1; --mx)
+      for (int my = 0; my >= -1; --my) {
+        const int bx0 = bx + mx * L, by0 = by + my * L;
+        if (!reachable(bx0, CW) || !reachable(by0, R)) continue;
+        int2 rng[2];
+        const int nr = block_angles<R, CW>(W, bx0, by0, thS, nt, rng);
+        for (int q = 0; q < nr; ++q)
+          for (int u = rng[q].x + lane; u < rng[q].y; u += 32)
+            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, beta, acc);
+      }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        float x = acc[r][c].x, y = acc[r][c].y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          x += __shfl_xor_sync(0xffffffffu, x, o);
+          y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        if (lane == (r * CW + c) % 32) Gp[(int64_t)(bx + c) * L + by + r] = make_float2(x, y);
+      }
+  }
+}
+
+// Column pass: one CTA per strip of CW grid columns (contiguous in G): the
+// columns' inverse FFTs in shared memory, then rows y in [-n/2, n/2) are
+// kept, times 1/Phi(y/L) -> H[pair][iy][gx].
+__global__ void __launch_bounds__(1024) k_frec_cols(const float2* __restrict__ G, int64_t g_pair, int lgL, int cw,
+                                                    int n, const float2* __restrict__ twL,
+                                                    const float* __restrict__ dec, float2* __restrict__ H,
+                                                    int64_t h_pair) {
   extern __shared__ float4 frec_smem4[];
   const int L = 1 << lgL;
   float2* strip = reinterpret_cast<float2*>(frec_smem4);  // [cw][L]
-  int* off = reinterpret_cast<int*>(strip + cw * L);      // [nt + 1]
   const int gx0 = blockIdx.x * cw, pb = blockIdx.y;
-  const float2* Pp = P + (int64_t)pb * p_pair;
-  for (int i = threadIdx.x; i < cw * L; i += blockDim.x) strip[i] = make_float2(0.f, 0.f);
+  const float4* src = reinterpret_cast<const float4*>(G + (int64_t)pb * g_pair + (int64_t)gx0 * L);
+  float4* dst = reinterpret_cast<float4*>(strip);
+  for (int i = threadIdx.x; i < (cw * L) / 2; i += blockDim.x) dst[i] = __ldg(src + i);
   __syncthreads();
-  // The strip's columns as signed frequencies: image 0 is [gx0, gx0 + cw),
-  // image -1 the same columns minus L (nodes lie in (-L/2 - W/2, L/2 + W/2)).
-  for (int img = 0; img >= -1; --img) {
-    const int lo = gx0 + img * L, hi = lo + cw - 1;
-    if (2 * hi <= -L - W || 2 * lo >= L + W) continue;  // uniform over the CTA
-    const float A = (float)lo - 0.5f * W, B = (float)hi + 0.5f * W;
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      int klo, khi;
-      k_range(__ldg(&geom[t].x), A, B, M, &klo, &khi);
-      off[t] = max(0, khi - klo + 1);
-    }
-    __syncthreads();
-    block_scan(off, nt);
-    const int total = off[nt];
-    const int per = (total + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int i0 = min(total, (int)threadIdx.x * per), i1 = min(total, i0 + per);
-    if (i0 < i1) {
-      int a = 0, b = nt;  // largest t with off[t] <= i0
-      while (b - a > 1) {
-        const int mid = (a + b) >> 1;
-        if (off[mid] <= i0) a = mid; else b = mid;
-      }
-      int t = a;
-      int klo, khi;
-      float4 g = __ldg(geom + t);
-      k_range(g.x, A, B, M, &klo, &khi);
-      int k = klo + (i0 - off[t]);
-      for (int it = i0; it < i1; ++it, ++k) {
-        while (it >= off[t + 1]) {
-          ++t;
-          g = __ldg(geom + t);
-          k_range(g.x, A, B, M, &klo, &khi);
-          k = klo;
-        }
-        const float2 v = __ldg(Pp + (int64_t)t * ms + k + M / 2);
-        const float fk = (float)k;
-        int gix, giy;
-        float frx, fry;
-        split_pos(fk, g.x, g.y, &gix, &frx);
-        split_pos(fk, g.z, g.w, &giy, &fry);
-        const float bx = frx - 0.5f * W, by = fry - 0.5f * W;
-        const float fbx = floorf(bx), fby = floorf(by);
-        const float tx = bx - fbx, ty = by - fby;
-        const int g0x = gix + (int)fbx + 1, g0y = giy + (int)fby + 1;
-        float wy[W];
-#pragma unroll
-        for (int r = 0; r < W; ++r) wy[r] = es_weight<W>(ty + (0.5f * W - 1.f - r), beta);
-#pragma unroll
-        for (int i = 0; i < W; ++i) {
-          const int c = g0x + i - lo;
-          if (c < 0 || c >= cw) continue;
-          const float2 vx = cscale(v, es_weight<W>(tx + (0.5f * W - 1.f - i), beta));
-          float2* col = strip + c * L;
-#pragma unroll
-          for (int r = 0; r < W; ++r) {
-            float2* q = col + ((g0y + r) & (L - 1));
-            atomicAdd(&q->x, vx.x * wy[r]);
-            atomicAdd(&q->y, vx.y * wy[r]);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
   fft_dif<true>(strip, lgL, cw, twL);
   float2* Hp = H + (int64_t)pb * h_pair;
   for (int i = threadIdx.x; i < n * cw; i += blockDim.x) {
@@ -363,9 +454,15 @@ __global__ void __launch_bounds__(256) k_frec_out(const float2* __restrict__ H, 
 
 // --------------------------------------------------------- host tables --
 
+struct SortedAngles {
+  std::vector<double> theta;
+  int2* meta = nullptr;   // (original index, sign of k) per sorted position
+  float* thS = nullptr;   // theta' in [0, pi), ascending
+};
 struct HostTables {
   std::map<std::pair<int, int>, float2*> tw;                 // (dev, N) -> e^{-2 pi i j / N}
   std::map<std::tuple<int, int, int, int>, float*> dec;      // (dev, n, L, W) -> 1 / Phi(x / L)
+  std::map<int, std::vector<SortedAngles>> ang;              // dev -> angle arrays seen
 };
 std::mutex g_frec_mu;
 HostTables g_frec;
@@ -440,6 +537,59 @@ tcp_status get_deconv(int dev, int n, int L, int W, const float** out) {
   return TCP_OK;
 }
 
+// Angles folded to theta' = theta mod pi in [0, pi) (k changes sign when
+// theta mod 2 pi >= pi: the same line through the origin), sorted ascending.
+tcp_status get_sorted_angles(int dev, const double* theta, int nt, const int2** meta, const float** thS) {
+  std::lock_guard<std::mutex> lk(g_frec_mu);
+  auto& lst = g_frec.ang[dev];
+  for (auto& e : lst)
+    if ((int)e.theta.size() == nt && std::equal(e.theta.begin(), e.theta.end(), theta)) {
+      *meta = e.meta;
+      *thS = e.thS;
+      return TCP_OK;
+    }
+  std::vector<std::pair<double, int2>> v((size_t)nt);
+  for (int t = 0; t < nt; ++t) {
+    double a = std::fmod(theta[t], 2.0 * M_PI);
+    if (a < 0.0) a += 2.0 * M_PI;
+    int sg = 1;
+    if (a >= M_PI) {
+      a -= M_PI;
+      sg = -1;
+    }
+    if (a >= M_PI) a = 0.0;  // rounding at the top of the range
+    v[(size_t)t] = {a, make_int2(t, sg)};
+  }
+  std::stable_sort(v.begin(), v.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+    return x.first < y.first;
+  });
+  std::vector<int2> hm((size_t)nt);
+  std::vector<float> ht((size_t)nt);
+  for (int u = 0; u < nt; ++u) {
+    hm[(size_t)u] = v[(size_t)u].second;
+    ht[(size_t)u] = (float)v[(size_t)u].first;
+  }
+  SortedAngles e;
+  e.theta.assign(theta, theta + nt);
+  TCP_CUDA_TRY(cudaMalloc(&e.meta, sizeof(int2) * (size_t)std::max(nt, 1)));
+  cudaError_t err = cudaMalloc(&e.thS, sizeof(float) * (size_t)std::max(nt, 1));
+  if (err != cudaSuccess) {
+    cudaFree(e.meta);
+    return cuda_fail(err, "cudaMalloc");
+  }
+  err = cudaMemcpy(e.meta, hm.data(), sizeof(int2) * (size_t)nt, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(e.thS, ht.data(), sizeof(float) * (size_t)nt, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(e.meta);
+    cudaFree(e.thS);
+    return cuda_fail(err, "upload FourierRec angle table");
+  }
+  lst.push_back(e);
+  *meta = e.meta;
+  *thS = e.thS;
+  return TCP_OK;
+}
+
 template <class TS>
 void launch_rows(const View3& sv, int z0, int nb, int lgM, const float2* twM, const float2* phase, float2* P,
                  int64_t p_pair, int ms, cudaStream_t st) {
@@ -449,14 +599,22 @@ void launch_rows(const View3& sv, int z0, int nb, int lgM, const float2* twM, co
       (const TS*)sv.p, sv.s0, sv.s1, (int)sv.d0, (int)sv.d2, z0, lgM, twM, phase, P, p_pair, ms);
 }
 
-template <int W>
-void launch_spread(const float2* P, int64_t p_pair, int ms, const float4* geom, int nt, int M, int lgL, int cw, int n,
-                   const float2* twL, const float* dec, float2* H, int64_t h_pair, int nb, cudaStream_t st) {
+template <int R, int CW>
+void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4* geomS, const int2* meta,
+                   const float* thS, int nt, int M, int lgL, float2* G, int64_t g_pair, int nb, cudaStream_t st) {
   const int L = 1 << lgL;
-  const size_t sm = sizeof(float2) * (size_t)cw * L + sizeof(int) * (size_t)(nt + 1);
-  cudaFuncSetAttribute(k_frec_spread<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_frec_spread<W><<<dim3((unsigned)(L / cw), (unsigned)nb), 512, sm, st>>>(P, p_pair, ms, geom, nt, M, lgL, cw, n, twL,
-                                                                          dec, (float)es_beta(W), H, h_pair);
+  const unsigned tiles = (unsigned)((L + kTile - 1) / kTile);
+  k_frec_gather<R, CW><<<dim3(tiles, tiles, (unsigned)nb), 256, 0, st>>>(W, P, p_pair, ms, geomS, meta, thS, nt, M,
+                                                                        lgL, (float)es_beta(W), G, g_pair);
+}
+
+void launch_cols(const float2* G, int64_t g_pair, int lgL, int n, const float2* twL, const float* dec, float2* H,
+                 int64_t h_pair, int nb, cudaStream_t st) {
+  const int L = 1 << lgL;
+  const int cw = std::max(1, std::min(std::min(4, L), (1 << kMaxLg) / L));
+  const size_t sm = sizeof(float2) * (size_t)cw * L;
+  cudaFuncSetAttribute(k_frec_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_frec_cols<<<dim3((unsigned)(L / cw), (unsigned)nb), 1024, sm, st>>>(G, g_pair, lgL, cw, n, twL, dec, H, h_pair);
 }
 
 template <class TV>
@@ -489,15 +647,14 @@ tcp_status fourierrec_check(int64_t nt, int64_t nd, int64_t n, int width) {
   return TCP_OK;
 }
 
-tcp_status launch_fourierrec(const View3& sv, const TrigTable& trig, double center, const View3& vv, float scale,
-                             int width, cudaStream_t st) {
+tcp_status launch_fourierrec(const View3& sv, const double* theta, const TrigTable& trig, double center,
+                             const View3& vv, float scale, int width, cudaStream_t st) {
   const int nz = (int)sv.d0, nt = (int)sv.d1, nd = (int)sv.d2, n = (int)vv.d1;
   tcp_status s;
   if ((s = fourierrec_check(nt, nd, n, width)) != TCP_OK) return s;
   const int lgM = std::max(1, ilog2(2 * (int64_t)nd)), lgL = std::max(1, ilog2(2 * (int64_t)n));
   const int M = 1 << lgM, L = 1 << lgL;
   const int ms = M + 1;
-  const int cw = std::max(1, std::min(std::min(4, L), (1 << kMaxLg) / L));
   int dev = 0;
   TCP_CUDA_TRY(cudaGetDevice(&dev));
   const float2 *twM = nullptr, *twL = nullptr;
@@ -505,10 +662,13 @@ tcp_status launch_fourierrec(const View3& sv, const TrigTable& trig, double cent
   if ((s = get_twiddles(dev, M, &twM)) != TCP_OK) return s;
   if ((s = get_twiddles(dev, L, &twL)) != TCP_OK) return s;
   if ((s = get_deconv(dev, n, L, width, &dec)) != TCP_OK) return s;
+  const int2* meta = nullptr;
+  const float* thS = nullptr;
+  if ((s = get_sorted_angles(dev, theta, nt, &meta, &thS)) != TCP_OK) return s;
 
   const int npairs = (nz + 1) / 2;
-  const int64_t p_pair = (int64_t)nt * ms, h_pair = (int64_t)n * L;
-  const size_t per_pair = sizeof(float2) * (size_t)(p_pair + h_pair);
+  const int64_t p_pair = (int64_t)nt * ms, h_pair = (int64_t)n * L, g_pair = (int64_t)L * L;
+  const size_t per_pair = sizeof(float2) * (size_t)(p_pair + h_pair + g_pair);
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(npairs, (int64_t)(kBatchBytes / per_pair)));
 
   struct Ws {
@@ -524,15 +684,16 @@ tcp_status launch_fourierrec(const View3& sv, const TrigTable& trig, double cent
       return TCP_OK;
     }
   } ws{st, {}};
-  void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr;
+  void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
   if ((s = ws.alloc(&geom, sizeof(float4) * (size_t)nt)) != TCP_OK) return s;
   if ((s = ws.alloc(&phase, sizeof(float2) * (size_t)ms)) != TCP_OK) return s;
   if ((s = ws.alloc(&P, sizeof(float2) * (size_t)p_pair * nb)) != TCP_OK) return s;
   if ((s = ws.alloc(&H, sizeof(float2) * (size_t)h_pair * nb)) != TCP_OK) return s;
+  if ((s = ws.alloc(&G, sizeof(float2) * (size_t)g_pair * nb)) != TCP_OK) return s;
   {
     const int cnt = std::max(nt, ms);
-    k_frec_geom<<<(cnt + 255) / 256, 256, 0, st>>>(trig.dev, nt, (double)L / (double)M, (float4*)geom, center, M,
-                                                     (float2*)phase);
+    k_frec_geom<<<(cnt + 255) / 256, 256, 0, st>>>(trig.dev, meta, nt, (double)L / (double)M, (float4*)geom,
+                                                     center, M, (float2*)phase);
     TCP_CUDA_TRY(cudaGetLastError());
   }
   for (int p0 = 0; p0 < npairs; p0 += nb) {
@@ -546,18 +707,10 @@ tcp_status launch_fourierrec(const View3& sv, const TrigTable& trig, double cent
       default: return fail(TCP_ERR_DTYPE, "fourierrec: sino must be F32, F16 or BF16");
     }
     TCP_CUDA_TRY(cudaGetLastError());
-#define TCP_FREC_W(w)                                                                                         \
-  case w:                                                                                                     \
-    launch_spread<w>((const float2*)P, p_pair, ms, (const float4*)geom, nt, M, lgL, cw, n, twL, dec, (float2*)H, \
-                     h_pair, b, st);                                                                          \
-    break;
-    switch (width) {
-      TCP_FREC_W(2) TCP_FREC_W(3) TCP_FREC_W(4) TCP_FREC_W(5) TCP_FREC_W(6) TCP_FREC_W(7) TCP_FREC_W(8)
-      TCP_FREC_W(9) TCP_FREC_W(10) TCP_FREC_W(11) TCP_FREC_W(12) TCP_FREC_W(13) TCP_FREC_W(14) TCP_FREC_W(15)
-      TCP_FREC_W(16)
-      default: return fail(TCP_ERR_ARG, "fourierrec: width must be in [2, 16]");
-    }
-#undef TCP_FREC_W
+    launch_gather<4, 4>(width, (const float2*)P, p_pair, ms, (const float4*)geom, meta, thS, nt, M, lgL, (float2*)G,
+                        g_pair, b, st);
+    TCP_CUDA_TRY(cudaGetLastError());
+    launch_cols((const float2*)G, g_pair, lgL, n, twL, dec, (float2*)H, h_pair, b, st);
     TCP_CUDA_TRY(cudaGetLastError());
     View3 ov = vv;
     switch (vv.dtype) {

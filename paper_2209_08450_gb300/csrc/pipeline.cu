@@ -147,11 +147,21 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   // (FP32-accurate on the tensor cores; needs ndet % 8 == 0 for 16-byte rows,
   // FP32 otherwise) and the volume's own type for 16-bit volumes.
   int sdt = o.sino_dtype;
+  if (o.algorithm != TCP_ALG_LINEREC && o.algorithm != TCP_ALG_FOURIERREC)
+    return fail(TCP_ERR_ARG, "fbp: unknown algorithm");
+  const bool frec = o.algorithm == TCP_ALG_FOURIERREC;
   if (sdt != TCP_F32 && sdt != TCP_F16 && sdt != TCP_BF16 && sdt != TCP_F16X2)
-    sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 ? TCP_F16X2 : TCP_F32);
+    sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 && !frec ? TCP_F16X2 : TCP_F32);
+  if (frec && sdt == TCP_F16X2) return fail(TCP_ERR_DTYPE, "fbp: FourierRec takes F32, F16 or BF16 sinograms");
+  const int frec_width = o.width == 0 ? fourierrec_default_width(vol->dtype, n) : o.width;
+  if (frec) {
+    tcp_status sf = fourierrec_check(nt, nd, n, frec_width);
+    if (sf != TCP_OK) return sf;
+  }
   // default chunk: 256 slices for 16-bit sinograms (the tensor-core
-  // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel)
-  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : (sdt == TCP_F32 ? 32 : 256);
+  // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel), 64 for
+  // FourierRec (32 slice pairs)
+  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : frec ? 64 : (sdt == TCP_F32 ? 32 : 256);
   if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
   if (!valid_pad_mode(o.pad_mode)) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
   const int B = o.n_buffers == 3 ? 3 : 2;
@@ -263,7 +273,10 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
       vv.p = (char*)vol->data + z0 * vol->stride[0] * esize(vol->dtype);
       vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
     }
-    TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st, bp_scale));
+    if (frec)
+      TRY_S(launch_fourierrec(sv, theta, trig, 0.5 * (double)nd, vv, bp_scale, frec_width, st));
+    else
+      TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st, bp_scale));
     if (host_vol) {
       const int es = esize(vol->dtype);
       TCP_CUDA_TRY(cudaEventRecord(vol_ready[b], st));

@@ -161,3 +161,23 @@ def test_fourierrec_argument_checks(lib):
     assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, 8.0, ctypes.byref(tiny), 1.0, 5, None) == 1
     assert _status(lib, "tcp_fourierrec", ctypes.byref(sino), th, float("nan"), ctypes.byref(vol), 1.0, 0,
                    None) == 1
+
+
+def test_fbp_algorithm_checks(lib):
+    raw = _t(_lib.U16, (4, 2, 16), ptr=1 << 20)
+    dark = _t(_lib.F32, (2, 16), ptr=1 << 21)
+    flat = _t(_lib.F32, (2, 16), ptr=1 << 22)
+    vol = _t(_lib.F32, (2, 16, 16), ptr=1 << 23)
+    th = (ctypes.c_double * 4)(0, 0.5, 1.0, 1.5)
+    o = _lib.FbpOpts()
+    o.algorithm = 7
+    assert _status(lib, "tcp_fbp", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat), th, 8.0,
+                   ctypes.byref(vol), ctypes.byref(o), None) == 1
+    o.algorithm = _lib.ALGORITHMS["fourierrec"]
+    o.sino_dtype = _lib.F16X2
+    assert _status(lib, "tcp_fbp", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat), th, 8.0,
+                   ctypes.byref(vol), ctypes.byref(o), None) == 3
+    o.sino_dtype = -1
+    odd = _t(_lib.F32, (2, 15, 15), ptr=1 << 23)
+    assert _status(lib, "tcp_fbp", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat), th, 8.0,
+                   ctypes.byref(odd), ctypes.byref(o), None) == 2
