@@ -392,8 +392,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=2048)
     ap.add_argument("--nz", type=int, default=0, help="slices (default: size); a small case of the same launches")
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "f32_cuda"],
-                    help="headline path (f32: FP32 volume from FP16 hi/lo sinogram pairs on the tensor cores)")
+    ap.add_argument("--dtype", default="f32", choices=list(PATHS),
+                    help="headline path (f32: FP32 volume from FP16 hi/lo sinogram pairs on the tensor cores; "
+                         "*_frec: FourierRec)")
     ap.add_argument("--chunk", type=int, default=0, help="slices per chunk (0: the path's default)")
     ap.add_argument("--variants", default="f32,f16,bf16,f32_cuda,f32_frec,f16_frec")
     ap.add_argument("--variant-steps", type=int, default=2)
@@ -494,7 +495,7 @@ def main():
         return float(max(errs))
 
     zs = [int(x) for x in np.linspace(nz // 5, 4 * nz // 5, args.parity_slices)]
-    par = {args.dtype: parity(vol, zs)} if rank == 0 and zs else {}
+    par = {args.dtype: parity(vol, zs, hp)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
     dm, fm = tcp.frame_mean(dark), tcp.frame_mean(flat)
@@ -577,6 +578,7 @@ def main():
 
         def e2e_step():
             tcp.fbp(raw_h, dark_h, flat_h, theta, center, out=vol_h, chunk_nz=chunk_for(hp), sino_dtype=sdt_of(hp),
+                    algorithm="fourierrec" if hp in FOURIERREC else "linerec", width=FOURIERREC.get(hp, 0),
                     stream=stream)
         e2e_step()
         torch.cuda.synchronize()
@@ -595,7 +597,7 @@ def main():
                "h2d_bytes_per_step": raw_h.numel() * 2 + dark_h.numel() * 2 + flat_h.numel() * 2,
                "d2h_bytes_per_step": vol_h.numel() * vol_h.element_size()}
         if rank == 0 and zs:
-            par[args.dtype + "_e2e"] = parity(vol_h, zs[:1])
+            par[args.dtype + "_e2e"] = parity(vol_h, zs[:1], hp)
         del raw_h, vol_h
 
     rows = None
@@ -605,14 +607,30 @@ def main():
         rows = measure_rows(dev)
     cpu = cpu_baseline(n, nt, args.cpu_slices) if rank == 0 and world == 1 and args.cpu_slices > 0 else None
     if rank == 0:
-        launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
+        if hp in FOURIERREC:
+            # per chunk: normalise+filter, the angle/phase table kernel, and per
+            # batch of slice pairs: row FFT, gather, column and row inverse FFTs
+            m = l = 1
+            while m < 2 * n:
+                m *= 2
+            while l < 2 * n:
+                l *= 2
+            per_pair = 8 * (nt * (m + 1) + n * l + l * l)
+            cz = min(chunk_for(hp), nz)
+            nb = max(1, min((cz + 1) // 2, (3 << 29) // per_pair))
+            per_chunk = [2 + 4 * (((min(cz, nz - z0) + 1) // 2 + nb - 1) // nb) for z0 in range(0, nz, cz)]
+            launches_per_step = 2 + sum(per_chunk)
+        else:
+            launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
         out = {
             "metric": METRIC, "value": value, "unit": "GVoxel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": "f32" if hp.startswith("f32") else hp,
             "path": hp, "data": DATA,
-            "config": {"workload": "%dx%d^2 FBP (LineRec) from %d uint16 projections of %dx%d, angles on [0, pi), "
-                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM" % (nz, n, nt, n, nz, chunk_for(hp)),
+            "config": {"workload": "%dx%d^2 FBP (%s) from %d uint16 projections of %dx%d, angles on [0, pi), "
+                                   "Shepp-Logan filter, %d-slice chunks, inputs resident in HBM"
+                                   % (nz, n, "FourierRec, window %d" % FOURIERREC[hp] if hp in FOURIERREC else "LineRec",
+                                      nt, n, nz, chunk_for(hp)),
                        "n": n, "nz": nz, "ntheta": nt, "chunk_nz": chunk_for(hp),
                        "sino_storage": "f16x2" if hp == "f32" else (PATHS[hp][1] or PATHS[hp][0]),
                        "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
