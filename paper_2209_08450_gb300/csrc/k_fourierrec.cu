@@ -183,13 +183,17 @@ __device__ __forceinline__ void split_pos(float fk, float hi, float lo, int* gi,
 }
 
 // Window weight at distance d (grid points): exp(beta (sqrt(1 - (2d/W)^2) - 1))
-// inside |d| < W/2, else 0.  The fast exponential and reciprocal square root
-// keep the weight within ~1e-6 relative, well inside the window's own error
-// at the default widths.
-__device__ __forceinline__ float es_weight(float d, float beta, float two_over_w) {
+// inside |d| < W/2, else 0, as 2^(bl2 (sqrt(z) - 1)) with bl2 = beta log2(e).
+// The approximate square root and base-2 exponential (~2^-22 relative each)
+// keep the weight within ~2e-6 relative, inside the window's own error at the
+// default widths.
+__device__ __forceinline__ float es_weight(float d, float bl2, float two_over_w) {
   const float s = d * two_over_w;
-  const float z = 1.f - s * s;
-  return z > 0.f ? __expf(beta * (z * rsqrtf(z) - 1.f)) : 0.f;
+  const float z = fmaf(-s, s, 1.f);
+  float q, w;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(z));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(w) : "f"(fmaf(bl2, q, -bl2)));
+  return z > 0.f ? w : 0.f;  // z <= 0: outside the window (sqrt of a negative is NaN, discarded)
 }
 
 // Intersect [klo, khi] with the integers k for which k * c lies in (A, B),
@@ -273,7 +277,7 @@ __device__ __forceinline__ int block_angles(int W, int bx0, int by0, const float
 template <int R, int CW>
 __device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, const float2* __restrict__ Pp, int ms,
                                              int M, const float4* __restrict__ geomS, const int2* __restrict__ meta,
-                                             float beta, float2 (&acc)[R][CW]) {
+                                             float bl2, float2 (&acc)[R][CW]) {
   const float tw = 2.f / (float)W;
   const float4 g = __ldg(geomS + u);
   int klo = -M / 2, khi = M / 2;
@@ -283,26 +287,50 @@ __device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, con
   if (klo > khi) return;
   const int2 m = __ldg(meta + u);  // original angle, sign of k
   const float2* row = Pp + (int64_t)m.x * ms + M / 2;
+  // positions k * (hi + lo) as integer part + fraction: exact split at klo,
+  // then steps by the exact integer/fraction split of the increment (the
+  // fraction's rounding is <= 2^-24 per step)
+  const float fk0 = (float)klo;
+  int gix, giy;
+  float frx, fry;
+  split_pos(fk0, g.x, g.y, &gix, &frx);
+  split_pos(fk0, g.z, g.w, &giy, &fry);
+  const float flx = floorf(g.x), fly = floorf(g.z);
+  const int sxi = (int)flx, syi = (int)fly;
+  const float sxf = (g.x - flx) + g.y, syf = (g.z - fly) + g.w;
   for (int k = klo; k <= khi; ++k) {
-    const float fk = (float)k;
-    int gix, giy;
-    float frx, fry;
-    split_pos(fk, g.x, g.y, &gix, &frx);
-    split_pos(fk, g.z, g.w, &giy, &fry);
     const float dx = (float)(gix - bx0) + frx, dy = (float)(giy - by0) + fry;
     float wy[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) wy[r] = es_weight(dy - (float)r, beta, tw);
+    for (int r = 0; r < R; ++r) wy[r] = es_weight(dy - (float)r, bl2, tw);
     const float2 v = __ldg(row + m.y * k);
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
-      const float wx = es_weight(dx - (float)c, beta, tw);
+      const float wx = es_weight(dx - (float)c, bl2, tw);
       const float2 vx = make_float2(v.x * wx, v.y * wx);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         acc[r][c].x = fmaf(vx.x, wy[r], acc[r][c].x);
         acc[r][c].y = fmaf(vx.y, wy[r], acc[r][c].y);
       }
+    }
+    frx += sxf;
+    gix += sxi;
+    if (frx >= 1.f) {
+      frx -= 1.f;
+      ++gix;
+    } else if (frx < 0.f) {
+      frx += 1.f;
+      --gix;
+    }
+    fry += syf;
+    giy += syi;
+    if (fry >= 1.f) {
+      fry -= 1.f;
+      ++giy;
+    } else if (fry < 0.f) {
+      fry += 1.f;
+      --giy;
     }
   }
 }
@@ -321,7 +349,7 @@ constexpr int kTile = 64;  // nodes per CTA tile side
 template <int R, int CW>
 __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __restrict__ P, int64_t p_pair, int ms,
                                                      const float4* __restrict__ geomS, const int2* __restrict__ meta,
-                                                     const float* __restrict__ thS, int nt, int M, int lgL, float beta,
+                                                     const float* __restrict__ thS, int nt, int M, int lgL, float bl2,
                                                      float2* __restrict__ G, int64_t g_pair) {
   const int L = 1 << lgL;
   const int pb = blockIdx.z;
@@ -361,7 +389,7 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
         const int nr = block_angles<R, CW>(W, bx0, by0, thS, nt, rng);
         for (int q = 0; q < nr; ++q)
           for (int u = rng[q].x; u < rng[q].y; ++u)
-            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, beta, acc);
+            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, bl2, acc);
       }
 #pragma unroll
     for (int c = 0; c < CW; ++c)
@@ -385,7 +413,7 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
         const int nr = block_angles<R, CW>(W, bx0, by0, thS, nt, rng);
         for (int q = 0; q < nr; ++q)
           for (int u = rng[q].x + lane; u < rng[q].y; u += 32)
-            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, beta, acc);
+            gather_angle<R, CW>(W, u, bx0, by0, Pp, ms, M, geomS, meta, bl2, acc);
       }
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -605,7 +633,7 @@ void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4*
   const int L = 1 << lgL;
   const unsigned tiles = (unsigned)((L + kTile - 1) / kTile);
   k_frec_gather<R, CW><<<dim3(tiles, tiles, (unsigned)nb), 256, 0, st>>>(W, P, p_pair, ms, geomS, meta, thS, nt, M,
-                                                                        lgL, (float)es_beta(W), G, g_pair);
+                                                                        lgL, (float)(es_beta(W) / M_LN2), G, g_pair);
 }
 
 void launch_cols(const float2* G, int64_t g_pair, int lgL, int n, const float2* twL, const float* dec, float2* H,
