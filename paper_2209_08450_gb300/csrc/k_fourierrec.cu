@@ -63,9 +63,21 @@ __device__ __forceinline__ int dif_pos(int k, int lg) {
   return pos;
 }
 
+// Shared-memory index of logical element g of an FFT buffer: the low four
+// bits are XORed with bits 4..7 (rotated), a bijection within every aligned
+// block of 16 elements.  It spreads the radix-4 stages with butterfly stride 4
+// and 1 (and the output gathers) over all banks; stages with stride >= 16 see
+// a permutation of 16 consecutive elements, as before.  Every access to an
+// FFT buffer goes through it.
+__device__ __forceinline__ int swz(int g) {
+  const int h = g >> 4;
+  return g ^ (((h & 3) << 2) | ((h >> 2) & 3));
+}
+
 // In-place decimation-in-frequency FFT of `count` sequences of length
-// N = 2^lg stored back to back in shared memory.  tw[j] = e^{-2 pi i j / N};
-// INV takes the conjugates (positive exponent, no 1/N).  The caller
+// N = 2^lg stored back to back in shared memory (swizzled, swz).
+// tw[j] = e^{-2 pi i j / N}; INV takes the conjugates (positive exponent, no
+// 1/N); w^2 and w^3 of a butterfly are formed from w.  The caller
 // synchronises before; this returns synchronised.
 template <bool INV>
 __device__ void fft_dif(float2* a, int lg, int count, const float2* __restrict__ tw) {
@@ -78,31 +90,29 @@ __device__ void fft_dif(float2* a, int lg, int count, const float2* __restrict__
     for (int b = tid; b < nb; b += nthr) {
       const int seq = b >> (lg - 2), bb = b & (per_seq - 1);
       const int blk = bb >> lgm, j = bb & (m - 1);
-      float2* p = a + (seq << lg) + (blk << lgs) + j;
-      const float2 x0 = p[0], x1 = p[m], x2 = p[2 * m], x3 = p[3 * m];
+      const int e0 = (seq << lg) + (blk << lgs) + j;
+      const int i0 = swz(e0), i1 = swz(e0 + m), i2 = swz(e0 + 2 * m), i3 = swz(e0 + 3 * m);
+      const float2 x0 = a[i0], x1 = a[i1], x2 = a[i2], x3 = a[i3];
       const float2 s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = csub(x1, x3);
       // omega_4 = -i (forward) or +i (inverse) times d13
       const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-      float2 w1 = __ldg(tw + j * ts), w2 = __ldg(tw + 2 * j * ts), w3 = __ldg(tw + 3 * j * ts);
-      if (INV) {
-        w1.y = -w1.y;
-        w2.y = -w2.y;
-        w3.y = -w3.y;
-      }
-      p[0] = cadd(s02, s13);
-      p[m] = cmul(cadd(d02, r13), w1);
-      p[2 * m] = cmul(csub(s02, s13), w2);
-      p[3 * m] = cmul(csub(d02, r13), w3);
+      float2 w1 = __ldg(tw + j * ts);
+      if (INV) w1.y = -w1.y;
+      const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+      a[i0] = cadd(s02, s13);
+      a[i1] = cmul(cadd(d02, r13), w1);
+      a[i2] = cmul(csub(s02, s13), w2);
+      a[i3] = cmul(csub(d02, r13), w3);
     }
     __syncthreads();
   }
   if (lgs == 1) {
     const int nb = count << (lg - 1);
     for (int b = tid; b < nb; b += nthr) {
-      float2* p = a + 2 * b;
-      const float2 x0 = p[0], x1 = p[1];
-      p[0] = cadd(x0, x1);
-      p[1] = csub(x0, x1);
+      const int i0 = swz(2 * b), i1 = swz(2 * b + 1);
+      const float2 x0 = a[i0], x1 = a[i1];
+      a[i0] = cadd(x0, x1);
+      a[i1] = csub(x0, x1);
     }
     __syncthreads();
   }
@@ -154,13 +164,13 @@ __global__ void __launch_bounds__(256) k_frec_rows(const TS* __restrict__ sino, 
       a = Store<TS>::load(r1 + j);
       if (two) b = Store<TS>::load(r2 + j);
     }
-    frec_buf[j] = make_float2(a, b);
+    frec_buf[swz(j)] = make_float2(a, b);
   }
   __syncthreads();
   fft_dif<false>(frec_buf, lgM, 1, twM);
   float2* out = P + (int64_t)pb * p_pair + (int64_t)t * ms;
   for (int i = threadIdx.x; i <= M; i += blockDim.x)
-    out[i] = cmul(frec_buf[dif_pos((i - M / 2) & (M - 1), lgM)], __ldg(phase + i));
+    out[i] = cmul(frec_buf[swz(dif_pos((i - M / 2) & (M - 1), lgM))], __ldg(phase + i));
 }
 
 // ------------------------------------------------------------- kernel 2 --
@@ -441,15 +451,14 @@ __global__ void __launch_bounds__(1024) k_frec_cols(const float2* __restrict__ G
   const int L = 1 << lgL;
   float2* strip = reinterpret_cast<float2*>(frec_smem4);  // [cw][L]
   const int gx0 = blockIdx.x * cw, pb = blockIdx.y;
-  const float4* src = reinterpret_cast<const float4*>(G + (int64_t)pb * g_pair + (int64_t)gx0 * L);
-  float4* dst = reinterpret_cast<float4*>(strip);
-  for (int i = threadIdx.x; i < (cw * L) / 2; i += blockDim.x) dst[i] = __ldg(src + i);
+  const float2* src = G + (int64_t)pb * g_pair + (int64_t)gx0 * L;
+  for (int i = threadIdx.x; i < cw * L; i += blockDim.x) strip[swz(i)] = __ldg(src + i);
   __syncthreads();
   fft_dif<true>(strip, lgL, cw, twL);
   float2* Hp = H + (int64_t)pb * h_pair;
   for (int i = threadIdx.x; i < n * cw; i += blockDim.x) {
     const int iy = i / cw, c = i - iy * cw;
-    const float2 v = strip[c * L + dif_pos((iy - n / 2) & (L - 1), lgL)];
+    const float2 v = strip[swz(c * L + dif_pos((iy - n / 2) & (L - 1), lgL))];
     Hp[(int64_t)iy * L + gx0 + c] = cscale(v, __ldg(dec + iy));
   }
 }
@@ -465,7 +474,7 @@ __global__ void __launch_bounds__(256) k_frec_out(const float2* __restrict__ H, 
   const int iy = blockIdx.x, pb = blockIdx.y;
   const int L = 1 << lgL;
   const float2* row = H + (int64_t)pb * h_pair + (int64_t)iy * L;
-  for (int j = threadIdx.x; j < L; j += blockDim.x) frec_buf[j] = __ldg(row + j);
+  for (int j = threadIdx.x; j < L; j += blockDim.x) frec_buf[swz(j)] = __ldg(row + j);
   __syncthreads();
   fft_dif<true>(frec_buf, lgL, 1, twL);
   const int z1 = z0 + 2 * pb, z2 = z1 + 1;
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(256) k_frec_out(const float2* __restrict__ H, 
   TV* o2 = vol + (int64_t)z2 * v0 + (int64_t)iy * v1;
   const bool two = z2 < nz;
   for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
-    const float2 v = frec_buf[dif_pos((ix - n / 2) & (L - 1), lgL)];
+    const float2 v = frec_buf[swz(dif_pos((ix - n / 2) & (L - 1), lgL))];
     const float d = __ldg(dec + ix) * scale;
     Store<TV>::put(o1 + ix, v.x * d);
     if (two) Store<TV>::put(o2 + ix, v.y * d);
