@@ -648,10 +648,12 @@ void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4*
 void launch_cols(const float2* G, int64_t g_pair, int lgL, int n, const float2* twL, const float* dec, float2* H,
                  int64_t h_pair, int nb, cudaStream_t st) {
   const int L = 1 << lgL;
-  const int cw = std::max(1, std::min(std::min(4, L), (1 << kMaxLg) / L));
+  // two columns (64 KB at L = 4096) per CTA: several CTAs per SM overlap one
+  // another's stage barriers
+  const int cw = std::max(1, std::min(std::min(2, L), (1 << (kMaxLg - 1)) / L));
   const size_t sm = sizeof(float2) * (size_t)cw * L;
   cudaFuncSetAttribute(k_frec_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_frec_cols<<<dim3((unsigned)(L / cw), (unsigned)nb), 1024, sm, st>>>(G, g_pair, lgL, cw, n, twL, dec, H, h_pair);
+  k_frec_cols<<<dim3((unsigned)(L / cw), (unsigned)nb), 512, sm, st>>>(G, g_pair, lgL, cw, n, twL, dec, H, h_pair);
 }
 
 template <class TV>
