@@ -128,7 +128,8 @@ tcp_status tcp_device_check(void* stream, uint32_t* word);
 /* Turn per-access index checks on (1) or off (0) for later launches. */
 tcp_status tcp_set_checked(int32_t on);
 
-/* Free every cached angle table and filter response (synchronises device). */
+/* Free every cached angle table, filter response and FourierRec table
+ * (twiddles, deconvolution factors, sorted angles); synchronises the device. */
 tcp_status tcp_cache_clear(void);
 
 /* ------------------------------------------------------------- normalise -- */
@@ -258,9 +259,9 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * "exponential of semicircle" window of `width` grid points (2..16; 0 picks
  * 7 for an F32 volume, 5 for F16/BF16, at most L): relative error about 1e-6 at 7 and
  * tenfold smaller per extra point.  Two slices share one complex transform.
- * sino:  F32/F16/BF16 [nz][ntheta][ndet], ndet <= 8192, ntheta <= 16384;
+ * sino:  F32/F16/BF16 [nz][ntheta][ndet], ndet <= 8192, ntheta <= 2^24;
  * theta: HOST FP64 [ntheta]; vol: F32/F16/BF16 [nz][n][n], n even, n <= 8192,
- * overwritten.  Works in about 1 GB of stream-ordered workspace
+ * overwritten.  Works in about 1.5 GiB of stream-ordered workspace
  * (cudaMallocAsync on `stream`).  Errors: TCP_ERR_SHAPE for odd n or sizes
  * over the limits, TCP_ERR_ARG for a width outside 2..16 or above L,
  * TCP_ERR_DTYPE for F16X2 or U16 sinograms. */

@@ -253,6 +253,7 @@ static tcp_status cache_clear() {
   g_resp.clear();
   for (auto& kv : g_tw) cudaFree(kv.second);
   g_tw.clear();
+  fourierrec_cache_clear();
   return TCP_OK;
 }
 

@@ -41,7 +41,7 @@ namespace tcp {
 namespace {
 
 constexpr int kMaxLg = 14;  // M, L <= 16384 (128 KB of complex FP32 in shared memory)
-constexpr int kMaxTheta = 16384;
+constexpr int kMaxTheta = 1 << 24;  // angle indices and counts stay far inside int
 constexpr size_t kBatchBytes = size_t(3) << 29;  // P + G + H workspace per batch (1.5 GiB)
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -667,6 +667,20 @@ void launch_out(const float2* H, int64_t h_pair, int lgL, int n, const float2* t
 
 }  // namespace
 
+void fourierrec_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_frec_mu);
+  for (auto& kv : g_frec.tw) cudaFree(kv.second);
+  g_frec.tw.clear();
+  for (auto& kv : g_frec.dec) cudaFree(kv.second);
+  g_frec.dec.clear();
+  for (auto& kv : g_frec.ang)
+    for (auto& e : kv.second) {
+      cudaFree(e.meta);
+      cudaFree(e.thS);
+    }
+  g_frec.ang.clear();
+}
+
 int fourierrec_default_width(int vol_dtype, int64_t n) {
   int64_t L = 1;
   while (L < 2 * n) L *= 2;
@@ -680,7 +694,7 @@ tcp_status fourierrec_check(int64_t nt, int64_t nd, int64_t n, int width) {
   while (L < 2 * n) L *= 2;
   if (M > (int64_t(1) << kMaxLg)) return fail(TCP_ERR_SHAPE, "fourierrec: ndet must be <= 8192");
   if (L > (int64_t(1) << kMaxLg)) return fail(TCP_ERR_SHAPE, "fourierrec: n must be <= 8192");
-  if (nt > kMaxTheta) return fail(TCP_ERR_SHAPE, "fourierrec: ntheta must be <= 16384");
+  if (nt > kMaxTheta) return fail(TCP_ERR_SHAPE, "fourierrec: ntheta must be <= 2^24");
   if (width < 2 || width > 16) return fail(TCP_ERR_ARG, "fourierrec: width must be in [2, 16]");
   if (width > L) return fail(TCP_ERR_ARG, "fourierrec: width must not exceed the grid size (2n rounded up)");
   return TCP_OK;

@@ -147,3 +147,12 @@ def test_fbp_fourierrec_ellipsoids(where, dt):
     q = oracle.filter_sino(p, ds.center, "shepp", "edge")
     ref = fr.backproject_exact(q, ds.theta, nd / 2.0, nd)
     assert rel(host(got), ref) <= (1e-5 if dt == torch.float32 else 5e-3)
+
+
+def test_fourierrec_after_cache_clear():
+    # the cached twiddle, deconvolution and sorted-angle tables are rebuilt
+    q, theta = _case(2, 24, 32, 21)
+    a = host(tcp.fourierrec(to_dev(q), theta, 16.3, n=32))
+    tcp.cache_clear()
+    b = host(tcp.fourierrec(to_dev(q), theta, 16.3, n=32))
+    np.testing.assert_array_equal(a, b)
