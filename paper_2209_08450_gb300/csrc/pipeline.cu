@@ -226,10 +226,30 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
   if (cin) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, ev_alloc, 0));
   if (cout) TCP_CUDA_TRY(cudaStreamWaitEvent(cout, ev_alloc, 0));
 
-  const int64_t nchunks = (nz + chunk - 1) / chunk;
+  // Chunk schedule.  With host buffers the first chunk's upload and the last
+  // chunk's download are not hidden behind compute, so those two chunks are
+  // half as deep (the middle ones, whose copies overlap compute, stay full).
+  std::vector<std::pair<int64_t, int64_t>> sched;  // (z0, slices)
+  {
+    int64_t z = 0;
+    if ((host_raw || host_vol) && nz > chunk && chunk > 1) {
+      sched.push_back({0, chunk / 2});
+      z = chunk / 2;
+    }
+    while (nz - z > chunk + ((host_raw || host_vol) ? chunk / 2 : 0) && chunk > 0) {
+      sched.push_back({z, chunk});
+      z += chunk;
+    }
+    if ((host_raw || host_vol) && nz - z > chunk) {  // tail: one full chunk, then the short last one
+      sched.push_back({z, chunk});
+      z += chunk;
+    }
+    if (nz - z > 0) sched.push_back({z, nz - z});
+  }
+  const int64_t nchunks = (int64_t)sched.size();
   auto issue_copy_in = [&](int64_t k) -> tcp_status {
     const int b = (int)(k % B);
-    const int64_t z0 = k * chunk, c = std::min(chunk, nz - z0);
+    const int64_t z0 = sched[(size_t)k].first, c = sched[(size_t)k].second;
     if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, raw_free[b], 0));
     TCP_CUDA_TRY(cudaMemcpy2DAsync(rring[b], (size_t)c * nd * 2,
                                    (const uint16_t*)raw->data + z0 * raw->stride[1], (size_t)raw->stride[0] * 2,
@@ -242,7 +262,7 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
 
   for (int64_t k = 0; k < nchunks; ++k) {
     const int b = (int)(k % B);
-    const int64_t z0 = k * chunk, c = std::min(chunk, nz - z0);
+    const int64_t z0 = sched[(size_t)k].first, c = sched[(size_t)k].second;
     View3 rv;
     rv.dtype = TCP_U16;
     rv.d0 = nt; rv.d1 = c; rv.d2 = nd;
