@@ -263,6 +263,12 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
                               "whole backprojector call, not the gather kernel alone" % (sms, clk_max)}
     vdt, sdt, _ = PATHS[path]
     split = path == "f32"
+    # the FP32 FMA ceiling of LineRec: one interpolation is 2 FP32 operations
+    # (the lerp as an FMA and the accumulation), i.e. lanes x clock / 2
+    fma_ceiling = sms * 128 * clk_max * 1e6 / 2
+    fma = {"fma_ceiling_ginterp_s": fma_ceiling / 1e9,
+           "frac_of_fma_ceiling": interps / (ms * 1e-3) / fma_ceiling,
+           "fma_ceiling_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 operations per interpolation" % (sms, clk_max)}
     traffic, tsrc = _traffic(path, nz, nt, n)
     sd = "f16x2" if split else getattr(torch, sdt or vdt)
     kernel = tcp.get_backproject_config(nz, nt, n, n, sd, getattr(torch, vdt))[3]
@@ -277,14 +283,15 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
                 "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; %d MMA flops per interp" % fl,
                 "note": "dense MMA flops executed: 30 of the 32 weights in each row of the 128 x 32 operand are zero; "
                         "the binding resource measured by ncu is the supply of sinogram windows (TMA copies from L2, "
-                        "~10 B/clock/SM), not the tensor pipe"}
+                        "~10 B/clock/SM), not the tensor pipe", **fma}
     per_clk = 16 if (sdt or vdt) == "float32" else 32
     peak = sms * per_clk * clk_max * 1e6
     return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
             "achieved": interps / (ms * 1e-3) / 1e9, "peak": peak / 1e9, "unit": "Ginterp/s",
             "frac": interps / (ms * 1e-3) / peak, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
             "interps_per_launch": interps,
-            "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max)}
+            "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max),
+            **fma}
 
 
 def measure_rows(dev) -> dict:
