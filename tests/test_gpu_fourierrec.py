@@ -156,3 +156,13 @@ def test_fourierrec_after_cache_clear():
     tcp.cache_clear()
     b = host(tcp.fourierrec(to_dev(q), theta, 16.3, n=32))
     np.testing.assert_array_equal(a, b)
+
+
+def test_fourierrec_angles_outside_half_turn():
+    # angles in [-pi, 2 pi): folded to [0, pi) with the sign of k flipped
+    rng = np.random.default_rng(12)
+    nz, nt, nd, n = 3, 40, 48, 48
+    q = rng.normal(size=(nz, nt, nd))
+    theta = rng.uniform(-np.pi, 2 * np.pi, nt)
+    got = host(tcp.fourierrec(to_dev(q), theta, 23.6, n=n))
+    assert rel(got, fr.backproject_exact(q, theta, 23.6, n)) <= 1e-5
