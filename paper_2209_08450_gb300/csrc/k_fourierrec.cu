@@ -10,25 +10,29 @@
 // x = ix - n/2, y = iy - n/2, n even.  With P[theta][k] =
 // (w_k / M) e^{2 pi i k center / M} Q_theta[k] (Q the DFT of the padded row)
 // that is sum_{theta,k} P e^{2 pi i nu.(x, y)} at the polar frequencies
-// nu = (k / M)(cos theta, sin theta), evaluated in three kernels per batch of
+// nu = (k / M)(cos theta, sin theta), evaluated in four kernels per batch of
 // slice pairs (two slices ride as the real and imaginary parts of one complex
 // row, since the map is real-linear):
 //   k_frec_rows       one CTA per (angle, pair): FFT of the padded row,
 //                     times the centre phase -> P[pair][theta][k + M/2];
-//   k_frec_spread     one CTA per strip of cw columns of the L x L Cartesian
-//                     frequency grid (L = next power of two >= 2n, so the
-//                     oversampling is >= 2): every polar sample whose window
-//                     reaches the strip is spread into shared memory with the
-//                     separable "exponential of semicircle" window of width
-//                     W (Barnett, Magland, af Klinteberg, SIAM J. Sci.
-//                     Comput. 41, 2019); then the strip's columns are
-//                     inverse-transformed and the n needed rows kept, divided
-//                     by the window's Fourier transform in y -> H[pair][iy][gx];
+//   k_frec_gather     the L x L Cartesian frequency grid (L = next power of
+//                     two >= 2n, so the oversampling is >= 2), one 4 x 4 node
+//                     block per thread: every polar sample whose window
+//                     reaches the block is added with the separable
+//                     "exponential of semicircle" window of width W (Barnett,
+//                     Magland, af Klinteberg, SIAM J. Sci. Comput. 41, 2019),
+//                     visiting only the angles whose line passes near the
+//                     block (angles folded to [0, pi) and sorted on the host);
+//                     no atomics -> G[pair][gx][gy];
+//   k_frec_cols       strips of grid columns: inverse FFTs, the n needed rows
+//                     kept, divided by the window's Fourier transform in y
+//                     -> H[pair][iy][gx];
 //   k_frec_out        one CTA per (row, pair): inverse FFT of the row, the
 //                     n needed columns divided by the window's transform in x,
 //                     times scale, real part -> slice 2p, imaginary -> 2p+1.
 // FFTs are in-place radix-4 (and one radix-2) decimation in frequency in
-// shared memory; their outputs are read at digit-reversed positions.
+// shared memory (XOR-swizzled layout); their outputs are read at
+// digit-reversed positions.
 #include <cmath>
 #include <map>
 #include <mutex>
