@@ -166,3 +166,19 @@ def test_fourierrec_angles_outside_half_turn():
     theta = rng.uniform(-np.pi, 2 * np.pi, nt)
     got = host(tcp.fourierrec(to_dev(q), theta, 23.6, n=n))
     assert rel(got, fr.backproject_exact(q, theta, 23.6, n)) <= 1e-5
+
+
+def test_fourierrec_4096_wide_sampled():
+    # n = ndet = 4096: grid L = 8192 and period M = 8192 (odd powers of two:
+    # the FFTs end with a radix-2 stage), one-column strips in the column pass
+    nz, nt, nd, n = 2, 24, 4096, 4096
+    rng = np.random.default_rng(4096)
+    theta = np.sort(rng.uniform(0, np.pi, nt))
+    q = rng.normal(size=(nz, nt, nd))
+    vol = tcp.fourierrec(to_dev(q), theta, nd / 2 - 0.3, n=n)
+    torch.cuda.synchronize()
+    for z in range(nz):
+        ix = rng.integers(0, n, 12)
+        iy = rng.integers(0, n, 12)
+        want = fr.backproject_exact_points(q[z], theta, nd / 2 - 0.3, n, ix, iy)
+        assert rel(host(vol[z])[iy, ix], want) <= 1e-5, z
