@@ -381,10 +381,12 @@ def measure_rows(dev) -> dict:
     centers = c + 0.25 * (np.arange(64) - 32)
     vol = torch.empty((64, 2048, 2048), dtype=torch.float32, device=dev)
     tms = ev_time(lambda: tcp.try_centers(raw, dark, flat, th, centers, slice=0, out=vol), 3)
+    fms = ev_time(lambda: tcp.try_centers(raw, dark, flat, th, centers, slice=0, out=vol, algorithm="fourierrec"), 3)
     out["f2_try_centers"] = {
         "workload": "one 2048^2 slice of the porous workload, 2048 angles, 64 candidate centres (step 0.25 px), "
-                    "FP32 volume from FP16 hi/lo pairs",
-        "ms": tms, "gvoxel_s": 64 * 2048 * 2048 / tms / 1e6}
+                    "FP32 volume (LineRec: from FP16 hi/lo pairs; FourierRec: FP32 rows, window 7)",
+        "ms": tms, "gvoxel_s": 64 * 2048 * 2048 / tms / 1e6,
+        "fourierrec_ms": fms, "fourierrec_gvoxel_s": 64 * 2048 * 2048 / fms / 1e6}
     del raw, dark, flat, vol
     return out
 

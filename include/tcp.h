@@ -343,6 +343,14 @@ tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, const tcp_tenso
                            const double* theta, const double* centers, int64_t ncenters, tcp_tensor* vol,
                            int32_t filter, void* stream);
 
+/* tcp_try_centers with the backprojector chosen: algorithm TCP_ALG_LINEREC
+ * (as tcp_try_centers) or TCP_ALG_FOURIERREC (the candidate stack stored as
+ * F32, or as the volume's 16-bit type, and backprojected by tcp_fourierrec
+ * with window `width`, 0 for its default; n must be even). */
+tcp_status tcp_try_centers_ex(const tcp_tensor* raw, int64_t slice, const tcp_tensor* dark, const tcp_tensor* flat,
+                              const double* theta, const double* centers, int64_t ncenters, tcp_tensor* vol,
+                              int32_t filter, int32_t algorithm, int32_t width, void* stream);
+
 /* Time every instantiated backprojector configuration on these tensors (the
  * output is overwritten) and keep the fastest for later calls with the same
  * shapes and dtypes (an explicit tcp_set_backproject_config still wins).

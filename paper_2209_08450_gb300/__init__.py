@@ -236,10 +236,12 @@ __all__.append("fbp")
 
 def try_centers(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, centers,
                 slice: int | None = None, n: int | None = None, out: torch.Tensor | None = None,
-                dtype=torch.float32, filter: str = "shepp", stream=None) -> torch.Tensor:
+                dtype=torch.float32, filter: str = "shepp", algorithm: str = "linerec", width: int = 0,
+                stream=None) -> torch.Tensor:
     """Multi-centre "try" reconstruction (Sec. 2.4): slice `slice` (default the
-    middle one) reconstructed about every candidate axis in `centers`; returns
-    [len(centers)][n][n] on the device of `raw` (CUDA)."""
+    middle one) reconstructed about every candidate axis in `centers`, by
+    LineRec or FourierRec (`algorithm`); returns [len(centers)][n][n] on the
+    CUDA device."""
     raw = _as_u16(raw)
     nt, nz, nd = raw.shape
     c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1)
@@ -254,9 +256,9 @@ def try_centers(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta
         return _lib.desc(x, _lib.U16 if x.dim() == 3 else None)
 
     r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
-    _lib.call("tcp_try_centers", _lib.ref(r), int(slice), _lib.ref(d), _lib.ref(f), th.ctypes.data_as(ctypes.c_void_p),
-              c.ctypes.data_as(ctypes.c_void_p), int(c.shape[0]), _lib.ref(o), _lib.FILTERS[filter],
-              _lib.stream_ptr(stream))
+    _lib.call("tcp_try_centers_ex", _lib.ref(r), int(slice), _lib.ref(d), _lib.ref(f),
+              th.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p), int(c.shape[0]), _lib.ref(o),
+              _lib.FILTERS[filter], _lib.ALGORITHMS[algorithm], int(width), _lib.stream_ptr(stream))
     return out
 
 

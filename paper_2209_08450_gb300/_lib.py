@@ -97,6 +97,7 @@ SIGNATURES = {
     "tcp_get_backproject_config": ([_I64, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(BpConfig)], _I32),
     "tcp_fbp": ([_T, _T, _T, _P, _D, _T, ctypes.POINTER(FbpOpts), _P], _I32),
     "tcp_try_centers": ([_T, _I64, _T, _T, _P, _P, _I64, _T, _I32, _P], _I32),
+    "tcp_try_centers_ex": ([_T, _I64, _T, _T, _P, _P, _I64, _T, _I32, _I32, _I32, _P], _I32),
 }
 
 

@@ -338,7 +338,18 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
 extern "C" tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, const tcp_tensor* dark,
                                       const tcp_tensor* flat, const double* theta, const double* centers,
                                       int64_t ncenters, tcp_tensor* vol, int32_t filter, void* stream) {
+  return tcp_try_centers_ex(raw, slice, dark, flat, theta, centers, ncenters, vol, filter, TCP_ALG_LINEREC, 0,
+                            stream);
+}
+
+extern "C" tcp_status tcp_try_centers_ex(const tcp_tensor* raw, int64_t slice, const tcp_tensor* dark,
+                                         const tcp_tensor* flat, const double* theta, const double* centers,
+                                         int64_t ncenters, tcp_tensor* vol, int32_t filter, int32_t algorithm,
+                                         int32_t width, void* stream) {
   if (!raw || !dark || !flat || !vol) return fail(TCP_ERR_ARG, "try_centers: null tensor");
+  if (algorithm != TCP_ALG_LINEREC && algorithm != TCP_ALG_FOURIERREC)
+    return fail(TCP_ERR_ARG, "try_centers: unknown algorithm");
+  const bool frec = algorithm == TCP_ALG_FOURIERREC;
   if (raw->ndim != 3 || raw->dtype != TCP_U16)
     return fail(TCP_ERR_DTYPE, "try_centers: raw must be U16 [ntheta][nz][ndet]");
   if (vol->ndim != 3 || (vol->dtype != TCP_F32 && vol->dtype != TCP_F16 && vol->dtype != TCP_BF16))
@@ -362,13 +373,19 @@ extern "C" tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, cons
   if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "try_centers: theta is null");
   for (int64_t i = 0; i < nt; ++i)
     if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "try_centers: theta must be finite");
+  const int frec_width = width == 0 ? fourierrec_default_width(vol->dtype, n) : width;
+  if (frec) {
+    tcp_status sf = fourierrec_check(nt, nd, n, frec_width);
+    if (sf != TCP_OK) return sf;
+  }
   if (ncenters == 0 || n == 0) return TCP_OK;
   if (nt == 0 || nd == 0) return fail(TCP_ERR_SHAPE, "try_centers: empty projections for a non-empty volume");
   if (where(vol->data) != kDevice) return fail(TCP_ERR_ARG, "try_centers: vol must be device memory");
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // storage of the candidate stack: as tcp_fbp chooses for this volume dtype
-  const int sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 ? TCP_F16X2 : TCP_F32);
+  // and algorithm
+  const int sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 && !frec ? TCP_F16X2 : TCP_F32);
   const double sscale = storage_scale(sdt);
   TrigTable trig;
   tcp_status s;
@@ -415,7 +432,9 @@ extern "C" tcp_status tcp_try_centers(const tcp_tensor* raw, int64_t slice, cons
   View3 vv;
   vv.p = vol->data; vv.dtype = vol->dtype; vv.d0 = ncenters; vv.d1 = n; vv.d2 = n;
   vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
+  const float bp_scale = (float)(M_PI / (double)nt / sscale);
+  if (frec) return launch_fourierrec(stack, theta, trig, 0.5 * (double)nd, vv, bp_scale, frec_width, st);
   tcp_bp_config cfg;
   tcp_get_backproject_config(ncenters, nt, nd, n, sdt, vol->dtype, &cfg);
-  return launch_backproject(stack, trig, 0.5 * (double)nd, vv, cfg, st, (float)(M_PI / (double)nt / sscale));
+  return launch_backproject(stack, trig, 0.5 * (double)nd, vv, cfg, st, bp_scale);
 }

@@ -181,3 +181,17 @@ def test_fbp_algorithm_checks(lib):
     odd = _t(_lib.F32, (2, 15, 15), ptr=1 << 23)
     assert _status(lib, "tcp_fbp", ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(flat), th, 8.0,
                    ctypes.byref(odd), ctypes.byref(o), None) == 2
+
+
+def test_try_centers_ex_algorithm_checks(lib):
+    raw = _t(_lib.U16, (10, 4, 32), ptr=1 << 20)
+    dark = _t(_lib.F32, (4, 32), ptr=1 << 21)
+    flat = _t(_lib.F32, (4, 32), ptr=1 << 22)
+    th = (ctypes.c_double * 10)(*[0.1 * i for i in range(10)])
+    cs = (ctypes.c_double * 2)(16.0, 17.0)
+    vol = _t(_lib.F32, (2, 32, 32), ptr=1 << 23)
+    assert _status(lib, "tcp_try_centers_ex", ctypes.byref(raw), 1, ctypes.byref(dark), ctypes.byref(flat), th, cs,
+                   2, ctypes.byref(vol), 0, 9, 0, None) == 1  # unknown algorithm
+    odd = _t(_lib.F32, (2, 31, 31), ptr=1 << 23)
+    assert _status(lib, "tcp_try_centers_ex", ctypes.byref(raw), 1, ctypes.byref(dark), ctypes.byref(flat), th, cs,
+                   2, ctypes.byref(odd), 0, 1, 0, None) == 2  # FourierRec needs an even n

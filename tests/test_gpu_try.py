@@ -57,3 +57,20 @@ def test_try_centers_rejects_bad_arguments():
         tcp.try_centers(raw, dark, flat, ds.theta, [16.0, float("nan")], slice=0)
     empty = tcp.try_centers(raw, dark, flat, ds.theta, np.zeros(0), slice=0)
     assert empty.shape == (0, 32, 32)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-5), (torch.float16, 5e-3)])
+def test_try_centers_fourierrec(dtype, tol):
+    from oracle import fourierrec as frc
+    c0 = 24 - 0.4
+    ds = synth.shepp_logan_dataset(ntheta=60, ndet=48, nz=3, center=c0, seed=13)
+    centers = c0 + np.array([-2.0, 0.0, 1.3, 3.7])
+    out = tcp.try_centers(u16(ds.raw), u16(ds.dark), u16(ds.flat), ds.theta, centers, slice=1, dtype=dtype,
+                          algorithm="fourierrec")
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    p = oracle.normalize(ds.raw[:, 1:2], oracle.frame_mean(ds.dark[:, 1:2]), oracle.frame_mean(ds.flat[:, 1:2]))
+    for k, c in enumerate(centers):
+        q = oracle.filter_sino(p, float(c), "shepp", "edge")
+        ref = frc.backproject_exact(q, ds.theta, 24.0, 48)[0]
+        assert rel(got[k], ref) <= tol
