@@ -16,6 +16,11 @@ What it computes (Nikitin, TomocuPy, arXiv 2209.08450):
   backprojection line integral with linear interpolation (C, FP64).
 * ``project`` -- the exact transpose of ``backproject`` (not in the paper).
 * ``fbp`` -- the three steps in the paper's order.
+* ``oracle.fourierrec`` -- FourierRec (Sec. 1, 2.2, 3): backprojection with
+  the band-limited interpolant of each zero-padded row, exact FP64 sums and
+  the gridding steps (``tests/test_oracle_fourierrec.py``).
+* ``oracle.lprec`` -- LpRec (Sec. 1, 3): the cubic-spline backprojection by
+  direct sums and its log-polar evaluation (``tests/test_oracle_lprec.py``).
 
 Every function is pinned by ``tests/test_oracle.py`` against closed forms,
 brute force and invariants; none is pinned against itself.

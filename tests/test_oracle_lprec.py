@@ -1,0 +1,56 @@
+"""Pins of the LpRec oracle (CPU only).
+
+The cubic B-spline interpolant is pinned by textbook properties (it
+interpolates, reproduces cubics away from the zero boundary, its weights
+form a partition of unity); the exact cubic-spline backprojection by its
+agreement with the LineRec oracle where every ray hits a detector node; the
+log-polar evaluation by convergence to the exact sums as its grid is refined.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import lprec as lp
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_bspline_interpolates_and_reproduces_cubics():
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(40)
+    np.testing.assert_allclose(lp.row_interp(v, np.arange(40.0)), v, rtol=0, atol=1e-12)
+    # a cubic sampled on a long row is reproduced exactly far from the ends
+    j = np.arange(200.0)
+    cub = lambda s: 0.3 - 0.02 * s + 1e-3 * s ** 2 - 4e-6 * s ** 3
+    s = np.linspace(90.0, 110.0, 57)
+    np.testing.assert_allclose(lp.row_interp(cub(j), s), cub(s), rtol=0, atol=1e-9)
+    # partition of unity of the four weights
+    _, w = lp._beta3_taps(np.linspace(-3.0, 5.0, 33))
+    np.testing.assert_allclose(sum(w), 1.0, rtol=0, atol=1e-15)
+
+
+def test_spline_backprojection_at_nodes_equals_linerec():
+    rng = np.random.default_rng(1)
+    q = rng.standard_normal((2, 2, 12))
+    th = np.array([0.0, np.pi / 2])
+    got = lp.backproject_spline_exact(q, th, 6.0, 10)
+    np.testing.assert_allclose(got, oracle.backproject(q, th, 6.0, 10), rtol=0, atol=1e-12)
+
+
+def test_lprec_converges_to_spline_backprojection():
+    rng = np.random.default_rng(2)
+    nt, nd, n = 48, 32, 32
+    theta = np.arange(nt) * np.pi / nt + 0.01
+    q = rng.standard_normal((1, nt, nd))
+    exact = lp.backproject_spline_exact(q, theta, 16.3, n)
+    errs = [rel(lp.backproject_lprec(q, theta, 16.3, n, os=o), exact) for o in (2, 4, 8)]
+    assert errs[0] > 4 * errs[1] > 16 * errs[2], errs
+    assert errs[2] < 1e-4, errs
+
+
+def test_lprec_needs_equally_spaced_angles():
+    th = np.sort(np.random.default_rng(3).uniform(0, np.pi, 12))
+    with pytest.raises(ValueError):
+        lp.backproject_lprec(np.zeros((1, 12, 16)), th, 8.0, 16)
