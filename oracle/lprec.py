@@ -130,9 +130,37 @@ def _check_equally_spaced(theta: np.ndarray) -> float:
     return float(d[0])
 
 
+def _span_by_fft(gcs: np.ndarray, p: int, r0: float, drho: float, dpsi: float, base: float, nrho: int,
+                 npsi: int) -> np.ndarray:
+    """Step (2) as one 2-D linear convolution, computed by FFT.
+
+    gcs[u][l]: B-spline coefficients of G for the span's u-th angle.  With the
+    angles placed every p columns, A[l][p u] = gcs[u][l], the sum
+    f[i][k] = sum_u sum_l gcs[u][l] beta3(i + base + s(k - p u) - l),
+    s(r) = log cos((r - r0) dpsi) / drho, is (A * K)[i][k] with
+    K[d][r] = beta3(d + base + s(r))."""
+    nu, nl = gcs.shape
+    kp = p * (nu - 1) + 1
+    A = np.zeros((nl, kp))
+    A[:, ::p] = gcs.T
+    r = np.arange(-(kp - 1), npsi)                      # every k - p u needed
+    sr = np.log(np.cos((r - r0) * dpsi)) / drho
+    # d = i - l spans [-(nl - 1), nrho - 1]; beta3 vanishes outside |.| < 2
+    d = np.arange(-(nl - 1), nrho)
+    arg = d[:, None] + base + sr[None, :]
+    K = np.where(np.abs(arg) < 2.0,
+                 np.where(np.abs(arg) < 1.0, 2.0 / 3.0 - arg ** 2 + np.abs(arg) ** 3 / 2.0,
+                          (2.0 - np.abs(arg)) ** 3 / 6.0), 0.0)
+    shape = (nl + K.shape[0] - 1, kp + K.shape[1] - 1)
+    full = np.fft.irfft2(np.fft.rfft2(A, shape) * np.fft.rfft2(K, shape), shape)
+    # output index (i, k) sits at (i + nl - 1, k + kp - 1) of the full product
+    return full[nl - 1:nl - 1 + nrho, kp - 1:kp - 1 + npsi]
+
+
 def backproject_lprec(sino: np.ndarray, theta: np.ndarray, center: float, n: int, os: float = 2.0,
-                      a_factor: float = 4.0, margin: int = 12) -> np.ndarray:
-    """LpRec by the steps (1)-(4) above, in FP64."""
+                      a_factor: float = 4.0, margin: int = 12, conv: str = "direct") -> np.ndarray:
+    """LpRec by the steps (1)-(4) above, in FP64.  conv="fft" evaluates step
+    (2) as the span's 2-D convolution by FFT (the same sum)."""
     sino = np.asarray(sino, dtype=np.float64)
     if sino.ndim == 2:
         sino = sino[None]
@@ -175,14 +203,20 @@ def backproject_lprec(sino: np.ndarray, theta: np.ndarray, center: float, n: int
         tk = (vpsi - psi[0]) / dpsi
         for z in range(nz):
             coef = bspline_coeffs(sino[z], axis=1)
-            f = np.zeros((nrho, psi.shape[0]))
+            gcs = []
             for j in js:
                 sh = center - a * np.cos(theta[j] - phi)
                 g = bspline_eval(coef[j], sh + np.exp(tau) + PAD)          # (1) G_theta on the tau grid
-                gc = bspline_coeffs(g)
-                shift = np.log(np.cos(psi - theta[j]))                       # (2) f_span on the grid
-                tt = (rho[:, None] + shift[None, :] - tau0) / drho
-                f += bspline_eval(gc, tt + PAD)
+                gcs.append(bspline_coeffs(g))
+            if conv == "fft":                                                # (2) f_span on the grid
+                r0 = kpsi - p * (js.size - 1) / 2.0
+                f = _span_by_fft(np.array(gcs), p, r0, drho, dpsi, ext + PAD, nrho, psi.shape[0])
+            else:
+                f = np.zeros((nrho, psi.shape[0]))
+                for u, j in enumerate(js):
+                    shift = np.log(np.cos(psi - theta[j]))
+                    tt = (rho[:, None] + shift[None, :] - tau0) / drho
+                    f += bspline_eval(gcs[u], tt + PAD)
             fc = bspline_coeffs(bspline_coeffs(f, axis=0), axis=1)         # (3) back to the voxels
             out[z] += bspline_eval2(fc, ti + PAD, tk + PAD)
     return out

@@ -54,3 +54,16 @@ def test_lprec_needs_equally_spaced_angles():
     th = np.sort(np.random.default_rng(3).uniform(0, np.pi, 12))
     with pytest.raises(ValueError):
         lp.backproject_lprec(np.zeros((1, 12, 16)), th, 8.0, 16)
+
+
+def test_lprec_span_convolution_by_fft_equals_direct_sum():
+    # step (2) is a 2-D linear convolution on the log-polar grid (the kernel
+    # uses the centred closed form of the cubic B-spline, independent of the
+    # tap weights of the direct route)
+    rng = np.random.default_rng(4)
+    nt, nd, n = 36, 24, 24
+    theta = np.arange(nt) * np.pi / nt
+    q = rng.standard_normal((2, nt, nd))
+    a = lp.backproject_lprec(q, theta, 11.7, n, os=2)
+    b = lp.backproject_lprec(q, theta, 11.7, n, os=2, conv="fft")
+    assert rel(b, a) < 1e-12
