@@ -264,7 +264,10 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * overwritten.  Works in about 1.5 GiB of stream-ordered workspace
  * (cudaMallocAsync on `stream`).  Errors: TCP_ERR_SHAPE for odd n or sizes
  * over the limits, TCP_ERR_ARG for a width outside 2..16 or above L,
- * TCP_ERR_DTYPE for F16X2 or U16 sinograms. */
+ * TCP_ERR_DTYPE for F16X2 or U16 sinograms.
+ * The first call for a new size, width or angle set builds cached tables
+ * (twiddles, deconvolution factors, sorted angles) with synchronous uploads,
+ * so that call must not be inside CUDA graph capture. */
 tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double center,
                           tcp_tensor* vol, double scale, int32_t width, void* stream);
 
