@@ -255,15 +255,16 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * and, for every voxel,
  *   vol[z][iy][ix] = scale * sum over theta of q~_{z,theta}(s(x, y, theta))
  * with the ray coordinate of tcp_backproject.  The sum is evaluated on an
- * L x L Cartesian frequency grid (L = the next power of two >= 2n) with the
+ * L x L Cartesian frequency grid (L = the next power of two >= 2n, at least
+ * 16) with the
  * "exponential of semicircle" window of `width` grid points (2..16; 0 picks
- * 7 for an F32 volume, 5 for F16/BF16, at most L): relative error about 1e-6 at 7 and
+ * 7 for an F32 volume, 5 for F16/BF16): relative error about 1e-6 at 7 and
  * tenfold smaller per extra point.  Two slices share one complex transform.
  * sino:  F32/F16/BF16 [nz][ntheta][ndet], ndet <= 8192, ntheta <= 2^24;
  * theta: HOST FP64 [ntheta]; vol: F32/F16/BF16 [nz][n][n], n even, n <= 8192,
  * overwritten.  Works in about 1.5 GiB of stream-ordered workspace
  * (cudaMallocAsync on `stream`).  Errors: TCP_ERR_SHAPE for odd n or sizes
- * over the limits, TCP_ERR_ARG for a width outside 2..16 or above L,
+ * over the limits, TCP_ERR_ARG for a width outside 2..16,
  * TCP_ERR_DTYPE for F16X2 or U16 sinograms.
  * The first call for a new size, width or angle set builds cached tables
  * (twiddles, deconvolution factors, sorted angles) with synchronous uploads,

@@ -34,7 +34,7 @@ nu = (k / M)(cos theta, sin theta): a transform from unequally spaced
 frequencies to the pixel grid.  It is evaluated by
   1. P from an FFT of each zero-padded row;
   2. spreading every P onto an L x L Cartesian frequency grid (L = the next
-     power of two >= 2n: oversampling >= 2) with a separable window phi of
+     power of two >= 2n, at least 16: oversampling >= 2) with a separable window phi of
      width W grid points;
   3. a 2-D inverse DFT of the grid;
   4. dividing pixel (x, y) by Phi(x / L) Phi(y / L), Phi the Fourier
@@ -60,8 +60,9 @@ def period(ndet: int) -> int:
 
 
 def grid_size(n: int) -> int:
-    """Cartesian frequency grid L: the next power of two >= 2 n."""
-    g = 1
+    """Cartesian frequency grid L: the next power of two >= 2 n, at least 16
+    (oversampling >= 2, and the window's W <= 16 points always fit)."""
+    g = 16
     while g < 2 * n:
         g *= 2
     return g

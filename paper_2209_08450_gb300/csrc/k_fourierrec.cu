@@ -16,7 +16,7 @@
 //   k_frec_rows       one CTA per (angle, pair): FFT of the padded row,
 //                     times the centre phase -> P[pair][theta][k + M/2];
 //   k_frec_gather     the L x L Cartesian frequency grid (L = next power of
-//                     two >= 2n, so the oversampling is >= 2), one 4 x 4 node
+//                     two >= 2n, at least 16: oversampling >= 2), one 4 x 4 node
 //                     block per thread: every polar sample whose window
 //                     reaches the block is added with the separable
 //                     "exponential of semicircle" window of width W (Barnett,
@@ -685,17 +685,23 @@ void fourierrec_cache_clear() {
   g_frec.ang.clear();
 }
 
-int fourierrec_default_width(int vol_dtype, int64_t n) {
-  int64_t L = 1;
+// Cartesian grid side: the next power of two >= 2n, at least 16 (oversampling
+// >= 2, and every window width 2..16 fits).
+int64_t fourierrec_grid(int64_t n) {
+  int64_t L = 16;
   while (L < 2 * n) L *= 2;
-  return (int)std::max<int64_t>(2, std::min<int64_t>(L, vol_dtype == TCP_F32 ? 7 : 5));
+  return L;
+}
+
+int fourierrec_default_width(int vol_dtype, int64_t n) {
+  return (int)std::min<int64_t>(fourierrec_grid(n), vol_dtype == TCP_F32 ? 7 : 5);
 }
 
 tcp_status fourierrec_check(int64_t nt, int64_t nd, int64_t n, int width) {
   if (n % 2) return fail(TCP_ERR_SHAPE, "fourierrec: n must be even");
-  int64_t M = 1, L = 1;
+  int64_t M = 1;
   while (M < 2 * nd) M *= 2;
-  while (L < 2 * n) L *= 2;
+  const int64_t L = fourierrec_grid(n);
   if (M > (int64_t(1) << kMaxLg)) return fail(TCP_ERR_SHAPE, "fourierrec: ndet must be <= 8192");
   if (L > (int64_t(1) << kMaxLg)) return fail(TCP_ERR_SHAPE, "fourierrec: n must be <= 8192");
   if (nt > kMaxTheta) return fail(TCP_ERR_SHAPE, "fourierrec: ntheta must be <= 2^24");
@@ -709,7 +715,7 @@ tcp_status launch_fourierrec(const View3& sv, const double* theta, const TrigTab
   const int nz = (int)sv.d0, nt = (int)sv.d1, nd = (int)sv.d2, n = (int)vv.d1;
   tcp_status s;
   if ((s = fourierrec_check(nt, nd, n, width)) != TCP_OK) return s;
-  const int lgM = std::max(1, ilog2(2 * (int64_t)nd)), lgL = std::max(1, ilog2(2 * (int64_t)n));
+  const int lgM = std::max(1, ilog2(2 * (int64_t)nd)), lgL = ilog2(fourierrec_grid(n));
   const int M = 1 << lgM, L = 1 << lgL;
   const int ms = M + 1;
   int dev = 0;

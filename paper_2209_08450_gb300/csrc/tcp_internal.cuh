@@ -158,6 +158,7 @@ tcp_status launch_project(const View3& vol, const TrigTable& trig, double center
                           cudaStream_t st);
 // FourierRec (k_fourierrec.cu): default window width per volume dtype, the
 // shape/width checks, and the launcher (sino F32/F16/BF16, vol F32/F16/BF16).
+int64_t fourierrec_grid(int64_t n);  // Cartesian grid side L
 int fourierrec_default_width(int vol_dtype, int64_t n);  // clamped to the grid size
 void fourierrec_cache_clear();  // frees the cached twiddle, deconvolution and angle tables
 tcp_status fourierrec_check(int64_t ntheta, int64_t ndet, int64_t n, int width);

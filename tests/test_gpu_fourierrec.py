@@ -182,3 +182,13 @@ def test_fourierrec_4096_wide_sampled():
         iy = rng.integers(0, n, 12)
         want = fr.backproject_exact_points(q[z], theta, nd / 2 - 0.3, n, ix, iy)
         assert rel(host(vol[z])[iy, ix], want) <= 1e-5, z
+
+
+@pytest.mark.parametrize("nd,n", [(2, 2), (3, 4), (5, 6), (1, 2)])
+def test_fourierrec_tiny(nd, n):
+    # grids of 4 and 8 points (window clamped to the grid), single-stage FFTs
+    rng = np.random.default_rng(nd * 10 + n)
+    q = rng.normal(size=(3, 7, nd))
+    theta = np.sort(rng.uniform(0, np.pi, 7))
+    got = host(tcp.fourierrec(to_dev(q), theta, nd / 2 + 0.2, n=n))
+    assert rel(got, fr.backproject_exact(q, theta, nd / 2 + 0.2, n)) <= 1e-5

@@ -28,6 +28,7 @@ def rel(a, b):
 def test_period_and_grid():
     assert fr.period(12) == 32 and fr.period(16) == 32 and fr.period(17) == 64 and fr.period(1) == 2
     assert fr.grid_size(10) == 32 and fr.grid_size(64) == 128 and fr.grid_size(2048) == 4096
+    assert fr.grid_size(1) == 16 and fr.grid_size(8) == 16 and fr.grid_size(9) == 32
 
 
 @pytest.mark.parametrize("theta0,center,j0", [(0.3, 5.37, 4), (1.9, 6.0, 0), (2.71, 4.25, 11)])
