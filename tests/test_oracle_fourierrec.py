@@ -121,3 +121,33 @@ def test_gridding_grid_larger_than_twice_n():
 def test_odd_n_rejected():
     with pytest.raises(ValueError):
         fr.backproject_exact(np.zeros((1, 2, 4)), np.zeros(2), 2.0, 5)
+
+
+def _bump_fbp_errors(backproject):
+    import synth
+    errs, lin = [], []
+    for n in (32, 64, 128):
+        R = 0.3 * n
+        x0, y0 = 0.07 * n, -0.05 * n
+        nt = 2 * n
+        theta = synth.uniform_theta(nt)
+        c = n / 2.0 + 0.3
+        p = synth.smooth_bump_sinogram(theta, n, c, R, x0, y0)
+        q = oracle.filter_sino(p[None], c, "ramp", "edge")
+        f = synth.smooth_bump(n, R, x0, y0)
+        xc = np.arange(n) - n / 2
+        X, Y = np.meshgrid(xc, xc)
+        m = X ** 2 + Y ** 2 < (n / 2 - 2.0) ** 2
+        e = lambda r: np.linalg.norm((r - f)[m]) / np.linalg.norm(f[m])
+        errs.append(e(backproject(q, theta, n / 2.0, n)[0]))
+        lin.append(e(oracle.backproject(q, theta, n / 2.0, n)[0]))
+    return errs, lin
+
+
+def test_fourierrec_fbp_of_smooth_bump_converges_to_the_function():
+    # FourierRec approximates the same FBP integral as LineRec: the FBP of the
+    # analytic Radon transform of f = (1 - r^2/R^2)^2 converges to f, and the
+    # band-limited interpolant does better than the linear one at every size
+    errs, lin = _bump_fbp_errors(lambda q, th, c, n: fr.backproject_gridding(q, th, c, n, width=10))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 3e-4, errs
+    assert all(a < b for a, b in zip(errs, lin)), (errs, lin)

@@ -67,3 +67,30 @@ def test_lprec_span_convolution_by_fft_equals_direct_sum():
     a = lp.backproject_lprec(q, theta, 11.7, n, os=2)
     b = lp.backproject_lprec(q, theta, 11.7, n, os=2, conv="fft")
     assert rel(b, a) < 1e-12
+
+
+def test_lprec_fbp_of_smooth_bump_converges_to_the_function():
+    # LpRec approximates the same FBP integral: with the analytic Radon
+    # transform of the smooth bump its FBP converges to the bump (about
+    # fourth order here), and its log-polar evaluation stays within 1 % of the
+    # cubic-spline FBP's own error
+    import synth
+    errs = []
+    for n in (32, 64, 128):
+        R = 0.3 * n
+        x0, y0 = 0.07 * n, -0.05 * n
+        nt = 2 * n
+        theta = synth.uniform_theta(nt)
+        c = n / 2.0 + 0.3
+        p = synth.smooth_bump_sinogram(theta, n, c, R, x0, y0)
+        q = oracle.filter_sino(p[None], c, "ramp", "edge")
+        f = synth.smooth_bump(n, R, x0, y0)
+        xc = np.arange(n) - n / 2
+        X, Y = np.meshgrid(xc, xc)
+        m = X ** 2 + Y ** 2 < (n / 2 - 2.0) ** 2
+        e = lambda r: np.linalg.norm((r - f)[m]) / np.linalg.norm(f[m])
+        a = e(lp.backproject_lprec(q, theta, n / 2.0, n, os=2)[0])
+        b = e(lp.backproject_spline_exact(q, theta, n / 2.0, n)[0])
+        assert abs(a - b) < 0.01 * b, (n, a, b)
+        errs.append(a)
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5 and errs[2] < 1e-4, errs
