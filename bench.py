@@ -231,14 +231,17 @@ def _traffic(path, nz, nt, n):
 def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     """Roofline of the backprojector launch of this path and chunk.
 
-    CUDA-core kernels are bound by the shared-memory pipe: per 32
-    interpolations a warp needs 2 wavefronts (FP32 samples) or 1 (16-bit
-    sample pairs), i.e. 16 or 32 interpolations per clock per SM.  The
-    tensor-core kernel is bound by the tensor pipe: each interpolation is one
-    row x column entry of a dense 128 x 32 x N product, 32 multiply-adds =
-    64 flops (30 of the 32 weights in a row are zero), three such products in
-    split mode (hi*hi + hi*lo + lo*hi), against the measured dense bf16 peak
-    (FP16 runs at the same rate)."""
+    LineRec's work is the interpolation count nz * n^2 * ntheta, each 2 FP32
+    operations (the lerp as an FMA and the accumulation), so its ceiling is
+    the FP32 FMA rate: SMs x 128 lanes x clock / 2 interpolations per second.
+    `frac` is always interpolations/s against that ceiling, whichever kernel
+    runs.  Alongside: the shared-memory roof of the CUDA-core kernel (per 32
+    interpolations a warp needs 2 wavefronts for FP32 samples or 1 for 16-bit
+    sample pairs: 16 or 32 interpolations per clock per SM), and for the
+    tensor-core kernel the dense MMA utilisation it reaches (each
+    interpolation is one entry of a dense 128 x 32 x N product, 64 flops, 30
+    of the 32 weights in a row zero; three products in split mode) against the
+    measured bf16 peak, a diagnostic of the tensor pipe, not of the method."""
     import torch
     pk = _peaks()
     clk_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -263,35 +266,38 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
                               "whole backprojector call, not the gather kernel alone" % (sms, clk_max)}
     vdt, sdt, _ = PATHS[path]
     split = path == "f32"
-    # the FP32 FMA ceiling of LineRec: one interpolation is 2 FP32 operations
-    # (the lerp as an FMA and the accumulation), i.e. lanes x clock / 2
     fma_ceiling = sms * 128 * clk_max * 1e6 / 2
-    fma = {"fma_ceiling_ginterp_s": fma_ceiling / 1e9,
-           "frac_of_fma_ceiling": interps / (ms * 1e-3) / fma_ceiling,
-           "fma_ceiling_basis": "%d SMs x 128 FP32 lanes x %.0f MHz / 2 operations per interpolation" % (sms, clk_max)}
+    ach = interps / (ms * 1e-3)
     traffic, tsrc = _traffic(path, nz, nt, n)
     sd = "f16x2" if split else getattr(torch, sdt or vdt)
     kernel = tcp.get_backproject_config(nz, nt, n, n, sd, getattr(torch, vdt))[3]
+    per_clk = 16 if (sdt or vdt) == "float32" else 32
+    smem_roof = sms * per_clk * clk_max * 1e6
+    out = {"bound": "alu", "achieved": ach / 1e9, "peak": fma_ceiling / 1e9, "unit": "Ginterp/s",
+           "frac": ach / fma_ceiling, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
+           "interps_per_launch": interps, "algorithmic_bytes_per_launch": None,
+           "peak_basis": "FP32 FMA ceiling of LineRec: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock) / 2 "
+                         "operations per interpolation (derived from the lane count and clock; no measured FP32 "
+                         "peak exists)" % (sms, clk_max)}
+    # algorithmic HBM bytes: the sinogram chunk read once, the volume written once
+    sbytes = (4 if split else (4 if (sdt or vdt) == "float32" else 2)) * nz * nt * n
+    vbytes = {"float32": 4, "float16": 2, "bfloat16": 2}[vdt] * nz * n * n
+    out["algorithmic_bytes_per_launch"] = sbytes + vbytes
     if kernel == 1:
         fl = 192 if split else 64
-        peak = float(pk.get("bf16_tflops", 1900.0))
-        ach = interps * fl / (ms * 1e-3) / 1e12
-        return {"bound": "tensor", "kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" %
-                ("FP16 hi/lo pairs, 3 products" if split else path),
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
-                "traffic_source": tsrc, "ms_per_launch": ms, "interps_per_launch": interps, "ginterp_s": interps / (ms * 1e-3) / 1e9,
-                "peak_basis": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured; %d MMA flops per interp" % fl,
-                "note": "dense MMA flops executed: 30 of the 32 weights in each row of the 128 x 32 operand are zero; "
-                        "the binding resource measured by ncu is the supply of sinogram windows (TMA copies from L2, "
-                        "~10 B/clock/SM), not the tensor pipe", **fma}
-    per_clk = 16 if (sdt or vdt) == "float32" else 32
-    peak = sms * per_clk * clk_max * 1e6
-    return {"bound": "alu", "kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
-            "achieved": interps / (ms * 1e-3) / 1e9, "peak": peak / 1e9, "unit": "Ginterp/s",
-            "frac": interps / (ms * 1e-3) / peak, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
-            "interps_per_launch": interps,
-            "peak_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz (max SM clock)" % (sms, per_clk, clk_max),
-            **fma}
+        bpk = float(pk.get("bf16_tflops", 1900.0))
+        mma = interps * fl / (ms * 1e-3) / 1e12
+        out.update({"kernel": "k_backproject_tc (LineRec on tcgen05.mma, %s)" %
+                              ("FP16 hi/lo pairs, 3 products" if split else path),
+                    "mma_tflops_executed": mma, "mma_frac_of_bf16_peak": mma / bpk,
+                    "mma_basis": "%d dense MMA flops per interpolation against the measured dense bf16 burst "
+                                 "(MEASURED_PEAKS.json, of measured); 30 of the 32 weights in each operand row are "
+                                 "zero" % fl})
+    else:
+        out.update({"kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
+                    "smem_roof_ginterp_s": smem_roof / 1e9, "frac_of_smem_roof": ach / smem_roof,
+                    "smem_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz" % (sms, per_clk, clk_max)})
+    return out
 
 
 def measure_rows(dev) -> dict:
@@ -408,7 +414,7 @@ def main():
     ap.add_argument("--variants", default="f32,f16,bf16,f32_cuda,f32_frec,f16_frec")
     ap.add_argument("--variant-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-slices", type=int, default=4)
+    ap.add_argument("--cpu-slices", type=int, default=16)
     ap.add_argument("--ref-slices", type=int, default=1)
     ap.add_argument("--parity-slices", type=int, default=2)
     ap.add_argument("--no-rows", action="store_true", help="skip the least-squares and batch rows")

@@ -267,7 +267,7 @@ static int dtype_size(int dt) {
   return 0;
 }
 
-static tcp_status check_tensor(const tcp_tensor* t, const char* name, int ndim_lo, int ndim_hi) {
+tcp_status check_tensor(const tcp_tensor* t, const char* name, int ndim_lo, int ndim_hi) {
   if (!t) return fail(TCP_ERR_ARG, std::string(name) + ": null tensor");
   if (t->ndim < ndim_lo || t->ndim > ndim_hi)
     return fail(TCP_ERR_SHAPE, std::string(name) + ": wrong number of dimensions");
@@ -328,7 +328,7 @@ static void extent(const tcp_tensor* t, uintptr_t* lo, uintptr_t* hi) {
   *lo = (uintptr_t)t->data;
   *hi = (uintptr_t)t->data + (uintptr_t)(last + 1) * dtype_size(t->dtype);
 }
-static bool overlap(const tcp_tensor* a, const tcp_tensor* b) {
+bool overlap(const tcp_tensor* a, const tcp_tensor* b) {
   if (numel(a) == 0 || numel(b) == 0) return false;
   uintptr_t al, ah, bl, bh;
   extent(a, &al, &ah);

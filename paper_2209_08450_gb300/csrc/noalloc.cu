@@ -83,6 +83,14 @@ using namespace tcp;
 
 extern "C" tcp_status tcp_normalize_noalloc(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
                                             tcp_tensor* sino, void* stream) {
+  // the descriptor checks of tcp_normalize (unit innermost stride, data
+  // aligned to its dtype, ...) come first, so that no misaligned pointer
+  // reaches a kernel
+  tcp_status s;
+  if ((s = check_tensor(raw, "raw", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(dark, "dark", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(flat, "flat", 3, 3)) != TCP_OK) return s;
+  if ((s = check_tensor(sino, "sino", 3, 3)) != TCP_OK) return s;
   if (!valid3(raw) || !valid3(dark) || !valid3(flat) || !valid3(sino))
     return fail(TCP_ERR_SHAPE, "normalize_noalloc: raw, dark, flat and sino must be 3-d with unit innermost stride");
   if (raw->dtype != TCP_U16 || dark->dtype != TCP_U16 || flat->dtype != TCP_U16)
@@ -99,11 +107,12 @@ extern "C" tcp_status tcp_normalize_noalloc(const tcp_tensor* raw, const tcp_ten
     return fail(TCP_ERR_SHAPE, "normalize_noalloc: nz * ndet = " + std::to_string(nz * nd) +
                                    " exceeds the fixed scratch of " + std::to_string(kMaxMean) +
                                    " elements per mean; use tcp_normalize");
+  if (overlap(raw, sino)) return fail(TCP_ERR_ALIAS, "normalize_noalloc: raw and sino overlap");
+  if (overlap(dark, sino) || overlap(flat, sino))
+    return fail(TCP_ERR_ALIAS, "normalize_noalloc: dark/flat and sino overlap");
   if (nt * nz * nd == 0) return TCP_OK;
-  for (const tcp_tensor* t : {raw, dark, flat, static_cast<const tcp_tensor*>(sino)})
-    if (!t->data) return fail(TCP_ERR_ARG, "normalize_noalloc: null data");
   float* scratch = nullptr;
-  tcp_status s = means_scratch(&scratch);
+  s = means_scratch(&scratch);
   if (s != TCP_OK) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   View3 dm, fm;

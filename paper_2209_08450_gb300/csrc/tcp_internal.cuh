@@ -40,6 +40,12 @@ tcp_status cuda_fail(cudaError_t e, const char* what);
 
 bool checked_mode();
 
+// Host-side checks shared by the entry points: a tensor descriptor (non-null,
+// ndim in [lo, hi], known dtype, non-negative extents, unit innermost stride,
+// data aligned to its dtype), and whether two tensors' byte ranges overlap.
+tcp_status check_tensor(const tcp_tensor* t, const char* name, int ndim_lo, int ndim_hi);
+bool overlap(const tcp_tensor* a, const tcp_tensor* b);
+
 // ----------------------------------------------------------------- dtypes --
 
 template <class T> struct Store;

@@ -193,3 +193,30 @@ def test_try_centers_ex_algorithm_checks(lib):
     odd = _t(_lib.F32, (2, 31, 31), ptr=1 << 23)
     assert _status(lib, "tcp_try_centers_ex", ctypes.byref(raw), 1, ctypes.byref(dark), ctypes.byref(flat), th, cs,
                    2, ctypes.byref(odd), 0, 1, 0, None) == 2  # FourierRec needs an even n
+
+
+@pytest.mark.parametrize("name", ["tcp_normalize", "tcp_normalize_noalloc"])
+def test_normalize_rejects_misaligned_and_aliased_buffers(lib, name):
+    # both normalisation calls check every descriptor on the host before any
+    # launch: a U16 pointer at an odd address or an F32 pointer off its 4-byte
+    # alignment is TCP_ERR_ALIGN, a sinogram overlapping raw is TCP_ERR_ALIAS
+    fn = getattr(lib, name)
+    fn.argtypes = [ctypes.POINTER(_lib.TcpTensor)] * 4 + [ctypes.c_void_p]
+    fn.restype = ctypes.c_int32
+    raw = _t(_lib.U16, (4, 2, 16), ptr=1 << 20)
+    dark = _t(_lib.U16, (3, 2, 16), ptr=1 << 21)
+    flat = _t(_lib.U16, (3, 2, 16), ptr=1 << 22)
+    out = _t(_lib.F32, (2, 4, 16), ptr=1 << 23)
+    args = lambda r, d, f, o: (ctypes.byref(r), ctypes.byref(d), ctypes.byref(f), ctypes.byref(o), None)
+    odd_raw = _t(_lib.U16, (4, 2, 16), ptr=(1 << 20) + 1)
+    assert fn(*args(odd_raw, dark, flat, out)) == 4
+    odd_dark = _t(_lib.U16, (3, 2, 16), ptr=(1 << 21) + 1)
+    assert fn(*args(raw, odd_dark, flat, out)) == 4
+    off_out = _t(_lib.F32, (2, 4, 16), ptr=(1 << 23) + 2)
+    assert fn(*args(raw, dark, flat, off_out)) == 4
+    strided = _t(_lib.U16, (4, 2, 16), ptr=1 << 20)
+    strided.stride[2] = 2
+    assert fn(*args(strided, dark, flat, out)) == 4
+    alias = _t(_lib.F32, (2, 4, 16), ptr=(1 << 20) + 64)  # inside raw's 256 bytes
+    assert fn(*args(raw, dark, flat, alias)) == 10
+    assert b"overlap" in lib.tcp_last_error()

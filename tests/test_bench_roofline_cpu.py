@@ -22,7 +22,7 @@ class _Tcp:
 
 
 @pytest.mark.parametrize("path,kernel,bound", [
-    ("f32", 1, "tensor"), ("f16", 1, "tensor"), ("bf16", 1, "tensor"), ("f32_cuda", 0, "alu"),
+    ("f32", 1, "alu"), ("f16", 1, "alu"), ("bf16", 1, "alu"), ("f32_cuda", 0, "alu"),
     ("f32_frec", 0, "alu"), ("f16_frec", 0, "alu")])
 def test_roofline_object(monkeypatch, path, kernel, bound):
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: _Props())
@@ -34,7 +34,16 @@ def test_roofline_object(monkeypatch, path, kernel, bound):
     if path in bench.FOURIERREC:
         assert r["window_width"] == bench.FOURIERREC[path]
     else:
-        # LineRec paths also state interpolations/s against the FP32 FMA ceiling
+        # every LineRec path: frac = interpolations/s against the FP32 FMA
+        # ceiling (2 FP32 operations per interpolation), whichever kernel runs
         clk = float(bench._peaks().get("sm_max_mhz", 2070.0))
-        assert r["fma_ceiling_ginterp_s"] == pytest.approx(152 * 128 * clk * 1e6 / 2 / 1e9, rel=1e-12)
-        assert 0 < r["frac_of_fma_ceiling"] < 10
+        ceiling = 152 * 128 * clk * 1e6 / 2
+        assert r["unit"] == "Ginterp/s"
+        assert r["peak"] == pytest.approx(ceiling / 1e9, rel=1e-12)
+        interps = 256 * 2048 * 2048 * 2048
+        assert r["achieved"] == pytest.approx(interps / 0.175 / 1e9, rel=1e-12)
+        assert r["frac"] == pytest.approx(interps / 0.175 / ceiling, rel=1e-12)
+        if kernel == 1:  # the dense MMA utilisation is a separately named diagnostic
+            assert 0 < r["mma_frac_of_bf16_peak"] < 10
+        else:
+            assert 0 < r["frac_of_smem_roof"] < 10
