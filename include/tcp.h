@@ -38,13 +38,18 @@
  *     queued surface at a later call or through tcp_device_check.
  *   - The library never synchronises the device inside a compute call, except
  *     where a call says so (first use of an angle set or filter, see below).
- *   - Angle arrays `theta` are HOST pointers to FP64 radians.  On first use of
- *     an angle set the library builds its FP64 cos/sin table, allocates device
- *     memory for it and copies it synchronously; later calls with the same
- *     contents reuse the cached table.  The same holds for filter responses
- *     (keyed by padded length, filter, angle count and centre).  Make the first
- *     call outside CUDA-graph capture.
- *   - Scratch memory that a call needs (a few tables) is taken from the CUDA
+ *   - Angle arrays `theta` are HOST pointers to FP64 radians.  The calls
+ *     without a plan build, on first use of an angle set, its FP64 cos/sin
+ *     table in device memory with a synchronous copy; later calls with the
+ *     same contents reuse the cached table.  The same holds for filter
+ *     responses (keyed by padded length, filter, weight and centre) and the
+ *     FourierRec tables.  Each cache keeps at most 64 entries and frees the
+ *     least recently used one beyond that (cudaFree, which waits for the
+ *     device).  Make the first such call outside CUDA-graph capture, and do
+ *     not let a captured graph outlive its tables.  Plans (tcp_plan_create)
+ *     own their tables and workspace instead: calls that take a plan
+ *     allocate nothing and never synchronise.
+ *   - Scratch memory that a call without a plan needs is taken from the CUDA
  *     stream-ordered allocator on `stream` and released on it.
  *   - No call aborts or throws across the ABI; failures return a tcp_status and
  *     record a message retrievable with tcp_last_error (thread-local).
@@ -409,6 +414,72 @@ tcp_status tcp_batch_info(const tcp_batch* b, tcp_bp_config* cfg, float* tuned_m
                           int32_t* grid_blocks);
 /* Synchronise the device and free the batch (NULL is accepted). */
 tcp_status tcp_batch_destroy(tcp_batch* b);
+
+/* ----------------------------------------------------------------- plans -- */
+
+/* A plan holds everything the reconstruction of one geometry needs besides
+ * the caller's buffers, set up once (Sec. 2.2: the transforms and their
+ * memory are prepared at start; Sec. 2.3: the chunks then run through fixed
+ * device buffers): the FP64 angle table, the filter responses and FFT
+ * twiddles, the FourierRec tables and workspace, the projector's tile-origin
+ * table, the FP32 frame-mean buffers, the chunk sinogram buffer and, for
+ * host input or output, the staging rings with their copy streams and events.
+ *
+ * tcp_plan_create allocates all of it with cudaMalloc on the current device,
+ * uploads the tables and synchronises the device once.  The calls that take
+ * a plan then allocate nothing, never synchronise, read no cached table and
+ * only enqueue work on `stream` (and, for host buffers, on the plan's copy
+ * streams, forked from and joined back to `stream` by events), so their
+ * first use may be captured into a CUDA graph; host buffers must then be
+ * page-locked.  A plan is used by one stream at a time: calls on different
+ * streams that overlap race on its buffers.  tcp_plan_destroy synchronises
+ * the device and frees everything (NULL is accepted). */
+typedef struct tcp_plan tcp_plan;
+
+#define TCP_IO_HOST_RAW 1 /* tcp_fbp_plan's raw may be host memory: allocate the upload ring */
+#define TCP_IO_HOST_VOL 2 /* tcp_fbp_plan's vol may be host memory: allocate the download ring */
+
+typedef struct {
+  int64_t ntheta;       /* projection angles (>= 1) */
+  int64_t nz;           /* slices: the most a tcp_fbp_plan call reconstructs */
+  int64_t ndet;         /* detector pixels per row (<= 4096) */
+  int64_t n;            /* volume side (<= 0: ndet) */
+  double center;        /* rotation axis in detector pixels (filter phase of tcp_fbp_plan/tcp_filter_plan) */
+  int32_t vol_dtype;    /* F32, F16 or BF16 */
+  int32_t io;           /* TCP_IO_HOST_RAW | TCP_IO_HOST_VOL, 0 for device buffers only */
+  int32_t host_frames;  /* U16 dark/flat frames that may come from host memory (0: device frames or means) */
+  int32_t reserved;
+  tcp_fbp_opts opts;    /* chunk, sinogram storage, filter, padding, ring depth, algorithm, width (as tcp_fbp) */
+} tcp_plan_desc;
+
+/* theta: HOST FP64 [ntheta], copied.  *out is NULL on failure.  Errors:
+ * TCP_ERR_SHAPE/DTYPE/ARG for an invalid description, TCP_ERR_OOM when the
+ * device memory does not fit. */
+tcp_status tcp_plan_create(const tcp_plan_desc* desc, const double* theta, tcp_plan** out);
+tcp_status tcp_plan_destroy(tcp_plan* plan);
+/* Device bytes the plan holds, and the options it resolved (chunk depth,
+ * sinogram storage, ring depth, FourierRec width).  Either output may be NULL. */
+tcp_status tcp_plan_info(const tcp_plan* plan, int64_t* device_bytes, tcp_fbp_opts* resolved);
+
+/* tcp_fbp through a plan: raw U16 [ntheta][nz][ndet] with nz <= the plan's,
+ * vol [nz][n][n] of the plan's dtype; raw and vol on the device, or in host
+ * memory where the plan's io flags allow it; dark/flat as for tcp_fbp (host
+ * U16 frames at most host_frames of them).  Same result as tcp_fbp with the
+ * plan's options. */
+tcp_status tcp_fbp_plan(tcp_plan* plan, const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                        tcp_tensor* vol, void* stream);
+/* tcp_filter through a plan (the plan's filter, padding and centre, weight
+ * pi/ntheta): sino F32/F16/BF16 [nz][ntheta][ndet] in place. */
+tcp_status tcp_filter_plan(const tcp_plan* plan, tcp_tensor* sino, void* stream);
+/* tcp_backproject_ex through a plan (its angle table): sino [nz][ntheta][ndet]
+ * (or F16X2 pairs), vol [nz][n][n]. */
+tcp_status tcp_backproject_plan(const tcp_plan* plan, const tcp_tensor* sino, double center, tcp_tensor* vol,
+                                double scale, void* stream);
+/* tcp_project through a plan (its angle table and tile-origin buffer): vol
+ * [nz][n][n] of the plan's n, sino [nz][ntheta][ndet].  Calls that overlap on
+ * the GPU share the origin buffer: serialise them. */
+tcp_status tcp_project_plan(const tcp_plan* plan, const tcp_tensor* vol, double center, tcp_tensor* sino,
+                            void* stream);
 
 #ifdef __cplusplus
 }

@@ -263,3 +263,7 @@ def try_centers(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta
 
 
 __all__.append("try_centers")
+
+from .plan import Plan  # noqa: E402
+
+__all__.append("Plan")

@@ -178,6 +178,24 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("sino_dtype", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("ntheta", ctypes.c_int64), ("nz", ctypes.c_int64), ("ndet", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("center", ctypes.c_double), ("vol_dtype", ctypes.c_int32), ("io", ctypes.c_int32),
+                ("host_frames", ctypes.c_int32), ("reserved", ctypes.c_int32), ("opts", FbpOpts)]
+
+
+IO_HOST_RAW, IO_HOST_VOL = 1, 2
+
+SIGNATURES.update({
+    "tcp_plan_create": ([ctypes.POINTER(PlanDesc), _P, ctypes.POINTER(ctypes.c_void_p)], _I32),
+    "tcp_plan_destroy": ([_P], _I32),
+    "tcp_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(FbpOpts)], _I32),
+    "tcp_fbp_plan": ([_P, _T, _T, _T, _T, _P], _I32),
+    "tcp_filter_plan": ([_P, _T, _P], _I32),
+    "tcp_backproject_plan": ([_P, _T, _D, _T, _D, _P], _I32),
+    "tcp_project_plan": ([_P, _T, _D, _T, _P], _I32),
+})
+
 SIGNATURES.update({
     "tcp_autotune_backproject": ([_T, _P, _D, _T, _P, ctypes.POINTER(BpConfig), ctypes.POINTER(ctypes.c_float)], _I32),
     "tcp_batch_create": ([ctypes.POINTER(BatchItem), _I32, ctypes.POINTER(BatchOpts), _P,

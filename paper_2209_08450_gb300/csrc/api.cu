@@ -58,11 +58,45 @@ static uint64_t fnv1a(const void* p, size_t n) {
   return h;
 }
 
+// The implicit caches below keep at most kCacheCap entries each (per kind);
+// beyond that the least recently used entry is freed.  cudaFree waits for the
+// device, so no queued kernel still reads a freed table; a CUDA graph captured
+// with tables from these caches must not outlive them (plans own theirs).
+constexpr size_t kCacheCap = 64;
+static uint64_t g_stamp = 0;
+
 struct TrigEntry {
   std::vector<double> theta;
   double2* dev = nullptr;
+  uint64_t used = 0;
 };
 static std::unordered_map<uint64_t, std::vector<TrigEntry>> g_trig;  // key: hash ^ device
+static size_t g_trig_count = 0;
+
+static std::vector<double2> trig_host(const double* theta, int64_t n) {
+  std::vector<double2> h((size_t)std::max<int64_t>(n, 1));
+  for (int64_t i = 0; i < n; ++i) h[(size_t)i] = make_double2(std::cos(theta[i]), std::sin(theta[i]));
+  return h;
+}
+
+static void trig_evict_lru() {
+  uint64_t best = UINT64_MAX;
+  uint64_t bkey = 0;
+  size_t bidx = 0;
+  for (auto& kv : g_trig)
+    for (size_t i = 0; i < kv.second.size(); ++i)
+      if (kv.second[i].used < best) {
+        best = kv.second[i].used;
+        bkey = kv.first;
+        bidx = i;
+      }
+  if (best == UINT64_MAX) return;
+  auto& v = g_trig[bkey];
+  cudaFree(v[bidx].dev);
+  v.erase(v.begin() + (long)bidx);
+  if (v.empty()) g_trig.erase(bkey);
+  --g_trig_count;
+}
 
 tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out) {
   int dev = 0;
@@ -70,25 +104,42 @@ tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out) {
   const uint64_t key = fnv1a(theta, sizeof(double) * (size_t)n) ^ ((uint64_t)(dev + 1) * 0x9e3779b97f4a7c15ull) ^
                        (uint64_t)n;
   std::lock_guard<std::mutex> lk(g_mu);
-  auto& bucket = g_trig[key];
-  for (auto& e : bucket)
-    if ((int64_t)e.theta.size() == n && std::memcmp(e.theta.data(), theta, sizeof(double) * (size_t)n) == 0) {
-      out->dev = e.dev;
-      out->n = n;
-      return TCP_OK;
-    }
-  std::vector<double2> h((size_t)std::max<int64_t>(n, 1));
-  for (int64_t i = 0; i < n; ++i) h[(size_t)i] = make_double2(std::cos(theta[i]), std::sin(theta[i]));
+  {
+    auto it = g_trig.find(key);
+    if (it != g_trig.end())
+      for (auto& e : it->second)
+        if ((int64_t)e.theta.size() == n && std::memcmp(e.theta.data(), theta, sizeof(double) * (size_t)n) == 0) {
+          e.used = ++g_stamp;
+          out->dev = e.dev;
+          out->n = n;
+          return TCP_OK;
+        }
+  }
+  if (g_trig_count >= kCacheCap) trig_evict_lru();
+  const std::vector<double2> h = trig_host(theta, n);
   TrigEntry e;
   e.theta.assign(theta, theta + n);
+  e.used = ++g_stamp;
   TCP_CUDA_TRY(cudaMalloc(&e.dev, h.size() * sizeof(double2)));
   cudaError_t err = cudaMemcpy(e.dev, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
     cudaFree(e.dev);
     return cuda_fail(err, "upload angle table");
   }
-  bucket.push_back(e);
+  g_trig[key].push_back(e);
+  ++g_trig_count;
   out->dev = e.dev;
+  out->n = n;
+  return TCP_OK;
+}
+
+tcp_status build_trig_owned(const double* theta, int64_t n, std::vector<void*>* owned, TrigTable* out) {
+  const std::vector<double2> h = trig_host(theta, n);
+  double2* d = nullptr;
+  TCP_CUDA_TRY(cudaMalloc(&d, h.size() * sizeof(double2)));
+  owned->push_back(d);
+  TCP_CUDA_TRY(cudaMemcpy(d, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  out->dev = d;
   out->n = n;
   return TCP_OK;
 }
@@ -179,8 +230,39 @@ struct FiltKey {
 struct FiltKeyHash {
   size_t operator()(const FiltKey& k) const { return (size_t)fnv1a(&k, sizeof(FiltKey)); }
 };
-static std::unordered_map<FiltKey, float2*, FiltKeyHash> g_resp;
+struct RespEntry {
+  float2* dev = nullptr;
+  uint64_t used = 0;
+};
+static std::unordered_map<FiltKey, RespEntry, FiltKeyHash> g_resp;
 static std::unordered_map<uint64_t, float2*> g_tw;  // (dev << 32) | npad
+
+// Two-level twiddle table: 64 low powers, then the powers of W^64.
+static std::vector<float2> twiddle_host(int64_t npad) {
+  const int64_t nhi = (npad + 63) / 64;
+  std::vector<float2> tw((size_t)(64 + nhi));
+  for (int64_t m = 0; m < 64 + nhi; ++m) {
+    const double e = m < 64 ? (double)m : 64.0 * (double)(m - 64);
+    const double ang = -2.0 * M_PI * e / (double)npad;
+    tw[(size_t)m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  }
+  return tw;
+}
+
+// Response bins 0..npad/2: H(k) * weight / npad * e^{2 pi i (k/npad)(center - ndet/2)}.
+static std::vector<float2> response_host(int64_t npad, int64_t ndet, int32_t filter, double weight, double center) {
+  const std::vector<double> H = filter_response(npad, filter);
+  const double shift = center - 0.5 * (double)ndet;
+  const double scale = weight / (double)npad;
+  std::vector<float2> F(H.size());
+  for (int64_t k = 0; k <= npad / 2; ++k) {
+    const double ph = 2.0 * M_PI * ((double)k / (double)npad) * shift;
+    double re = H[(size_t)k] * scale * std::cos(ph), im = H[(size_t)k] * scale * std::sin(ph);
+    if (k == npad / 2) im = 0.0;  // Hermitian Nyquist bin: real part only
+    F[(size_t)k] = make_float2((float)re, (float)im);
+  }
+  return F;
+}
 
 tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out,
                             bool smooth) {
@@ -199,15 +281,8 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
   out->npad = (int)npad;
   const uint64_t twkey = ((uint64_t)(uint32_t)dev << 32) | (uint64_t)npad;
   auto tit = g_tw.find(twkey);
-  if (tit == g_tw.end()) {
-    // two-level table: 64 low powers, then the powers of W^64
-    const int64_t nhi = (npad + 63) / 64;
-    std::vector<float2> tw((size_t)(64 + nhi));
-    for (int64_t m = 0; m < 64 + nhi; ++m) {
-      const double e = m < 64 ? (double)m : 64.0 * (double)(m - 64);
-      const double ang = -2.0 * M_PI * e / (double)npad;
-      tw[(size_t)m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
+  if (tit == g_tw.end()) {  // one small table per padded length: not evicted
+    const std::vector<float2> tw = twiddle_host(npad);
     float2* d = nullptr;
     TCP_CUDA_TRY(cudaMalloc(&d, tw.size() * sizeof(float2)));
     cudaError_t e = cudaMemcpy(d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
@@ -220,16 +295,14 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
   out->twiddle = tit->second;
   auto rit = g_resp.find(key);
   if (rit == g_resp.end()) {
-    const std::vector<double> H = filter_response(npad, filter);
-    const double shift = center - 0.5 * (double)ndet;
-    const double scale = weight / (double)npad;
-    std::vector<float2> F(H.size());
-    for (int64_t k = 0; k <= npad / 2; ++k) {
-      const double ph = 2.0 * M_PI * ((double)k / (double)npad) * shift;
-      double re = H[(size_t)k] * scale * std::cos(ph), im = H[(size_t)k] * scale * std::sin(ph);
-      if (k == npad / 2) im = 0.0;  // Hermitian Nyquist bin: real part only
-      F[(size_t)k] = make_float2((float)re, (float)im);
+    if (g_resp.size() >= kCacheCap) {
+      auto lru = g_resp.begin();
+      for (auto it = g_resp.begin(); it != g_resp.end(); ++it)
+        if (it->second.used < lru->second.used) lru = it;
+      cudaFree(lru->second.dev);
+      g_resp.erase(lru);
     }
+    const std::vector<float2> F = response_host(npad, ndet, filter, weight, center);
     float2* d = nullptr;
     TCP_CUDA_TRY(cudaMalloc(&d, F.size() * sizeof(float2)));
     cudaError_t e = cudaMemcpy(d, F.data(), F.size() * sizeof(float2), cudaMemcpyHostToDevice);
@@ -237,9 +310,28 @@ tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double 
       cudaFree(d);
       return cuda_fail(e, "upload filter response");
     }
-    rit = g_resp.emplace(key, d).first;
+    rit = g_resp.emplace(key, RespEntry{d, 0}).first;
   }
-  out->response = rit->second;
+  rit->second.used = ++g_stamp;
+  out->response = rit->second.dev;
+  return TCP_OK;
+}
+
+tcp_status build_filter_owned(int64_t ndet, int32_t filter, double weight, double center, bool smooth,
+                              std::vector<void*>* owned, FilterTable* out) {
+  const int64_t npad = padded_length(ndet, smooth);
+  const std::vector<float2> tw = twiddle_host(npad);
+  const std::vector<float2> F = response_host(npad, ndet, filter, weight, center);
+  float2 *dt = nullptr, *dr = nullptr;
+  TCP_CUDA_TRY(cudaMalloc(&dt, tw.size() * sizeof(float2)));
+  owned->push_back(dt);
+  TCP_CUDA_TRY(cudaMalloc(&dr, F.size() * sizeof(float2)));
+  owned->push_back(dr);
+  TCP_CUDA_TRY(cudaMemcpy(dt, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  TCP_CUDA_TRY(cudaMemcpy(dr, F.data(), F.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  out->npad = (int)npad;
+  out->twiddle = dt;
+  out->response = dr;
   return TCP_OK;
 }
 
@@ -249,7 +341,8 @@ static tcp_status cache_clear() {
   for (auto& kv : g_trig)
     for (auto& e : kv.second) cudaFree(e.dev);
   g_trig.clear();
-  for (auto& kv : g_resp) cudaFree(kv.second);
+  g_trig_count = 0;
+  for (auto& kv : g_resp) cudaFree(kv.second.dev);
   g_resp.clear();
   for (auto& kv : g_tw) cudaFree(kv.second);
   g_tw.clear();

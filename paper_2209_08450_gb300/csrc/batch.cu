@@ -248,9 +248,11 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     b->owned.push_back(w);
     it.sino.p = w; it.sino.dtype = b->sdt; it.sino.d0 = nz; it.sino.d1 = nt; it.sino.d2 = nd;
     it.sino.s0 = nt * nd; it.sino.s1 = nd;
-    if ((s = get_trig_table(in.theta, nt, &it.trig)) != TCP_OK) break;
-    if ((s = get_filter_table(nd, in.filter, storage_scale(b->sdt), in.center, &it.ft, pad_smooth(in.pad_mode))) !=
-        TCP_OK)
+    // the batch owns its tables, so that its captured graph never depends on
+    // the library's bounded caches
+    if ((s = build_trig_owned(in.theta, nt, &b->owned, &it.trig)) != TCP_OK) break;
+    if ((s = build_filter_owned(nd, in.filter, storage_scale(b->sdt), in.center, pad_smooth(in.pad_mode), &b->owned,
+                                &it.ft)) != TCP_OK)
       break;
     b->items.push_back(it);
   }

@@ -497,9 +497,21 @@ __global__ void __launch_bounds__(256) k_frec_out(const float2* __restrict__ H, 
 
 struct SortedAngles {
   std::vector<double> theta;
+  uint64_t hash = 0;      // of the angle array's bytes
+  uint64_t used = 0;      // last-use stamp (least recently used goes first)
   int2* meta = nullptr;   // (original index, sign of k) per sorted position
   float* thS = nullptr;   // theta' in [0, pi), ascending
 };
+// Angle sets kept per device; beyond this the least recently used set is freed.
+constexpr size_t kAngleCacheCap = 64;
+uint64_t g_frec_stamp = 0;
+
+uint64_t bytes_hash(const void* p, size_t n) {  // FNV-1a
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
 struct HostTables {
   std::map<std::pair<int, int>, float2*> tw;                 // (dev, N) -> e^{-2 pi i j / N}
   std::map<std::tuple<int, int, int, int>, float*> dec;      // (dev, n, L, W) -> 1 / Phi(x / L)
@@ -579,16 +591,9 @@ tcp_status get_deconv(int dev, int n, int L, int W, const float** out) {
 }
 
 // Angles folded to theta' = theta mod pi in [0, pi) (k changes sign when
-// theta mod 2 pi >= pi: the same line through the origin), sorted ascending.
-tcp_status get_sorted_angles(int dev, const double* theta, int nt, const int2** meta, const float** thS) {
-  std::lock_guard<std::mutex> lk(g_frec_mu);
-  auto& lst = g_frec.ang[dev];
-  for (auto& e : lst)
-    if ((int)e.theta.size() == nt && std::equal(e.theta.begin(), e.theta.end(), theta)) {
-      *meta = e.meta;
-      *thS = e.thS;
-      return TCP_OK;
-    }
+// theta mod 2 pi >= pi: the same line through the origin), sorted ascending:
+// per sorted position the original index and the sign of k, and theta'.
+void sort_angles(const double* theta, int nt, std::vector<int2>* meta, std::vector<float>* ths) {
   std::vector<std::pair<double, int2>> v((size_t)nt);
   for (int t = 0; t < nt; ++t) {
     double a = std::fmod(theta[t], 2.0 * M_PI);
@@ -604,14 +609,41 @@ tcp_status get_sorted_angles(int dev, const double* theta, int nt, const int2** 
   std::stable_sort(v.begin(), v.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
     return x.first < y.first;
   });
-  std::vector<int2> hm((size_t)nt);
-  std::vector<float> ht((size_t)nt);
+  meta->resize((size_t)std::max(nt, 1));
+  ths->resize((size_t)std::max(nt, 1));
   for (int u = 0; u < nt; ++u) {
-    hm[(size_t)u] = v[(size_t)u].second;
-    ht[(size_t)u] = (float)v[(size_t)u].first;
+    (*meta)[(size_t)u] = v[(size_t)u].second;
+    (*ths)[(size_t)u] = (float)v[(size_t)u].first;
   }
+}
+
+// Cached per device and angle set.
+tcp_status get_sorted_angles(int dev, const double* theta, int nt, const int2** meta, const float** thS) {
+  std::lock_guard<std::mutex> lk(g_frec_mu);
+  auto& lst = g_frec.ang[dev];
+  const uint64_t h = bytes_hash(theta, sizeof(double) * (size_t)nt);
+  for (auto& e : lst)
+    if (e.hash == h && (int)e.theta.size() == nt && std::equal(e.theta.begin(), e.theta.end(), theta)) {
+      e.used = ++g_frec_stamp;
+      *meta = e.meta;
+      *thS = e.thS;
+      return TCP_OK;
+    }
+  if (lst.size() >= kAngleCacheCap) {
+    // cudaFree waits for the device, so no queued kernel still reads the set
+    auto lru = std::min_element(lst.begin(), lst.end(),
+                                [](const SortedAngles& a, const SortedAngles& b) { return a.used < b.used; });
+    cudaFree(lru->meta);
+    cudaFree(lru->thS);
+    lst.erase(lru);
+  }
+  std::vector<int2> hm;
+  std::vector<float> ht;
+  sort_angles(theta, nt, &hm, &ht);
   SortedAngles e;
   e.theta.assign(theta, theta + nt);
+  e.hash = h;
+  e.used = ++g_frec_stamp;
   TCP_CUDA_TRY(cudaMalloc(&e.meta, sizeof(int2) * (size_t)std::max(nt, 1)));
   cudaError_t err = cudaMalloc(&e.thS, sizeof(float) * (size_t)std::max(nt, 1));
   if (err != cudaSuccess) {
@@ -710,83 +742,155 @@ tcp_status fourierrec_check(int64_t nt, int64_t nd, int64_t n, int width) {
   return TCP_OK;
 }
 
-tcp_status launch_fourierrec(const View3& sv, const double* theta, const TrigTable& trig, double center,
-                             const View3& vv, float scale, int width, cudaStream_t st) {
+// Slice pairs per batch and workspace bytes of one FourierRec call on nz
+// slices (the batch is capped at about 1.5 GiB of P + H + G).
+size_t fourierrec_workspace_bytes(int64_t nt, int64_t nd, int64_t n, int64_t nz, int* nb_out) {
+  const int lgM = std::max(1, ilog2(2 * nd)), lgL = ilog2(fourierrec_grid(n));
+  const int64_t ms = (int64_t(1) << lgM) + 1, L = int64_t(1) << lgL;
+  const int64_t npairs = std::max<int64_t>(1, (nz + 1) / 2);
+  const int64_t p_pair = nt * ms, h_pair = n * L, g_pair = L * L;
+  const size_t per_pair = sizeof(float2) * (size_t)(p_pair + h_pair + g_pair);
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(npairs, (int64_t)(kBatchBytes / per_pair)));
+  if (nb_out) *nb_out = nb;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up(sizeof(float4) * (size_t)std::max<int64_t>(nt, 1)) + up(sizeof(float2) * (size_t)ms) +
+         up(sizeof(float2) * (size_t)p_pair * nb) + up(sizeof(float2) * (size_t)h_pair * nb) +
+         up(sizeof(float2) * (size_t)g_pair * nb);
+}
+
+// Carve the workspace of fourierrec_workspace_bytes out of `base`.
+FrecWorkspace fourierrec_workspace(void* base, int64_t nt, int64_t nd, int64_t n, int64_t nz) {
+  FrecWorkspace w;
+  const int lgM = std::max(1, ilog2(2 * nd)), lgL = ilog2(fourierrec_grid(n));
+  const int64_t ms = (int64_t(1) << lgM) + 1, L = int64_t(1) << lgL;
+  fourierrec_workspace_bytes(nt, nd, n, nz, &w.nb);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* p = (char*)base;
+  w.geom = p;
+  p += up(sizeof(float4) * (size_t)std::max<int64_t>(nt, 1));
+  w.phase = p;
+  p += up(sizeof(float2) * (size_t)ms);
+  w.P = p;
+  p += up(sizeof(float2) * (size_t)(nt * ms) * w.nb);
+  w.H = p;
+  p += up(sizeof(float2) * (size_t)(n * L) * w.nb);
+  w.G = p;
+  return w;
+}
+
+// Cached tables (built on first use of a size, width or angle set).
+tcp_status fourierrec_tables_cached(const double* theta, int64_t nt, int64_t nd, int64_t n, int width,
+                                    FrecTables* t) {
+  const int lgM = std::max(1, ilog2(2 * nd)), lgL = ilog2(fourierrec_grid(n));
+  int dev = 0;
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
+  tcp_status s;
+  if ((s = get_twiddles(dev, 1 << lgM, &t->twM)) != TCP_OK) return s;
+  if ((s = get_twiddles(dev, 1 << lgL, &t->twL)) != TCP_OK) return s;
+  if ((s = get_deconv(dev, (int)n, 1 << lgL, width, &t->dec)) != TCP_OK) return s;
+  return get_sorted_angles(dev, theta, (int)nt, &t->meta, &t->thS);
+}
+
+// Tables owned by the caller (a plan): cudaMalloc and synchronous upload, the
+// allocations appended to `owned`.
+tcp_status fourierrec_tables_owned(const double* theta, int64_t nt, int64_t nd, int64_t n, int width,
+                                   std::vector<void*>* owned, FrecTables* t) {
+  const int lgM = std::max(1, ilog2(2 * nd)), lgL = ilog2(fourierrec_grid(n));
+  auto upload = [&](const void* h, size_t bytes, const void** out) -> tcp_status {
+    void* d = nullptr;
+    TCP_CUDA_TRY(cudaMalloc(&d, bytes ? bytes : 16));
+    owned->push_back(d);
+    if (bytes) TCP_CUDA_TRY(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice));
+    *out = d;
+    return TCP_OK;
+  };
+  auto twiddles = [](int N) {
+    std::vector<float2> h((size_t)N);
+    for (int j = 0; j < N; ++j) {
+      const double a = -2.0 * M_PI * (double)j / (double)N;
+      h[(size_t)j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    return h;
+  };
+  tcp_status s;
+  const std::vector<float2> hM = twiddles(1 << lgM), hL = twiddles(1 << lgL);
+  if ((s = upload(hM.data(), hM.size() * sizeof(float2), (const void**)&t->twM)) != TCP_OK) return s;
+  if ((s = upload(hL.data(), hL.size() * sizeof(float2), (const void**)&t->twL)) != TCP_OK) return s;
+  std::vector<float> hd((size_t)n);
+  for (int64_t i = 0; i < n; ++i) hd[(size_t)i] = (float)(1.0 / es_fourier((double)(i - n / 2) / (double)(1 << lgL), width));
+  if ((s = upload(hd.data(), hd.size() * sizeof(float), (const void**)&t->dec)) != TCP_OK) return s;
+  std::vector<int2> hm;
+  std::vector<float> ht;
+  sort_angles(theta, (int)nt, &hm, &ht);
+  if ((s = upload(hm.data(), hm.size() * sizeof(int2), (const void**)&t->meta)) != TCP_OK) return s;
+  return upload(ht.data(), ht.size() * sizeof(float), (const void**)&t->thS);
+}
+
+tcp_status launch_fourierrec_ws(const View3& sv, const FrecTables& tb, const FrecWorkspace& w, const TrigTable& trig,
+                                double center, const View3& vv, float scale, int width, cudaStream_t st) {
   const int nz = (int)sv.d0, nt = (int)sv.d1, nd = (int)sv.d2, n = (int)vv.d1;
   tcp_status s;
   if ((s = fourierrec_check(nt, nd, n, width)) != TCP_OK) return s;
   const int lgM = std::max(1, ilog2(2 * (int64_t)nd)), lgL = ilog2(fourierrec_grid(n));
   const int M = 1 << lgM, L = 1 << lgL;
   const int ms = M + 1;
-  int dev = 0;
-  TCP_CUDA_TRY(cudaGetDevice(&dev));
-  const float2 *twM = nullptr, *twL = nullptr;
-  const float* dec = nullptr;
-  if ((s = get_twiddles(dev, M, &twM)) != TCP_OK) return s;
-  if ((s = get_twiddles(dev, L, &twL)) != TCP_OK) return s;
-  if ((s = get_deconv(dev, n, L, width, &dec)) != TCP_OK) return s;
-  const int2* meta = nullptr;
-  const float* thS = nullptr;
-  if ((s = get_sorted_angles(dev, theta, nt, &meta, &thS)) != TCP_OK) return s;
-
   const int npairs = (nz + 1) / 2;
   const int64_t p_pair = (int64_t)nt * ms, h_pair = (int64_t)n * L, g_pair = (int64_t)L * L;
-  const size_t per_pair = sizeof(float2) * (size_t)(p_pair + h_pair + g_pair);
-  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(npairs, (int64_t)(kBatchBytes / per_pair)));
-
-  struct Ws {
-    cudaStream_t st;
-    std::vector<void*> p;
-    ~Ws() {
-      for (void* q : p) cudaFreeAsync(q, st);
-    }
-    tcp_status alloc(void** q, size_t bytes) {
-      const cudaError_t e = cudaMallocAsync(q, bytes ? bytes : 16, st);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
-      p.push_back(*q);
-      return TCP_OK;
-    }
-  } ws{st, {}};
-  void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
-  if ((s = ws.alloc(&geom, sizeof(float4) * (size_t)nt)) != TCP_OK) return s;
-  if ((s = ws.alloc(&phase, sizeof(float2) * (size_t)ms)) != TCP_OK) return s;
-  if ((s = ws.alloc(&P, sizeof(float2) * (size_t)p_pair * nb)) != TCP_OK) return s;
-  if ((s = ws.alloc(&H, sizeof(float2) * (size_t)h_pair * nb)) != TCP_OK) return s;
-  if ((s = ws.alloc(&G, sizeof(float2) * (size_t)g_pair * nb)) != TCP_OK) return s;
+  const int nb = std::max(1, std::min(npairs, w.nb));
   {
     const int cnt = std::max(nt, ms);
-    k_frec_geom<<<(cnt + 255) / 256, 256, 0, st>>>(trig.dev, meta, nt, (double)L / (double)M, (float4*)geom,
-                                                     center, M, (float2*)phase);
+    k_frec_geom<<<(cnt + 255) / 256, 256, 0, st>>>(trig.dev, tb.meta, nt, (double)L / (double)M, (float4*)w.geom,
+                                                     center, M, (float2*)w.phase);
     TCP_CUDA_TRY(cudaGetLastError());
   }
   for (int p0 = 0; p0 < npairs; p0 += nb) {
     const int b = std::min(nb, npairs - p0), z0 = 2 * p0;
     switch (sv.dtype) {
-      case TCP_F32: launch_rows<float>(sv, z0, b, lgM, twM, (const float2*)phase, (float2*)P, p_pair, ms, st); break;
-      case TCP_F16: launch_rows<__half>(sv, z0, b, lgM, twM, (const float2*)phase, (float2*)P, p_pair, ms, st); break;
+      case TCP_F32:
+        launch_rows<float>(sv, z0, b, lgM, tb.twM, (const float2*)w.phase, (float2*)w.P, p_pair, ms, st);
+        break;
+      case TCP_F16:
+        launch_rows<__half>(sv, z0, b, lgM, tb.twM, (const float2*)w.phase, (float2*)w.P, p_pair, ms, st);
+        break;
       case TCP_BF16:
-        launch_rows<__nv_bfloat16>(sv, z0, b, lgM, twM, (const float2*)phase, (float2*)P, p_pair, ms, st);
+        launch_rows<__nv_bfloat16>(sv, z0, b, lgM, tb.twM, (const float2*)w.phase, (float2*)w.P, p_pair, ms, st);
         break;
       default: return fail(TCP_ERR_DTYPE, "fourierrec: sino must be F32, F16 or BF16");
     }
     TCP_CUDA_TRY(cudaGetLastError());
-    launch_gather<4, 4>(width, (const float2*)P, p_pair, ms, (const float4*)geom, meta, thS, nt, M, lgL, (float2*)G,
-                        g_pair, b, st);
+    launch_gather<4, 4>(width, (const float2*)w.P, p_pair, ms, (const float4*)w.geom, tb.meta, tb.thS, nt, M, lgL,
+                        (float2*)w.G, g_pair, b, st);
     TCP_CUDA_TRY(cudaGetLastError());
-    launch_cols((const float2*)G, g_pair, lgL, n, twL, dec, (float2*)H, h_pair, b, st);
+    launch_cols((const float2*)w.G, g_pair, lgL, n, tb.twL, tb.dec, (float2*)w.H, h_pair, b, st);
     TCP_CUDA_TRY(cudaGetLastError());
     View3 ov = vv;
     switch (vv.dtype) {
-      case TCP_F32: launch_out<float>((const float2*)H, h_pair, lgL, n, twL, dec, scale, ov, z0, b, st); break;
-      case TCP_F16: launch_out<__half>((const float2*)H, h_pair, lgL, n, twL, dec, scale, ov, z0, b, st); break;
+      case TCP_F32: launch_out<float>((const float2*)w.H, h_pair, lgL, n, tb.twL, tb.dec, scale, ov, z0, b, st); break;
+      case TCP_F16: launch_out<__half>((const float2*)w.H, h_pair, lgL, n, tb.twL, tb.dec, scale, ov, z0, b, st); break;
       case TCP_BF16:
-        launch_out<__nv_bfloat16>((const float2*)H, h_pair, lgL, n, twL, dec, scale, ov, z0, b, st);
+        launch_out<__nv_bfloat16>((const float2*)w.H, h_pair, lgL, n, tb.twL, tb.dec, scale, ov, z0, b, st);
         break;
       default: return fail(TCP_ERR_DTYPE, "fourierrec: vol must be F32, F16 or BF16");
     }
     TCP_CUDA_TRY(cudaGetLastError());
   }
   return TCP_OK;
+}
+
+tcp_status launch_fourierrec(const View3& sv, const double* theta, const TrigTable& trig, double center,
+                             const View3& vv, float scale, int width, cudaStream_t st) {
+  const int64_t nz = sv.d0, nt = sv.d1, nd = sv.d2, n = vv.d1;
+  tcp_status s;
+  if ((s = fourierrec_check(nt, nd, n, width)) != TCP_OK) return s;
+  FrecTables tb;
+  if ((s = fourierrec_tables_cached(theta, nt, nd, n, width, &tb)) != TCP_OK) return s;
+  const size_t bytes = fourierrec_workspace_bytes(nt, nd, n, nz, nullptr);
+  void* base = nullptr;
+  TCP_CUDA_TRY(cudaMallocAsync(&base, bytes, st));
+  s = launch_fourierrec_ws(sv, tb, fourierrec_workspace(base, nt, nd, n, nz), trig, center, vv, scale, width, st);
+  const cudaError_t e = cudaFreeAsync(base, st);
+  if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+  return s;
 }
 
 }  // namespace tcp

@@ -126,8 +126,13 @@ void (*pick_s(int sdt, int K))(PjArgs) {
 
 }  // namespace
 
-tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
-                          cudaStream_t st) {
+size_t project_origin_bytes(int64_t ntheta, int64_t n) {
+  const int64_t ntx = (n + kTile - 1) / kTile;
+  return (size_t)std::max<int64_t>(1, ntheta * ntx * ntx) * sizeof(int2);
+}
+
+tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* orig_ws,
+                             cudaStream_t st) {
   const int nz = (int)vol.d0, n = (int)vol.d1, nt = (int)sino.d1, nd = (int)sino.d2;
   if (nz == 0 || nt == 0 || nd == 0) return TCP_OK;
   const int K = nz >= 8 ? 8 : (nz >= 4 ? 4 : (nz >= 2 ? 2 : 1));
@@ -153,27 +158,30 @@ tcp_status launch_project(const View3& vol, const TrigTable& trig, double center
   a.trig = trig.dev;
   a.center = center;
   a.half_n = 0.5 * (double)n;
-  int2* orig = nullptr;
-  const size_t bytes = (size_t)nt * a.ntx * a.ntx * sizeof(int2);
-  TCP_CUDA_TRY(cudaMallocAsync((void**)&orig, bytes > 0 ? bytes : 8, st));
+  dim3 grid((unsigned)((nd + kPjThreads - 1) / kPjThreads), (unsigned)nt, (unsigned)((nz + K - 1) / K));
+  if (grid.y > 65535u || grid.z > 65535u)
+    return fail(TCP_ERR_SHAPE, "project: too many angles or slice blocks for one launch");
+  int2* orig = reinterpret_cast<int2*>(orig_ws);
   if (n > 0) {
     const int64_t total = (int64_t)nt * a.ntx * a.ntx;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     k_origin_table<<<blocks, 256, 0, st>>>(trig.dev, nt, a.ntx, a.half_n, center, orig);
   }
   a.orig = orig;
-  dim3 grid((unsigned)((nd + kPjThreads - 1) / kPjThreads), (unsigned)nt, (unsigned)((nz + K - 1) / K));
-  cudaError_t e1 = cudaSuccess;
-  if (grid.y > 65535u || grid.z > 65535u) {
-    cudaFreeAsync(orig, st);
-    return fail(TCP_ERR_SHAPE, "project: too many angles or slice blocks for one launch");
-  }
   k<<<grid, kPjThreads, 0, st>>>(a);
-  e1 = cudaGetLastError();
-  cudaError_t e2 = cudaFreeAsync(orig, st);
-  if (e1 != cudaSuccess) return cuda_fail(e1, "project kernel launch");
-  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  TCP_CUDA_TRY(cudaGetLastError());
   return TCP_OK;
+}
+
+tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
+                          cudaStream_t st) {
+  if (vol.d0 == 0 || sino.d1 == 0 || sino.d2 == 0) return TCP_OK;
+  void* orig = nullptr;
+  TCP_CUDA_TRY(cudaMallocAsync(&orig, project_origin_bytes(sino.d1, vol.d1), st));
+  const tcp_status s = launch_project_ws(vol, trig, center, sino, orig, st);
+  const cudaError_t e = cudaFreeAsync(orig, st);
+  if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+  return s;
 }
 
 }  // namespace tcp

@@ -117,144 +117,106 @@ tcp_status device_means(const tcp_tensor* t, int64_t nz, int64_t nd, Scope& sc, 
   return TCP_OK;
 }
 
+// Chunk schedule.  With host buffers the first chunk's upload and the last
+// chunk's download are not hidden behind compute, so those two chunks are
+// half as deep (the middle ones, whose copies overlap compute, stay full).
+std::vector<std::pair<int64_t, int64_t>> chunk_schedule(int64_t nz, int64_t chunk, bool host_io) {
+  std::vector<std::pair<int64_t, int64_t>> sched;  // (z0, slices)
+  int64_t z = 0;
+  if (host_io && nz > chunk && chunk > 1) {
+    sched.push_back({0, chunk / 2});
+    z = chunk / 2;
+  }
+  while (nz - z > chunk + (host_io ? chunk / 2 : 0) && chunk > 0) {
+    sched.push_back({z, chunk});
+    z += chunk;
+  }
+  if (host_io && nz - z > chunk) {  // tail: one full chunk, then the short last one
+    sched.push_back({z, chunk});
+    z += chunk;
+  }
+  if (nz - z > 0) sched.push_back({z, nz - z});
+  return sched;
+}
+
 }  // namespace
-}  // namespace tcp
 
-using namespace tcp;
-
-extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
-                              const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
-                              void* stream) {
-  if (!raw || !dark || !flat || !vol) return fail(TCP_ERR_ARG, "fbp: null tensor");
+tcp_status fbp_resolve(const tcp_tensor* raw, const tcp_tensor* vol, const tcp_fbp_opts* opts, FbpParams* p) {
+  if (!raw || !vol) return fail(TCP_ERR_ARG, "fbp: null tensor");
   if (raw->ndim != 3 || raw->dtype != TCP_U16) return fail(TCP_ERR_DTYPE, "fbp: raw must be U16 [ntheta][nz][ndet]");
   if (vol->ndim != 3 || (vol->dtype != TCP_F32 && vol->dtype != TCP_F16 && vol->dtype != TCP_BF16))
     return fail(TCP_ERR_DTYPE, "fbp: vol must be F32/F16/BF16 [nz][n][n]");
-  const int64_t nt = raw->shape[0], nz = raw->shape[1], nd = raw->shape[2], n = vol->shape[1];
-  if (vol->shape[0] != nz || vol->shape[2] != n) return fail(TCP_ERR_SHAPE, "fbp: vol must be [nz][n][n]");
-  if (raw->stride[2] != 1 || vol->stride[2] != 1) return fail(TCP_ERR_ALIGN, "fbp: innermost stride must be 1");
-  for (const tcp_tensor* df : {dark, flat}) {
-    const bool ok = (df->ndim == 2 && df->dtype == TCP_F32 && df->shape[0] == nz && df->shape[1] == nd) ||
-                    (df->ndim == 3 && df->dtype == TCP_U16 && df->shape[0] >= 1 && df->shape[1] == nz &&
-                     df->shape[2] == nd);
-    if (!ok) return fail(TCP_ERR_SHAPE, "fbp: dark/flat must be F32 [nz][ndet] or U16 [nf][nz][ndet]");
-  }
-  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "fbp: center must be finite");
-  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "fbp: theta is null");
+  return fbp_resolve_shape(raw->shape[0], raw->shape[1], raw->shape[2], vol->shape[1], vol->dtype, opts, p);
+}
+
+tcp_status fbp_resolve_shape(int64_t nt, int64_t nz, int64_t nd, int64_t n, int vdt, const tcp_fbp_opts* opts,
+                             FbpParams* p) {
   if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "fbp: ndet > 4096");
   tcp_fbp_opts o{};
   if (opts) o = *opts;
+  if (o.algorithm != TCP_ALG_LINEREC && o.algorithm != TCP_ALG_FOURIERREC)
+    return fail(TCP_ERR_ARG, "fbp: unknown algorithm");
+  const bool frec = o.algorithm == TCP_ALG_FOURIERREC;
   // Sinogram storage: as requested, else FP16 hi/lo pairs for an FP32 volume
   // (FP32-accurate on the tensor cores; needs ndet % 8 == 0 for 16-byte rows,
   // FP32 otherwise) and the volume's own type for 16-bit volumes.
   int sdt = o.sino_dtype;
-  if (o.algorithm != TCP_ALG_LINEREC && o.algorithm != TCP_ALG_FOURIERREC)
-    return fail(TCP_ERR_ARG, "fbp: unknown algorithm");
-  const bool frec = o.algorithm == TCP_ALG_FOURIERREC;
   if (sdt != TCP_F32 && sdt != TCP_F16 && sdt != TCP_BF16 && sdt != TCP_F16X2)
-    sdt = vol->dtype != TCP_F32 ? vol->dtype : (nd % 8 == 0 && !frec ? TCP_F16X2 : TCP_F32);
+    sdt = vdt != TCP_F32 ? vdt : (nd % 8 == 0 && !frec ? TCP_F16X2 : TCP_F32);
   if (frec && sdt == TCP_F16X2) return fail(TCP_ERR_DTYPE, "fbp: FourierRec takes F32, F16 or BF16 sinograms");
-  const int frec_width = o.width == 0 ? fourierrec_default_width(vol->dtype, n) : o.width;
+  const int frec_width = o.width == 0 ? fourierrec_default_width(vdt, n) : o.width;
   if (frec) {
     tcp_status sf = fourierrec_check(nt, nd, n, frec_width);
     if (sf != TCP_OK) return sf;
   }
+  if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
+  if (!valid_pad_mode(o.pad_mode)) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
+  p->nt = nt;
+  p->nz = nz;
+  p->nd = nd;
+  p->n = n;
+  p->vdt = vdt;
+  p->sdt = sdt;
+  p->frec = frec;
+  p->width = frec_width;
   // default chunk: 256 slices for 16-bit sinograms (the tensor-core
   // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel), 64 for
   // FourierRec (32 slice pairs)
-  const int64_t chunk = o.chunk_nz > 0 ? o.chunk_nz : frec ? 64 : (sdt == TCP_F32 ? 32 : 256);
-  if (o.filter < TCP_FILTER_SHEPP || o.filter > TCP_FILTER_NONE) return fail(TCP_ERR_ARG, "fbp: unknown filter");
-  if (!valid_pad_mode(o.pad_mode)) return fail(TCP_ERR_ARG, "fbp: unknown pad mode");
-  const int B = o.n_buffers == 3 ? 3 : 2;
-  if (nz == 0 || n == 0 || nt == 0 || nd == 0) {
-    if (nz * n * n > 0) return fail(TCP_ERR_SHAPE, "fbp: empty projections for a non-empty volume");
-    return TCP_OK;
-  }
-  for (int64_t i = 0; i < nt; ++i)
-    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "fbp: theta must be finite");
-
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const Where wraw = where(raw->data), wvol = where(vol->data);
-  if (wraw != kDevice && raw->stride[1] != nd) return fail(TCP_ERR_ALIGN, "fbp: host raw rows must be packed");
-
-  TrigTable trig;
-  FilterTable ft;
-  tcp_status s;
-  if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
+  p->chunk = o.chunk_nz > 0 ? o.chunk_nz : frec ? 64 : (sdt == TCP_F32 ? 32 : 256);
+  p->cz = std::max<int64_t>(1, std::min(p->chunk, nz));
+  p->B = o.n_buffers == 3 ? 3 : 2;
+  p->filter = o.filter;
+  p->pad = o.pad_mode;
   // The stored sinogram carries the band-limited ramp times storage_scale;
   // the pi/N_theta FBP weight and 1/storage_scale are applied when the
   // backprojector writes each voxel (Sec. 2.1: reorder so 16-bit values stay
   // in range).
-  const double sscale = storage_scale(sdt);
-  if ((s = get_filter_table(nd, o.filter, sscale, center, &ft, pad_smooth(o.pad_mode))) != TCP_OK) return s;
-  const float bp_scale = (float)(M_PI / (double)nt / sscale);
-  tcp_bp_config cfg;
-  tcp_get_backproject_config(std::min(chunk, nz), nt, nd, n, sdt, vol->dtype, &cfg);
+  p->sscale = storage_scale(sdt);
+  p->bp_scale = nt > 0 ? (float)(M_PI / (double)nt / p->sscale) : 1.f;
+  tcp_get_backproject_config(p->cz, nt, nd, n, sdt, vdt, &p->cfg);
+  return TCP_OK;
+}
 
-  Scope sc;
-  sc.st = st;
-  View3 dm, fm;
-  if ((s = device_means(dark, nz, nd, sc, &dm)) != TCP_OK) return s;
-  if ((s = device_means(flat, nz, nd, sc, &fm)) != TCP_OK) return s;
-
-  const int64_t cz = std::min(chunk, nz);
-  void* sino = nullptr;
-  if ((s = sc.alloc(&sino, (size_t)cz * nt * nd * esize(sdt))) != TCP_OK) return s;
-
-  cudaStream_t cin = nullptr, cout = nullptr;
-  cudaEvent_t ev_alloc;
-  std::vector<void*> rring(B, nullptr), vring(B, nullptr);
-  std::vector<cudaEvent_t> raw_ready(B), raw_free(B), vol_ready(B), vol_free(B);
-  const bool host_raw = wraw != kDevice, host_vol = wvol != kDevice;
-  if (host_raw) {
-    if ((s = sc.stream(&cin)) != TCP_OK) return s;
-    for (int b = 0; b < B; ++b) {
-      if ((s = sc.alloc(&rring[b], (size_t)nt * cz * nd * 2)) != TCP_OK) return s;
-      if ((s = sc.event(&raw_ready[b])) != TCP_OK) return s;
-      if ((s = sc.event(&raw_free[b])) != TCP_OK) return s;
-    }
+tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const View3& fm, const tcp_tensor* raw,
+                   tcp_tensor* vol, bool host_raw, bool host_vol, cudaStream_t st) {
+  const int64_t nt = p.nt, nz = p.nz, nd = p.nd, n = p.n, chunk = p.chunk, cz = p.cz;
+  const int B = p.B, sdt = p.sdt;
+  cudaStream_t cin = r.cin, cout = r.cout;
+  if (host_raw || host_vol) {  // fork the copy streams off the caller's stream
+    TCP_CUDA_TRY(cudaEventRecord(r.fork, st));
+    if (host_raw) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, r.fork, 0));
+    if (host_vol) TCP_CUDA_TRY(cudaStreamWaitEvent(cout, r.fork, 0));
   }
-  if (host_vol) {
-    if ((s = sc.stream(&cout)) != TCP_OK) return s;
-    for (int b = 0; b < B; ++b) {
-      if ((s = sc.alloc(&vring[b], (size_t)cz * n * n * esize(vol->dtype))) != TCP_OK) return s;
-      if ((s = sc.event(&vol_ready[b])) != TCP_OK) return s;
-      if ((s = sc.event(&vol_free[b])) != TCP_OK) return s;
-    }
-  }
-  if ((s = sc.event(&ev_alloc)) != TCP_OK) return s;
-  TCP_CUDA_TRY(cudaEventRecord(ev_alloc, st));
-  if (cin) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, ev_alloc, 0));
-  if (cout) TCP_CUDA_TRY(cudaStreamWaitEvent(cout, ev_alloc, 0));
-
-  // Chunk schedule.  With host buffers the first chunk's upload and the last
-  // chunk's download are not hidden behind compute, so those two chunks are
-  // half as deep (the middle ones, whose copies overlap compute, stay full).
-  std::vector<std::pair<int64_t, int64_t>> sched;  // (z0, slices)
-  {
-    int64_t z = 0;
-    if ((host_raw || host_vol) && nz > chunk && chunk > 1) {
-      sched.push_back({0, chunk / 2});
-      z = chunk / 2;
-    }
-    while (nz - z > chunk + ((host_raw || host_vol) ? chunk / 2 : 0) && chunk > 0) {
-      sched.push_back({z, chunk});
-      z += chunk;
-    }
-    if ((host_raw || host_vol) && nz - z > chunk) {  // tail: one full chunk, then the short last one
-      sched.push_back({z, chunk});
-      z += chunk;
-    }
-    if (nz - z > 0) sched.push_back({z, nz - z});
-  }
+  const auto sched = chunk_schedule(nz, chunk, host_raw || host_vol);
   const int64_t nchunks = (int64_t)sched.size();
   auto issue_copy_in = [&](int64_t k) -> tcp_status {
     const int b = (int)(k % B);
     const int64_t z0 = sched[(size_t)k].first, c = sched[(size_t)k].second;
-    if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, raw_free[b], 0));
-    TCP_CUDA_TRY(cudaMemcpy2DAsync(rring[b], (size_t)c * nd * 2,
+    if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, r.raw_free[b], 0));
+    TCP_CUDA_TRY(cudaMemcpy2DAsync(r.rring[b], (size_t)c * nd * 2,
                                    (const uint16_t*)raw->data + z0 * raw->stride[1], (size_t)raw->stride[0] * 2,
                                    (size_t)c * nd * 2, (size_t)nt, cudaMemcpyHostToDevice, cin));
-    TCP_CUDA_TRY(cudaEventRecord(raw_ready[b], cin));
+    TCP_CUDA_TRY(cudaEventRecord(r.raw_ready[b], cin));
     return TCP_OK;
   };
   if (host_raw)
@@ -267,8 +229,8 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
     rv.dtype = TCP_U16;
     rv.d0 = nt; rv.d1 = c; rv.d2 = nd;
     if (host_raw) {
-      TCP_CUDA_TRY(cudaStreamWaitEvent(st, raw_ready[b], 0));
-      rv.p = rring[b]; rv.s0 = c * nd; rv.s1 = nd;
+      TCP_CUDA_TRY(cudaStreamWaitEvent(st, r.raw_ready[b], 0));
+      rv.p = r.rring[b]; rv.s0 = c * nd; rv.s1 = nd;
     } else {
       rv.p = (uint16_t*)raw->data + z0 * raw->stride[1];
       rv.s0 = raw->stride[0]; rv.s1 = raw->stride[1];
@@ -277,56 +239,128 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
     dv.p = (float*)dm.p + z0 * dm.s1; dv.d1 = c;
     fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
     View3 sv;
-    sv.p = sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
-    sv.plane = sdt == TCP_F16X2 ? cz * nt * nd : 0;
-    TRY_S(launch_normalize_filter(rv, dv, fv, sv, ft, o.pad_mode, st));
+    sv.p = r.sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    sv.plane = sdt == TCP_F16X2 ? r.sino_cz * nt * nd : 0;
+    TRY_S(launch_normalize_filter(rv, dv, fv, sv, r.ft, p.pad, st));
     if (host_raw) {
-      TCP_CUDA_TRY(cudaEventRecord(raw_free[b], st));
+      TCP_CUDA_TRY(cudaEventRecord(r.raw_free[b], st));
       if (k + B < nchunks) TRY_S(issue_copy_in(k + B));
     }
     View3 vv;
-    vv.dtype = vol->dtype; vv.d0 = c; vv.d1 = n; vv.d2 = n;
+    vv.dtype = p.vdt; vv.d0 = c; vv.d1 = n; vv.d2 = n;
     if (host_vol) {
-      if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(st, vol_free[b], 0));
-      vv.p = vring[b]; vv.s0 = n * n; vv.s1 = n;
+      if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(st, r.vol_free[b], 0));
+      vv.p = r.vring[b]; vv.s0 = n * n; vv.s1 = n;
     } else {
-      vv.p = (char*)vol->data + z0 * vol->stride[0] * esize(vol->dtype);
+      vv.p = (char*)vol->data + z0 * vol->stride[0] * esize(p.vdt);
       vv.s0 = vol->stride[0]; vv.s1 = vol->stride[1];
     }
-    if (frec)
-      TRY_S(launch_fourierrec(sv, theta, trig, 0.5 * (double)nd, vv, bp_scale, frec_width, st));
+    if (p.frec)
+      TRY_S(launch_fourierrec_ws(sv, r.frt, r.fws, r.trig, 0.5 * (double)nd, vv, p.bp_scale, p.width, st));
     else
-      TRY_S(launch_backproject(sv, trig, 0.5 * (double)nd, vv, cfg, st, bp_scale));
+      TRY_S(launch_backproject(sv, r.trig, 0.5 * (double)nd, vv, p.cfg, st, p.bp_scale));
     if (host_vol) {
-      const int es = esize(vol->dtype);
-      TCP_CUDA_TRY(cudaEventRecord(vol_ready[b], st));
-      TCP_CUDA_TRY(cudaStreamWaitEvent(cout, vol_ready[b], 0));
+      const int es = esize(p.vdt);
+      TCP_CUDA_TRY(cudaEventRecord(r.vol_ready[b], st));
+      TCP_CUDA_TRY(cudaStreamWaitEvent(cout, r.vol_ready[b], 0));
       if (vol->stride[1] == n && vol->stride[0] == n * n) {
-        TCP_CUDA_TRY(cudaMemcpyAsync((char*)vol->data + z0 * n * n * es, vring[b], (size_t)c * n * n * es,
+        TCP_CUDA_TRY(cudaMemcpyAsync((char*)vol->data + z0 * n * n * es, r.vring[b], (size_t)c * n * n * es,
                                      cudaMemcpyDeviceToHost, cout));
       } else {
         for (int64_t z = 0; z < c; ++z)
-          TCP_CUDA_TRY(cudaMemcpy2DAsync((char*)vol->data + ((z0 + z) * vol->stride[0]) * es, (size_t)vol->stride[1] * es,
-                                       (char*)vring[b] + (size_t)z * n * n * es, (size_t)n * es, (size_t)n * es,
-                                       (size_t)n, cudaMemcpyDeviceToHost, cout));
+          TCP_CUDA_TRY(cudaMemcpy2DAsync((char*)vol->data + ((z0 + z) * vol->stride[0]) * es,
+                                         (size_t)vol->stride[1] * es, (char*)r.vring[b] + (size_t)z * n * n * es,
+                                         (size_t)n * es, (size_t)n * es, (size_t)n, cudaMemcpyDeviceToHost, cout));
       }
-      TCP_CUDA_TRY(cudaEventRecord(vol_free[b], cout));
+      TCP_CUDA_TRY(cudaEventRecord(r.vol_free[b], cout));
     }
   }
+  (void)cz;
   // Join the side streams so that `stream` completes after every copy.
-  if (cout) {
-    cudaEvent_t done;
-    TRY_S(sc.event(&done));
-    TCP_CUDA_TRY(cudaEventRecord(done, cout));
-    TCP_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+  if (host_vol) {
+    TCP_CUDA_TRY(cudaEventRecord(r.join_out, cout));
+    TCP_CUDA_TRY(cudaStreamWaitEvent(st, r.join_out, 0));
   }
-  if (cin) {
-    cudaEvent_t done;
-    TRY_S(sc.event(&done));
-    TCP_CUDA_TRY(cudaEventRecord(done, cin));
-    TCP_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+  if (host_raw) {
+    TCP_CUDA_TRY(cudaEventRecord(r.join_in, cin));
+    TCP_CUDA_TRY(cudaStreamWaitEvent(st, r.join_in, 0));
   }
   return TCP_OK;
+}
+
+bool is_device_ptr(const void* p) { return where(p) == kDevice; }
+bool is_pinned_ptr(const void* p) { return where(p) == kPinned; }
+
+}  // namespace tcp
+
+using namespace tcp;
+
+extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
+                              const double* theta, double center, tcp_tensor* vol, const tcp_fbp_opts* opts,
+                              void* stream) {
+  if (!raw || !dark || !flat || !vol) return fail(TCP_ERR_ARG, "fbp: null tensor");
+  FbpParams p;
+  tcp_status s;
+  if ((s = fbp_resolve(raw, vol, opts, &p)) != TCP_OK) return s;
+  const int64_t nt = p.nt, nz = p.nz, nd = p.nd, n = p.n;
+  if (vol->shape[0] != nz || vol->shape[2] != n) return fail(TCP_ERR_SHAPE, "fbp: vol must be [nz][n][n]");
+  if (raw->stride[2] != 1 || vol->stride[2] != 1) return fail(TCP_ERR_ALIGN, "fbp: innermost stride must be 1");
+  for (const tcp_tensor* df : {dark, flat}) {
+    const bool ok = (df->ndim == 2 && df->dtype == TCP_F32 && df->shape[0] == nz && df->shape[1] == nd) ||
+                    (df->ndim == 3 && df->dtype == TCP_U16 && df->shape[0] >= 1 && df->shape[1] == nz &&
+                     df->shape[2] == nd);
+    if (!ok) return fail(TCP_ERR_SHAPE, "fbp: dark/flat must be F32 [nz][ndet] or U16 [nf][nz][ndet]");
+  }
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "fbp: center must be finite");
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "fbp: theta is null");
+  if (nz == 0 || n == 0 || nt == 0 || nd == 0) {
+    if (nz * n * n > 0) return fail(TCP_ERR_SHAPE, "fbp: empty projections for a non-empty volume");
+    return TCP_OK;
+  }
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "fbp: theta must be finite");
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Where wraw = where(raw->data), wvol = where(vol->data);
+  if (wraw != kDevice && raw->stride[1] != nd) return fail(TCP_ERR_ALIGN, "fbp: host raw rows must be packed");
+
+  FbpRes r;
+  if ((s = get_trig_table(theta, nt, &r.trig)) != TCP_OK) return s;
+  if ((s = get_filter_table(nd, p.filter, p.sscale, center, &r.ft, pad_smooth(p.pad))) != TCP_OK) return s;
+  Scope sc;
+  sc.st = st;
+  if (p.frec) {
+    if ((s = fourierrec_tables_cached(theta, nt, nd, n, p.width, &r.frt)) != TCP_OK) return s;
+    void* ws = nullptr;
+    if ((s = sc.alloc(&ws, fourierrec_workspace_bytes(nt, nd, n, p.cz, nullptr))) != TCP_OK) return s;
+    r.fws = fourierrec_workspace(ws, nt, nd, n, p.cz);
+  }
+  View3 dm, fm;
+  if ((s = device_means(dark, nz, nd, sc, &dm)) != TCP_OK) return s;
+  if ((s = device_means(flat, nz, nd, sc, &fm)) != TCP_OK) return s;
+  if ((s = sc.alloc(&r.sino, (size_t)p.cz * nt * nd * esize(p.sdt))) != TCP_OK) return s;
+  r.sino_cz = p.cz;
+  const bool host_raw = wraw != kDevice, host_vol = wvol != kDevice;
+  if (host_raw) {
+    if ((s = sc.stream(&r.cin)) != TCP_OK) return s;
+    for (int b = 0; b < p.B; ++b) {
+      if ((s = sc.alloc(&r.rring[b], (size_t)nt * p.cz * nd * 2)) != TCP_OK) return s;
+      if ((s = sc.event(&r.raw_ready[b])) != TCP_OK) return s;
+      if ((s = sc.event(&r.raw_free[b])) != TCP_OK) return s;
+    }
+    if ((s = sc.event(&r.join_in)) != TCP_OK) return s;
+  }
+  if (host_vol) {
+    if ((s = sc.stream(&r.cout)) != TCP_OK) return s;
+    for (int b = 0; b < p.B; ++b) {
+      if ((s = sc.alloc(&r.vring[b], (size_t)p.cz * n * n * esize(p.vdt))) != TCP_OK) return s;
+      if ((s = sc.event(&r.vol_ready[b])) != TCP_OK) return s;
+      if ((s = sc.event(&r.vol_free[b])) != TCP_OK) return s;
+    }
+    if ((s = sc.event(&r.join_out)) != TCP_OK) return s;
+  }
+  if ((s = sc.event(&r.fork)) != TCP_OK) return s;
+  return fbp_run(p, r, dm, fm, raw, vol, host_raw, host_vol, st);
 }
 
 // Multi-centre "try" reconstruction (Sec. 2.4, --reconstruction-type try): one

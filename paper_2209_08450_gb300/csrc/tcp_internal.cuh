@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <string>
 #include <type_traits>
+#include <vector>
 
 #include "tcp.h"
 
@@ -120,6 +121,8 @@ struct TrigTable {
 };
 // Cached FP64 cos/sin table for a host angle array (first use uploads it).
 tcp_status get_trig_table(const double* theta, int64_t n, TrigTable* out);
+// The same table in memory owned by the caller (appended to `owned`).
+tcp_status build_trig_owned(const double* theta, int64_t n, std::vector<void*>* owned, TrigTable* out);
 
 struct FilterTable {
   const float2* response = nullptr;  // npad/2+1 complex factors (incl. 1/npad)
@@ -132,6 +135,9 @@ struct FilterTable {
 // weight multiplies the response (pi/N_theta for FBP; any value > 0).
 tcp_status get_filter_table(int64_t ndet, int32_t filter, double weight, double center, FilterTable* out,
                             bool smooth = false);
+// The same response and twiddles in memory owned by the caller.
+tcp_status build_filter_owned(int64_t ndet, int32_t filter, double weight, double center, bool smooth,
+                              std::vector<void*>* owned, FilterTable* out);
 // pad_mode: bit 0 zero padding (else edge), bit 1 smooth padded length
 inline bool valid_pad_mode(int32_t m) { return m >= 0 && m <= (TCP_PAD_ZERO | TCP_PAD_SMOOTH); }
 inline bool pad_smooth(int32_t m) { return (m & TCP_PAD_SMOOTH) != 0; }
@@ -162,6 +168,11 @@ tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double c
                               const tcp_bp_config& cfg, cudaStream_t st, float scale = 1.0f);
 tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
                           cudaStream_t st);
+// The projector with its per-call tile-origin table (ntheta x ntx^2 int2,
+// project_origin_bytes) in caller-provided device memory.
+size_t project_origin_bytes(int64_t ntheta, int64_t n);
+tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* orig,
+                             cudaStream_t st);
 // FourierRec (k_fourierrec.cu): default window width per volume dtype, the
 // shape/width checks, and the launcher (sino F32/F16/BF16, vol F32/F16/BF16).
 int64_t fourierrec_grid(int64_t n);  // Cartesian grid side L
@@ -170,6 +181,28 @@ void fourierrec_cache_clear();  // frees the cached twiddle, deconvolution and a
 tcp_status fourierrec_check(int64_t ntheta, int64_t ndet, int64_t n, int width);
 tcp_status launch_fourierrec(const View3& sino, const double* theta, const TrigTable& trig, double center,
                              const View3& vol, float scale, int width, cudaStream_t st);
+// The same split into tables (twiddles of the row and grid lengths, 1/Phi
+// deconvolution factors, angles folded to [0, pi) and sorted) and a
+// workspace (geometry, centre phase, spectra P, half-transformed H, grid G
+// for nb slice pairs), so that a plan can own both.
+struct FrecTables {
+  const float2 *twM = nullptr, *twL = nullptr;
+  const float* dec = nullptr;
+  const int2* meta = nullptr;
+  const float* thS = nullptr;
+};
+struct FrecWorkspace {
+  void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
+  int nb = 1;  // slice pairs per batch
+};
+size_t fourierrec_workspace_bytes(int64_t nt, int64_t nd, int64_t n, int64_t nz, int* nb);
+FrecWorkspace fourierrec_workspace(void* base, int64_t nt, int64_t nd, int64_t n, int64_t nz);
+tcp_status fourierrec_tables_cached(const double* theta, int64_t nt, int64_t nd, int64_t n, int width,
+                                    FrecTables* t);
+tcp_status fourierrec_tables_owned(const double* theta, int64_t nt, int64_t nd, int64_t n, int width,
+                                   std::vector<void*>* owned, FrecTables* t);
+tcp_status launch_fourierrec_ws(const View3& sv, const FrecTables& tb, const FrecWorkspace& w, const TrigTable& trig,
+                                double center, const View3& vv, float scale, int width, cudaStream_t st);
 
 // Arguments of one backprojection (one dataset of a batch).
 struct BpArgs {
@@ -203,6 +236,45 @@ int bp_threads(const tcp_bp_config& c);
 tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* blocks);
 tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, const tcp_bp_config& cfg, int blocks,
                                          cudaStream_t st);
+
+// ------------------------------------------------ chunked FBP (pipeline.cu) --
+
+// Resolved options of one chunked FBP.
+struct FbpParams {
+  int64_t nt = 0, nz = 0, nd = 0, n = 0;
+  int vdt = TCP_F32, sdt = TCP_F32;
+  bool frec = false;
+  int width = 0;
+  int64_t chunk = 0, cz = 0;  // requested chunk depth, and the deepest chunk of this run
+  int B = 2;                  // ring depth for host buffers
+  int filter = 0, pad = 0;
+  double sscale = 1.0;        // storage scale of the filtered sinogram
+  float bp_scale = 1.f;       // pi / ntheta / sscale, applied at the voxel store
+  tcp_bp_config cfg{};
+};
+// Device resources of one chunked FBP: tables, workspace, ring buffers,
+// copy streams and events (from a plan, or taken for one call).
+struct FbpRes {
+  TrigTable trig;
+  FilterTable ft;
+  FrecTables frt;
+  FrecWorkspace fws;
+  void* sino = nullptr;  // chunk sinogram buffer
+  int64_t sino_cz = 0;   // slices it holds (F16X2: the distance between the planes)
+  void* rring[3] = {nullptr, nullptr, nullptr};
+  void* vring[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t raw_ready[3] = {}, raw_free[3] = {}, vol_ready[3] = {}, vol_free[3] = {};
+  cudaEvent_t fork = nullptr, join_in = nullptr, join_out = nullptr;
+};
+tcp_status fbp_resolve(const tcp_tensor* raw, const tcp_tensor* vol, const tcp_fbp_opts* opts, FbpParams* p);
+tcp_status fbp_resolve_shape(int64_t nt, int64_t nz, int64_t nd, int64_t n, int vdt, const tcp_fbp_opts* opts,
+                             FbpParams* p);
+// dm/fm: FP32 means [nz][nd] on the device.
+tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const View3& fm, const tcp_tensor* raw,
+                   tcp_tensor* vol, bool host_raw, bool host_vol, cudaStream_t st);
+bool is_device_ptr(const void* p);
+bool is_pinned_ptr(const void* p);
 
 bool tuned_bp_config(int64_t nz, int64_t nt, int64_t nd, int64_t n, int sdt, int vdt, tcp_bp_config* cfg);
 tcp_bp_config bp_override();

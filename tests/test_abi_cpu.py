@@ -220,3 +220,40 @@ def test_normalize_rejects_misaligned_and_aliased_buffers(lib, name):
     alias = _t(_lib.F32, (2, 4, 16), ptr=(1 << 20) + 64)  # inside raw's 256 bytes
     assert fn(*args(raw, dark, flat, alias)) == 10
     assert b"overlap" in lib.tcp_last_error()
+
+
+def test_plan_create_validates_its_arguments(lib):
+    # every check of tcp_plan_create runs on the host before any CUDA call
+    th = (ctypes.c_double * 4)(0, 0.5, 1.0, 1.5)
+    h = ctypes.c_void_p(1234)
+
+    def desc(**kw):
+        d = _lib.PlanDesc()
+        d.ntheta, d.nz, d.ndet, d.n, d.center, d.vol_dtype = 4, 8, 32, 0, 16.0, _lib.F32
+        d.opts.sino_dtype = -1
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    create = lambda d, t=th: lib.tcp_plan_create(ctypes.byref(d), t, ctypes.byref(h))
+    assert lib.tcp_plan_create(None, th, ctypes.byref(h)) == 1 and h.value is None
+    assert lib.tcp_plan_create(ctypes.byref(desc()), th, None) == 1
+    assert create(desc(ntheta=0)) == 2
+    assert create(desc(nz=-1)) == 2
+    assert create(desc(ndet=0)) == 2
+    assert create(desc(vol_dtype=_lib.U16)) == 3
+    assert create(desc(io=4)) == 1
+    assert create(desc(host_frames=-1)) == 1
+    assert create(desc(center=float("nan"))) == 1
+    assert create(desc(), None) == 1
+    bad = (ctypes.c_double * 4)(0, float("inf"), 1.0, 1.5)
+    assert create(desc(), bad) == 1
+    assert b"theta" in lib.tcp_last_error()
+    # calls on a null plan are rejected, destroying NULL is accepted
+    t = _t(_lib.F32, (2, 4, 32))
+    assert lib.tcp_fbp_plan(None, ctypes.byref(t), ctypes.byref(t), ctypes.byref(t), ctypes.byref(t), None) == 1
+    assert lib.tcp_filter_plan(None, ctypes.byref(t), None) == 1
+    assert lib.tcp_backproject_plan(None, ctypes.byref(t), 16.0, ctypes.byref(t), 1.0, None) == 1
+    assert lib.tcp_project_plan(None, ctypes.byref(t), 16.0, ctypes.byref(t), None) == 1
+    assert lib.tcp_plan_info(None, None, None) == 1
+    assert lib.tcp_plan_destroy(None) == 0
