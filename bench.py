@@ -63,9 +63,8 @@ def barrier(world: int, device_index=None):
 
 def slab(nz: int, rank: int, world: int) -> tuple[int, int]:
     """Contiguous z-slab [z0, z1) of rank among world (the paper's start/end rows)."""
-    base, extra = divmod(nz, world)
-    z0 = rank * base + min(rank, extra)
-    return z0, z0 + base + (1 if rank < extra else 0)
+    from paper_2209_08450_gb300.slabs import slab as _slab
+    return _slab(nz, rank, world)
 
 
 # ---------------------------------------------------------------- clocks --
@@ -418,6 +417,9 @@ def main():
     ap.add_argument("--ref-slices", type=int, default=1)
     ap.add_argument("--parity-slices", type=int, default=2)
     ap.add_argument("--no-rows", action="store_true", help="skip the least-squares and batch rows")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: 'replicas' (each rank its own seeded dataset, weak scaling) or 'slab' (one dataset, "
+                         "rank r reconstructs its z-slab through views of the shared stack, strong scaling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -442,7 +444,8 @@ def main():
     # ---- input: seeded synthetic dataset, resident in HBM (not timed)
     t_gen = time.perf_counter()
     nz = args.nz or n
-    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, nt, n, seed=rank, device=dev,
+    split = args.split == "slab" and world > 1
+    raw, dark, flat, theta, center, mu = sgpu.porous_frames(n, nt, n, seed=0 if split else rank, device=dev,
                                                             slices=np.arange((n - nz) // 2, (n - nz) // 2 + nz))
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
@@ -459,11 +462,18 @@ def main():
     hdt = vdt_of(hp)
     nchunks = (nz + chunk_for(hp) - 1) // chunk_for(hp)
 
+    from paper_2209_08450_gb300 import slabs
+    z0_r, z1_r = slabs.slab(nz, rank, world) if split else (0, nz)
+    my_nz = z1_r - z0_r  # slices this rank reconstructs
+
     def run_steps(path, steps, warmup, out):
         stream = torch.cuda.current_stream()
+        # split mode: this rank's z-slab of the one dataset, through views
+        fbp = (lambda r, d, f, th, c, **kw: slabs.reconstruct_slab(r, d, f, th, c, kw.pop("out"), rank, world, **kw)) \
+            if split else tcp.fbp
 
         def step():
-            tcp.fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(path), sino_dtype=sdt_of(path),
+            fbp(raw, dark, flat, theta, center, out=out, chunk_nz=chunk_for(path), sino_dtype=sdt_of(path),
                     algorithm="fourierrec" if path in FOURIERREC else "linerec", width=FOURIERREC.get(path, 0),
                     stream=stream)
         for _ in range(warmup):
@@ -480,11 +490,12 @@ def main():
         return reduce_max(e0.elapsed_time(e1) / steps, world, dev)
 
     # ---- headline: FP32 storage and arithmetic (unless --dtype says otherwise)
-    vol = torch.empty((nz, n, n), dtype=hdt, device=dev)
+    vol = torch.empty((my_nz, n, n), dtype=hdt, device=dev)
     with ClockSampler(local) as clk:
         ms = run_steps(hp, args.steps, args.warmup, vol)
     clocks = clk.summary()
-    value = world * nz * n * n / (ms * 1e-3) / 1e9
+    # replicas: every rank a full dataset; slab: the ranks share one
+    value = (nz if split else world * nz) * n * n / (ms * 1e-3) / 1e9
 
     # ---- parity on sampled slices (oracle on the same uint16 frames)
     def parity(v, zs, path=None):
@@ -510,6 +521,8 @@ def main():
         return float(max(errs))
 
     zs = [int(x) for x in np.linspace(nz // 5, 4 * nz // 5, args.parity_slices)]
+    if split:  # rank 0 checks slices of its own slab (vol holds only that slab)
+        zs = [int(x) for x in np.linspace(my_nz // 5, 4 * my_nz // 5, args.parity_slices)] if my_nz > 0 else []
     par = {args.dtype: parity(vol, zs, hp)} if rank == 0 and zs else {}
 
     # ---- dominant kernel, timed alone on one filtered chunk (same launch shape)
@@ -565,7 +578,7 @@ def main():
 
     # ---- other paths: 16-bit storage, FP32 sinograms on the CUDA cores
     variants = {}
-    for name in [v for v in args.variants.split(",") if v and v != hp]:
+    for name in [v for v in args.variants.split(",") if v and v != hp and not split]:
         vv = torch.empty((nz, n, n), dtype=vdt_of(name), device=dev)
         vms = run_steps(name, args.variant_steps, 1, vv)
         variants[name] = {"value": world * nz * n * n / (vms * 1e-3) / 1e9, "ms_per_step": vms,
@@ -581,7 +594,7 @@ def main():
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not split:
         del vol
         torch.cuda.empty_cache()
         raw_h = torch.empty(raw.shape, dtype=raw.dtype, pin_memory=True)
@@ -616,7 +629,7 @@ def main():
         del raw_h, vol_h
 
     rows = None
-    if not args.no_rows and world == 1:
+    if not args.no_rows and world == 1 and not split:
         del raw, dark, flat
         torch.cuda.empty_cache()
         rows = measure_rows(dev)
@@ -639,7 +652,7 @@ def main():
             launches_per_step = 2 + 2 * nchunks  # 2 frame means + per chunk: normalise+filter, backproject
         out = {
             "metric": METRIC, "value": value, "unit": "GVoxel/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong" if split else "weak",
             "vs_baseline": value / PAPER_LINEREC_GVOXS, "dtype": "f32" if hp.startswith("f32") else hp,
             "path": hp, "data": DATA,
             "config": {"workload": "%dx%d^2 FBP (%s) from %d uint16 projections of %dx%d, angles on [0, pi), "
@@ -648,7 +661,9 @@ def main():
                                       nt, n, nz, chunk_for(hp)),
                        "n": n, "nz": nz, "ntheta": nt, "chunk_nz": chunk_for(hp),
                        "sino_storage": "f16x2" if hp == "f32" else (PATHS[hp][1] or PATHS[hp][0]),
-                       "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9)},
+                       "l2": "inputs larger than L2 (%.1f GB uint16 per step)" % (raw_bytes / 1e9),
+                       "parallelism": ("z-slab split of one dataset over %d ranks, no collective on the data path"
+                                       % world) if split else ("%d independent replicas" % world)},
             "roofline": roofline, "secondary_kernels": secondary, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "parity_rel_l2_sampled": par, "tolerance": {"f32": 1e-5, "f32_cuda": 1e-5, "f16": 5e-3, "bf16": 5e-3, "f32_frec": 1e-5,
