@@ -277,7 +277,32 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
 tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double center,
                           tcp_tensor* vol, double scale, int32_t width, void* stream);
 
-/* Backprojector launch configuration.  k_slices: slices per thread block
+/* LpRec backprojection (Sec. 1, Sec. 3: the backprojection evaluated in
+ * log-polar coordinates, where it is a convolution, with cubic B-splines, for
+ * equally spaced angles).  Each filtered row is replaced by its interpolating
+ * cubic B-spline q~ (zero samples outside the detector) and, per voxel,
+ *   vol[z][iy][ix] = scale * sum over theta of q~_{z,theta}(s(x, y, theta))
+ * with the ray coordinate of tcp_backproject, evaluated as: three spans of a
+ * third of the angles each; per span the log-polar origin at 4 R outside the
+ * object (R = n/sqrt(2) + 2) on the span's middle direction, G_theta(tau) =
+ * q~_theta(center - a cos(theta - phi) + e^tau) sampled on a uniform
+ * log-radius grid and turned into B-spline coefficients, the span's sum as a
+ * convolution on the uniform (log-radius, angle) grid, its 2-D B-spline
+ * coefficients, and the 4 x 4 cubic interpolation at every voxel.  Grid steps
+ * are 1/oversampling pixel at the far radius (oversampling <= 0: 2; the error
+ * to the direct cubic-spline sums falls with it, about 6e-3, 6e-4, 5e-5 at
+ * 2, 4, 8 on white-noise rows).
+ * theta: HOST FP64 [ntheta], ntheta >= 3, equally spaced (to 1e-9) over a
+ * half turn [theta0, theta0 + pi), else TCP_ERR_ARG; sino: F32/F16/BF16
+ * [nz][ntheta][ndet]; vol: F32/F16/BF16 [nz][n][n], overwritten.  Works in
+ * stream-ordered workspace (about 0.9 GiB per slice of a pass at n = 2048,
+ * oversampling 2, passes of at most 16 slices) and caches the slice-independent
+ * geometry (8 sets, least recently used freed beyond that) built on first use
+ * with synchronous uploads: make that call outside CUDA-graph capture. */
+tcp_status tcp_lprec(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol, double scale,
+                     double oversampling, void* stream);
+
+/* Backprojector launch configuration./* Backprojector launch configuration.  k_slices: slices per thread block
  * (1, 2, 4, 8 or 16); theta_stage: angles staged in shared memory per step
  * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4).
  * kernel: 0 = FP32 pipes (every dtype); 1 = tensor cores (tcgen05.mma with
@@ -310,16 +335,19 @@ typedef struct {
   int32_t pad_mode;     /* tcp_pad_mode */
   int32_t n_buffers;    /* device ring depth, 2 or 3 (default 2) */
   int32_t algorithm;    /* tcp_algorithm: backprojector (0 = LineRec) */
-  int32_t width;        /* FourierRec window width (0: the tcp_fourierrec default) */
+  int32_t width;        /* FourierRec window width (0: the tcp_fourierrec default); LpRec
+                           oversampling, an integer 1..8 (0: 2) */
   int32_t reserved[1];
 } tcp_fbp_opts;
 
-/* Backprojector of tcp_fbp (Sec. 3 names both): LineRec, the direct
- * linear-interpolation sum (tcp_backproject), or FourierRec, the
- * Fourier-slice evaluation with band-limited interpolation (tcp_fourierrec;
- * F32/F16/BF16 sinogram chunks, the default F32 for FP32 volumes; chunk_nz
- * <= 0 gives 64; n must be even). */
-typedef enum { TCP_ALG_LINEREC = 0, TCP_ALG_FOURIERREC = 1 } tcp_algorithm;
+/* Backprojector of tcp_fbp (Sec. 3 names all three): LineRec, the direct
+ * linear-interpolation sum (tcp_backproject); FourierRec, the Fourier-slice
+ * evaluation with band-limited interpolation (tcp_fourierrec; F32/F16/BF16
+ * sinogram chunks, the default F32 for FP32 volumes; chunk_nz <= 0 gives 64;
+ * n must be even); or LpRec, the log-polar evaluation with cubic B-splines
+ * (tcp_lprec; F32/F16/BF16 chunks as FourierRec; chunk_nz <= 0 gives 16;
+ * equally spaced angles over a half turn). */
+typedef enum { TCP_ALG_LINEREC = 0, TCP_ALG_FOURIERREC = 1, TCP_ALG_LPREC = 2 } tcp_algorithm;
 
 /* Chunked FBP (Sec. 2.3): for each chunk of chunk_nz slices, copy the raw
  * z-slab in, normalise, filter (axis moved to ndet/2) and backproject into

@@ -159,6 +159,27 @@ def fourierrec(sino: torch.Tensor, theta, center: float, n: int | None = None,
     return out
 
 
+def lprec(sino: torch.Tensor, theta, center: float, n: int | None = None, out: torch.Tensor | None = None,
+          dtype=None, scale: float = 1.0, oversampling: float = 0.0, stream=None) -> torch.Tensor:
+    """LpRec backprojection sino[z][theta][j] -> vol[z][n][n]: scale x (sum over
+    angles of each row's interpolating cubic B-spline), evaluated per third of
+    the angles in log-polar coordinates (grid steps 1/oversampling pixel at
+    the far radius; 0 picks 2).  The angles must be equally spaced over a half
+    turn."""
+    th = _lib.theta_array(theta)
+    nz, nt, nd = sino.shape
+    if out is None:
+        n = nd if n is None else n
+        out = torch.empty((nz, n, n), dtype=_lib.DTYPES[dtype or sino.dtype], device=sino.device)
+    a, b = _lib.desc(sino), _lib.desc(out)
+    _lib.call("tcp_lprec", _lib.ref(a), th.ctypes.data_as(ctypes.c_void_p), float(center), _lib.ref(b),
+              float(scale), float(oversampling), _lib.stream_ptr(stream))
+    return out
+
+
+__all__.append("lprec")
+
+
 def device_check(stream=None) -> int:
     """Read and clear the device error word (synchronises the stream); raises if set."""
     w = ctypes.c_uint32(0)
@@ -202,8 +223,10 @@ def fbp(raw: torch.Tensor, dark: torch.Tensor, flat: torch.Tensor, theta, center
     (page-locked host memory lets the slab copies overlap compute).  dark/flat
     are uint16 frames [nf][z][j] or FP32 means [z][j].  The volume is
     reconstructed about the filtered axis ndet/2 with the `center` shift folded
-    into the filter.  algorithm: "linerec" (direct sum, linear interpolation)
-    or "fourierrec" (Fourier-slice evaluation, window `width`; n even).
+    into the filter.  algorithm: "linerec" (direct sum, linear interpolation),
+    "fourierrec" (Fourier-slice evaluation, window `width`; n even) or
+    "lprec" (log-polar evaluation with cubic B-splines, oversampling `width`,
+    0 for 2; equally spaced angles).
     Returns `out` once the work is queued on the stream."""
     raw = _as_u16(raw)
     nt, nz, nd = raw.shape

@@ -64,7 +64,7 @@ class FbpOpts(ctypes.Structure):
                 ("width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
-ALGORITHMS = {"linerec": 0, "fourierrec": 1}
+ALGORITHMS = {"linerec": 0, "fourierrec": 1, "lprec": 2}
 
 
 _lock = threading.Lock()
@@ -93,6 +93,7 @@ SIGNATURES = {
     "tcp_backproject": ([_T, _P, _D, _T, _P], _I32),
     "tcp_project": ([_T, _P, _D, _T, _P], _I32),
     "tcp_fourierrec": ([_T, _P, _D, _T, _D, _I32, _P], _I32),
+    "tcp_lprec": ([_T, _P, _D, _T, _D, _D, _P], _I32),
     "tcp_set_backproject_config": ([ctypes.POINTER(BpConfig)], _I32),
     "tcp_get_backproject_config": ([_I64, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(BpConfig)], _I32),
     "tcp_fbp": ([_T, _T, _T, _P, _D, _T, ctypes.POINTER(FbpOpts), _P], _I32),

@@ -347,6 +347,7 @@ static tcp_status cache_clear() {
   for (auto& kv : g_tw) cudaFree(kv.second);
   g_tw.clear();
   fourierrec_cache_clear();
+  lprec_cache_clear();
   return TCP_OK;
 }
 
@@ -728,6 +729,42 @@ tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double ce
   TrigTable trig;
   if ((s = get_trig_table(theta, nt, &trig)) != TCP_OK) return s;
   return launch_fourierrec(view3(sino), theta, trig, center, view3(vol), (float)scale, w, st);
+}
+
+tcp_status tcp_lprec(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol, double scale,
+                     double oversampling, void* stream) {
+  tcp_status s;
+  if (!std::isfinite(scale)) return fail(TCP_ERR_ARG, "scale must be finite");
+  if ((s = check_tensor(sino, "sino", 3, 4)) != TCP_OK) return s;
+  if (!is_float(sino->dtype) || sino->ndim != 3)
+    return fail(TCP_ERR_DTYPE, "lprec: sino must be F32, F16 or BF16 [nz][ntheta][ndet]");
+  if ((s = check_tensor(vol, "vol", 3, 3)) != TCP_OK) return s;
+  if (!is_float(vol->dtype)) return fail(TCP_ERR_DTYPE, "vol must be F32, F16 or BF16");
+  if (vol->shape[0] != sino->shape[0]) return fail(TCP_ERR_SHAPE, "vol and sino must have the same slice count");
+  if (vol->shape[1] != vol->shape[2]) return fail(TCP_ERR_SHAPE, "vol slices must be square [n][n]");
+  if (!std::isfinite(center)) return fail(TCP_ERR_ARG, "center must be finite");
+  const int64_t nt = sino->shape[1], nd = sino->shape[2], n = vol->shape[1];
+  if (nt > 0 && !theta) return fail(TCP_ERR_ARG, "theta is null");
+  for (int64_t i = 0; i < nt; ++i)
+    if (!std::isfinite(theta[i])) return fail(TCP_ERR_ARG, "theta must be finite");
+  const double os = oversampling > 0 ? oversampling : 2.0;
+  if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
+  LpHostGeom probe;
+  if (nt >= 1 && (s = lprec_geometry(theta, nt, nd, std::max<int64_t>(n, 1), center, os, &probe)) != TCP_OK) return s;
+  if (nt >= 1 && (s = lprec_check(probe)) != TCP_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (numel(vol) == 0) return TCP_OK;
+  if (nt == 0 || nd == 0) return fail(TCP_ERR_SHAPE, "lprec: empty projections for a non-empty volume");
+  const LpHostGeom* g = nullptr;
+  const LpDevGeom* d = nullptr;
+  if ((s = lprec_cached(theta, nt, nd, n, center, os, &g, &d)) != TCP_OK) return s;
+  const int zpass = lprec_slices_per_pass(*g, vol->shape[0]);
+  void* ws = nullptr;
+  TCP_CUDA_TRY(cudaMallocAsync(&ws, lprec_workspace_bytes(*g, zpass), st));
+  s = launch_lprec_ws(view3(sino), *g, *d, ws, zpass, view3(vol), (float)scale, st);
+  const cudaError_t e = cudaFreeAsync(ws, st);
+  if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
+  return s;
 }
 
 tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center, tcp_tensor* sino, void* stream) {

@@ -154,16 +154,19 @@ tcp_status fbp_resolve_shape(int64_t nt, int64_t nz, int64_t nd, int64_t n, int 
   if (nd > 4096) return fail(TCP_ERR_UNSUPPORTED, "fbp: ndet > 4096");
   tcp_fbp_opts o{};
   if (opts) o = *opts;
-  if (o.algorithm != TCP_ALG_LINEREC && o.algorithm != TCP_ALG_FOURIERREC)
+  if (o.algorithm != TCP_ALG_LINEREC && o.algorithm != TCP_ALG_FOURIERREC && o.algorithm != TCP_ALG_LPREC)
     return fail(TCP_ERR_ARG, "fbp: unknown algorithm");
+  const bool lprec = o.algorithm == TCP_ALG_LPREC;
   const bool frec = o.algorithm == TCP_ALG_FOURIERREC;
+  if (lprec && (o.width < 0 || o.width > 8)) return fail(TCP_ERR_ARG, "fbp: LpRec oversampling must be 1..8");
   // Sinogram storage: as requested, else FP16 hi/lo pairs for an FP32 volume
   // (FP32-accurate on the tensor cores; needs ndet % 8 == 0 for 16-byte rows,
   // FP32 otherwise) and the volume's own type for 16-bit volumes.
   int sdt = o.sino_dtype;
   if (sdt != TCP_F32 && sdt != TCP_F16 && sdt != TCP_BF16 && sdt != TCP_F16X2)
-    sdt = vdt != TCP_F32 ? vdt : (nd % 8 == 0 && !frec ? TCP_F16X2 : TCP_F32);
-  if (frec && sdt == TCP_F16X2) return fail(TCP_ERR_DTYPE, "fbp: FourierRec takes F32, F16 or BF16 sinograms");
+    sdt = vdt != TCP_F32 ? vdt : (nd % 8 == 0 && !frec && !lprec ? TCP_F16X2 : TCP_F32);
+  if ((frec || lprec) && sdt == TCP_F16X2)
+    return fail(TCP_ERR_DTYPE, "fbp: FourierRec and LpRec take F32, F16 or BF16 sinograms");
   const int frec_width = o.width == 0 ? fourierrec_default_width(vdt, n) : o.width;
   if (frec) {
     tcp_status sf = fourierrec_check(nt, nd, n, frec_width);
@@ -178,11 +181,13 @@ tcp_status fbp_resolve_shape(int64_t nt, int64_t nz, int64_t nd, int64_t n, int 
   p->vdt = vdt;
   p->sdt = sdt;
   p->frec = frec;
+  p->lprec = lprec;
   p->width = frec_width;
+  p->os = lprec ? (o.width > 0 ? (double)o.width : 2.0) : 2.0;
   // default chunk: 256 slices for 16-bit sinograms (the tensor-core
   // backprojector's N), 32 for FP32 sinograms (the CUDA-core kernel), 64 for
   // FourierRec (32 slice pairs)
-  p->chunk = o.chunk_nz > 0 ? o.chunk_nz : frec ? 64 : (sdt == TCP_F32 ? 32 : 256);
+  p->chunk = o.chunk_nz > 0 ? o.chunk_nz : lprec ? 16 : frec ? 64 : (sdt == TCP_F32 ? 32 : 256);
   p->cz = std::max<int64_t>(1, std::min(p->chunk, nz));
   p->B = o.n_buffers == 3 ? 3 : 2;
   p->filter = o.filter;
@@ -257,6 +262,8 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
     }
     if (p.frec)
       TRY_S(launch_fourierrec_ws(sv, r.frt, r.fws, r.trig, 0.5 * (double)nd, vv, p.bp_scale, p.width, st));
+    else if (p.lprec)
+      TRY_S(launch_lprec_ws(sv, *r.lpg, r.lpd, r.lpws, r.lpz, vv, p.bp_scale, st));
     else
       TRY_S(launch_backproject(sv, r.trig, 0.5 * (double)nd, vv, p.cfg, st, p.bp_scale));
     if (host_vol) {
@@ -334,6 +341,14 @@ extern "C" tcp_status tcp_fbp(const tcp_tensor* raw, const tcp_tensor* dark, con
     void* ws = nullptr;
     if ((s = sc.alloc(&ws, fourierrec_workspace_bytes(nt, nd, n, p.cz, nullptr))) != TCP_OK) return s;
     r.fws = fourierrec_workspace(ws, nt, nd, n, p.cz);
+  }
+  if (p.lprec) {  // the filter moved the axis to ndet/2
+    const LpDevGeom* d = nullptr;
+    if ((s = lprec_cached(theta, nt, nd, n, 0.5 * (double)nd, p.os, &r.lpg, &d)) != TCP_OK) return s;
+    if ((s = lprec_check(*r.lpg)) != TCP_OK) return s;
+    r.lpd = *d;
+    r.lpz = lprec_slices_per_pass(*r.lpg, p.cz);
+    if ((s = sc.alloc(&r.lpws, lprec_workspace_bytes(*r.lpg, r.lpz))) != TCP_OK) return s;
   }
   View3 dm, fm;
   if ((s = device_means(dark, nz, nd, sc, &dm)) != TCP_OK) return s;

@@ -25,7 +25,8 @@ struct tcp_plan {
   float* means = nullptr;       // [2][nz][ndet] FP32: dark, then flat
   void* frames = nullptr;       // staging of host U16 frames: host_frames x nz x ndet
   void* proj_orig = nullptr;    // projector tile origins
-  void* frec_ws = nullptr;      // FourierRec workspace (also for tcp_fourierrec_plan)
+  void* frec_ws = nullptr;      // FourierRec workspace
+  tcp::LpHostGeom lpg;          // LpRec geometry (host copy; its tables are in `owned`)
   size_t bytes = 0;
   ~tcp_plan() {
     for (void* q : owned) cudaFree(q);
@@ -83,6 +84,14 @@ tcp_status plan_build(tcp_plan* pl, const double* theta) {
     PTRY(fourierrec_tables_owned(theta, nt, nd, n, p.width, &pl->owned, &r.frt));
     PTRY(plan_alloc(pl, &pl->frec_ws, fourierrec_workspace_bytes(nt, nd, n, p.cz, nullptr)));
     r.fws = fourierrec_workspace(pl->frec_ws, nt, nd, n, p.cz);
+  }
+  if (p.lprec) {  // the filter moves the axis to ndet/2
+    PTRY(lprec_geometry(theta, nt, nd, n, 0.5 * (double)nd, p.os, &pl->lpg));
+    PTRY(lprec_check(pl->lpg));
+    PTRY(lprec_upload(pl->lpg, &pl->owned, &r.lpd, nullptr, false));
+    r.lpg = &pl->lpg;
+    r.lpz = lprec_slices_per_pass(pl->lpg, p.cz);
+    PTRY(plan_alloc(pl, &r.lpws, lprec_workspace_bytes(pl->lpg, r.lpz)));
   }
   // buffers
   void* m = nullptr;

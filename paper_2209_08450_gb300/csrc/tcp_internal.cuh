@@ -237,6 +237,38 @@ tcp_status bp_persistent_grid(int sdt, int vdt, const tcp_bp_config& cfg, int* b
 tcp_status launch_backproject_persistent(const BpWork& w, int sdt, int vdt, const tcp_bp_config& cfg, int blocks,
                                          cudaStream_t st);
 
+// LpRec (k_lprec.cu): host geometry of the three angle spans (FP64), its
+// device tables, the workspace of one call and the launcher.
+struct LpHostSpan {
+  int j0 = 0, nu = 0, p = 1, nrho = 0, npsi = 0, kpsi = 0, ext = 0, ntau = 0;
+  double phi = 0, ox = 0, oy = 0, rho0 = 0, tau0 = 0, drho = 0, dpsi = 0, psi0 = 0;
+  std::vector<int2> esplit, shsplit;  // (floor, FP32 fraction bits)
+  std::vector<int> dbase;
+  std::vector<float4> dw;
+};
+struct LpHostGeom {
+  int64_t nt = 0, nd = 0, n = 0;
+  double os = 2.0;
+  LpHostSpan span[3];
+};
+struct LpDevGeom {
+  const int2* esplit[3] = {};
+  const int2* shsplit[3] = {};
+  const int* dbase[3] = {};
+  const float4* dw[3] = {};
+};
+tcp_status lprec_geometry(const double* theta, int64_t nt, int64_t nd, int64_t n, double center, double os,
+                          LpHostGeom* g);
+tcp_status lprec_check(const LpHostGeom& g);
+int lprec_slices_per_pass(const LpHostGeom& g, int64_t nz);
+size_t lprec_workspace_bytes(const LpHostGeom& g, int zpass);
+tcp_status lprec_upload(const LpHostGeom& g, std::vector<void*>* owned, LpDevGeom* d, cudaStream_t st, bool async);
+tcp_status lprec_cached(const double* theta, int64_t nt, int64_t nd, int64_t n, double center, double os,
+                        const LpHostGeom** g, const LpDevGeom** d);
+void lprec_cache_clear();
+tcp_status launch_lprec_ws(const View3& sv, const LpHostGeom& g, const LpDevGeom& d, void* ws, int zpass,
+                           const View3& vv, float scale, cudaStream_t st);
+
 // ------------------------------------------------ chunked FBP (pipeline.cu) --
 
 // Resolved options of one chunked FBP.
@@ -244,7 +276,9 @@ struct FbpParams {
   int64_t nt = 0, nz = 0, nd = 0, n = 0;
   int vdt = TCP_F32, sdt = TCP_F32;
   bool frec = false;
-  int width = 0;
+  bool lprec = false;
+  int width = 0;       // FourierRec window width
+  double os = 2.0;     // LpRec oversampling
   int64_t chunk = 0, cz = 0;  // requested chunk depth, and the deepest chunk of this run
   int B = 2;                  // ring depth for host buffers
   int filter = 0, pad = 0;
@@ -259,6 +293,10 @@ struct FbpRes {
   FilterTable ft;
   FrecTables frt;
   FrecWorkspace fws;
+  const LpHostGeom* lpg = nullptr;  // LpRec geometry (host copy) and its tables
+  LpDevGeom lpd;
+  void* lpws = nullptr;             // LpRec workspace for passes of lpz slices
+  int lpz = 1;
   void* sino = nullptr;  // chunk sinogram buffer
   int64_t sino_cz = 0;   // slices it holds (F16X2: the distance between the planes)
   void* rring[3] = {nullptr, nullptr, nullptr};

@@ -257,3 +257,30 @@ def test_plan_create_validates_its_arguments(lib):
     assert lib.tcp_project_plan(None, ctypes.byref(t), 16.0, ctypes.byref(t), None) == 1
     assert lib.tcp_plan_info(None, None, None) == 1
     assert lib.tcp_plan_destroy(None) == 0
+
+
+def test_lprec_argument_checks(lib):
+    # host-side checks of tcp_lprec, made before any device work
+    sino = _t(_lib.F32, (2, 6, 16))
+    vol = _t(_lib.F32, (2, 16, 16), ptr=1 << 20)
+    eq = (ctypes.c_double * 6)(*[i * 3.141592653589793 / 6 for i in range(6)])
+    uneq = (ctypes.c_double * 6)(*[i * 3.141592653589793 / 6 + (0.01 if i == 2 else 0) for i in range(6)])
+    full = (ctypes.c_double * 6)(*[i * 2 * 3.141592653589793 / 6 for i in range(6)])
+    assert lib.tcp_lprec(ctypes.byref(sino), uneq, 8.0, ctypes.byref(vol), 1.0, 2.0, None) == 1
+    assert b"equally spaced" in lib.tcp_last_error()
+    assert lib.tcp_lprec(ctypes.byref(sino), full, 8.0, ctypes.byref(vol), 1.0, 2.0, None) == 1
+    assert b"half turn" in lib.tcp_last_error()
+    assert lib.tcp_lprec(ctypes.byref(sino), eq, 8.0, ctypes.byref(vol), 1.0, 40.0, None) == 1  # oversampling
+    two = _t(_lib.F32, (2, 2, 16))
+    assert lib.tcp_lprec(ctypes.byref(two), eq, 8.0, ctypes.byref(vol), 1.0, 2.0, None) == 2
+    pair = _t(_lib.F16X2, (2, 2, 6, 16))
+    assert lib.tcp_lprec(ctypes.byref(pair), eq, 8.0, ctypes.byref(vol), 1.0, 2.0, None) == 3
+    assert lib.tcp_lprec(ctypes.byref(sino), eq, float("nan"), ctypes.byref(vol), 1.0, 2.0, None) == 1
+    # tcp_fbp: LpRec oversampling outside 1..8
+    raw = _t(_lib.U16, (6, 2, 16), ptr=1 << 22)
+    dark = _t(_lib.F32, (2, 16), ptr=1 << 23)
+    o = _lib.FbpOpts()
+    o.algorithm = _lib.ALGORITHMS["lprec"]
+    o.width = 9
+    assert lib.tcp_fbp(ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(dark), eq, 8.0, ctypes.byref(vol),
+                       ctypes.byref(o), None) == 1
