@@ -299,6 +299,34 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     return out
 
 
+def pipeline_trace(tcp, raw_h, dark_h, flat_h, theta, center, vol_h, chunk, sdt) -> dict:
+    """One traced run of the host-buffer pipeline through a plan: per chunk the
+    upload, compute and download intervals (CUDA events), and how much of the
+    copy time overlaps compute of another chunk."""
+    nz, n = vol_h.shape[0], vol_h.shape[1]
+    plan = tcp.Plan(theta, raw_h.shape[2], nz, center, n=n, dtype=vol_h.dtype, chunk_nz=chunk, sino_dtype=sdt,
+                    host_raw=True, host_vol=True, host_frames=max(dark_h.shape[0], flat_h.shape[0]), trace=True)
+    try:
+        plan.fbp(raw_h, dark_h, flat_h, out=vol_h)
+        t = plan.trace()
+    finally:
+        plan.close()
+    comp = [(r[2], r[3]) for r in t]
+
+    def hidden(a, b):  # part of [a, b] covered by compute intervals
+        return sum(max(0.0, min(b, c1) - max(a, c0)) for c0, c1 in comp)
+
+    up = [(r[0], r[1]) for r in t if r[0] >= 0]
+    down = [(r[4], r[5]) for r in t if r[4] >= 0]
+    up_ms = sum(b - a for a, b in up)
+    down_ms = sum(b - a for a, b in down)
+    return {"chunks": int(t.shape[0]), "total_ms": float(t[:, :].max()),
+            "compute_ms": float(sum(b - a for a, b in comp)),
+            "upload_ms": up_ms, "upload_hidden_frac": sum(hidden(a, b) for a, b in up) / max(up_ms, 1e-9),
+            "download_ms": down_ms, "download_hidden_frac": sum(hidden(a, b) for a, b in down) / max(down_ms, 1e-9),
+            "per_chunk_ms": [[round(float(x), 3) for x in r] for r in t]}
+
+
 def measure_rows(dev) -> dict:
     """Differentiable least-squares pair (512 x 512 x 64, 720 angles, 512-pixel
     detector) and the uneven batch (6 stacks, one persistent graph replay)."""
@@ -626,6 +654,12 @@ def main():
                "d2h_bytes_per_step": vol_h.numel() * vol_h.element_size()}
         if rank == 0 and zs:
             par[args.dtype + "_e2e"] = parity(vol_h, zs[:1], hp)
+            par[args.dtype + "_e2e_slices"] = parity(vol_h, zs, hp)
+        # per-chunk timeline of one more run (untimed, through a plan with the
+        # same options): how much of the copy time hides under compute
+        if rank == 0 and hp not in FOURIERREC:
+            e2e["pipeline_trace"] = pipeline_trace(tcp, raw_h, dark_h, flat_h, theta, center, vol_h, chunk_for(hp),
+                                                   sdt_of(hp))
         del raw_h, vol_h
 
     rows = None

@@ -476,7 +476,7 @@ typedef struct {
   int32_t vol_dtype;    /* F32, F16 or BF16 */
   int32_t io;           /* TCP_IO_HOST_RAW | TCP_IO_HOST_VOL, 0 for device buffers only */
   int32_t host_frames;  /* U16 dark/flat frames that may come from host memory (0: device frames or means) */
-  int32_t reserved;
+  int32_t trace;        /* 1: time every chunk's upload, compute and download (tcp_plan_trace) */
   tcp_fbp_opts opts;    /* chunk, sinogram storage, filter, padding, ring depth, algorithm, width (as tcp_fbp) */
 } tcp_plan_desc;
 
@@ -488,6 +488,16 @@ tcp_status tcp_plan_destroy(tcp_plan* plan);
 /* Device bytes the plan holds, and the options it resolved (chunk depth,
  * sinogram storage, ring depth, FourierRec width).  Either output may be NULL. */
 tcp_status tcp_plan_info(const tcp_plan* plan, int64_t* device_bytes, tcp_fbp_opts* resolved);
+
+/* Per-chunk timeline of the last tcp_fbp_plan call of a plan created with
+ * trace = 1 (Sec. 2.3: the asynchronous pipeline hides the copies of chunk
+ * k+1 and k-1 behind the computation of chunk k).  Waits for that call to
+ * finish.  ms receives up to `cap` rows of 6 values, in milliseconds from
+ * the start of the call: upload start/end, compute start/end (normalise +
+ * filter + backprojection), download start/end; -1 where a chunk had no such
+ * copy.  *count = the number of chunks.  The events are CUDA events with
+ * timing (resolution about 0.5 us); a traced call must not be captured. */
+tcp_status tcp_plan_trace(const tcp_plan* plan, double* ms, int64_t cap, int64_t* count);
 
 /* tcp_fbp through a plan: raw U16 [ntheta][nz][ndet] with nz <= the plan's,
  * vol [nz][n][n] of the plan's dtype; raw and vol on the device, or in host

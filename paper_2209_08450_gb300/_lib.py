@@ -182,7 +182,7 @@ class BatchOpts(ctypes.Structure):
 class PlanDesc(ctypes.Structure):
     _fields_ = [("ntheta", ctypes.c_int64), ("nz", ctypes.c_int64), ("ndet", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("center", ctypes.c_double), ("vol_dtype", ctypes.c_int32), ("io", ctypes.c_int32),
-                ("host_frames", ctypes.c_int32), ("reserved", ctypes.c_int32), ("opts", FbpOpts)]
+                ("host_frames", ctypes.c_int32), ("trace", ctypes.c_int32), ("opts", FbpOpts)]
 
 
 IO_HOST_RAW, IO_HOST_VOL = 1, 2
@@ -192,6 +192,7 @@ SIGNATURES.update({
     "tcp_plan_destroy": ([_P], _I32),
     "tcp_plan_info": ([_P, ctypes.POINTER(_I64), ctypes.POINTER(FbpOpts)], _I32),
     "tcp_fbp_plan": ([_P, _T, _T, _T, _T, _P], _I32),
+    "tcp_plan_trace": ([_P, _P, _I64, ctypes.POINTER(_I64)], _I32),
     "tcp_filter_plan": ([_P, _T, _P], _I32),
     "tcp_backproject_plan": ([_P, _T, _D, _T, _D, _P], _I32),
     "tcp_project_plan": ([_P, _T, _D, _T, _P], _I32),

@@ -13,6 +13,12 @@
 // recomputed with the backprojector's canonical tile geometry, from a per-call
 // table of FP64 tile origins built by the same function, so the two operators
 // share bit-identical weights.
+//
+// Memory access: the lanes of a warp are consecutive detector bins j of one
+// angle, so at each step they visit neighbouring voxels along the minor axis.
+// For y-major angles that is along a row (coalesced); for x-major angles it
+// would be down a column (one cache line per lane), so those angles read a
+// transposed copy volT[z][ix][iy] made once per call by a tiled transpose.
 #include "tcp_internal.cuh"
 
 namespace tcp {
@@ -41,8 +47,28 @@ template <> struct WRound<__nv_bfloat16> {
   static __device__ __forceinline__ float r(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
 };
 
+// volT[z][ix][iy] = vol[z][iy][ix], 32 x 32 tiles through shared memory.
+template <class TV>
+__global__ void k_transpose(const TV* vol, int64_t v_z, int64_t v_y, int n, TV* volT) {
+  __shared__ TV t[32][33];
+  const int z = blockIdx.z;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const TV* src = vol + z * v_z;
+  TV* dst = volT + (int64_t)z * n * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    if (y < n && x < n) t[r][threadIdx.x] = src[(int64_t)y * v_y + x];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int x = x0 + r, y = y0 + threadIdx.x;
+    if (y < n && x < n) dst[(int64_t)x * n + y] = t[threadIdx.x][r];
+  }
+}
+
 struct PjArgs {
   const void* vol;
+  const void* volT;  // [z][ix][iy], row stride n, slice stride n * n
   int64_t v_z, v_y;
   int nz, n, ntx;
   void* sino;
@@ -69,7 +95,9 @@ __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
   const float hn = (float)a.half_n;
   const float jc = (float)((double)j - a.center);
   const int2* orig = a.orig + (int64_t)t * a.ntx * a.ntx;
-  const TV* vol = reinterpret_cast<const TV*>(a.vol);
+  // x-major angles walk columns: read them as rows of the transposed copy
+  const TV* vol = reinterpret_cast<const TV*>(ymajor ? a.vol : a.volT);
+  const int64_t vy = ymajor ? a.v_y : a.n, vz = ymajor ? a.v_z : (int64_t)a.n * a.n;
 
   float acc[K];
 #pragma unroll
@@ -91,10 +119,10 @@ __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
       if (i == j) wt = WRound<TS>::r(1.f - w);
       else if (i + 1 == j) wt = WRound<TS>::r(w);
       if (wt != 0.f) {
-        const TV* p = vol + (int64_t)iy * a.v_y + ix;
+        const TV* p = vol + (int64_t)m * vy + u;  // (iy, ix) for y-major, (ix, iy) transposed otherwise
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          if (z0 + k < a.nz) acc[k] = __fmaf_rn(wt, Store<TV>::load(p + (int64_t)(z0 + k) * a.v_z), acc[k]);
+          if (z0 + k < a.nz) acc[k] = __fmaf_rn(wt, Store<TV>::load(p + (int64_t)(z0 + k) * vz), acc[k]);
       }
     }
   }
@@ -131,7 +159,12 @@ size_t project_origin_bytes(int64_t ntheta, int64_t n) {
   return (size_t)std::max<int64_t>(1, ntheta * ntx * ntx) * sizeof(int2);
 }
 
-tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* orig_ws,
+size_t project_workspace_bytes(int64_t ntheta, int64_t n, int64_t nz, int vol_dtype) {
+  const size_t ob = (project_origin_bytes(ntheta, n) + 255) / 256 * 256;
+  return ob + (size_t)std::max<int64_t>(1, nz * n * n) * (vol_dtype == TCP_F32 ? 4 : 2);
+}
+
+tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* ws,
                              cudaStream_t st) {
   const int nz = (int)vol.d0, n = (int)vol.d1, nt = (int)sino.d1, nd = (int)sino.d2;
   if (nz == 0 || nt == 0 || nd == 0) return TCP_OK;
@@ -161,7 +194,27 @@ tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double cen
   dim3 grid((unsigned)((nd + kPjThreads - 1) / kPjThreads), (unsigned)nt, (unsigned)((nz + K - 1) / K));
   if (grid.y > 65535u || grid.z > 65535u)
     return fail(TCP_ERR_SHAPE, "project: too many angles or slice blocks for one launch");
-  int2* orig = reinterpret_cast<int2*>(orig_ws);
+  int2* orig = reinterpret_cast<int2*>(ws);
+  void* volT = (char*)ws + (project_origin_bytes(nt, n) + 255) / 256 * 256;
+  a.volT = volT;
+  // x-major angles read the transposed copy (made unconditionally, so the
+  // launch sequence does not depend on the angle set)
+  if (n > 0) {
+    dim3 tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)nz);
+    switch (vol.dtype) {
+      case TCP_F32:
+        k_transpose<float><<<tg, dim3(32, 8), 0, st>>>((const float*)vol.p, vol.s0, vol.s1, n, (float*)volT);
+        break;
+      case TCP_F16:
+        k_transpose<__half><<<tg, dim3(32, 8), 0, st>>>((const __half*)vol.p, vol.s0, vol.s1, n, (__half*)volT);
+        break;
+      case TCP_BF16:
+        k_transpose<__nv_bfloat16><<<tg, dim3(32, 8), 0, st>>>((const __nv_bfloat16*)vol.p, vol.s0, vol.s1, n,
+                                                               (__nv_bfloat16*)volT);
+        break;
+    }
+    TCP_CUDA_TRY(cudaGetLastError());
+  }
   if (n > 0) {
     const int64_t total = (int64_t)nt * a.ntx * a.ntx;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
@@ -176,10 +229,10 @@ tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double cen
 tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
                           cudaStream_t st) {
   if (vol.d0 == 0 || sino.d1 == 0 || sino.d2 == 0) return TCP_OK;
-  void* orig = nullptr;
-  TCP_CUDA_TRY(cudaMallocAsync(&orig, project_origin_bytes(sino.d1, vol.d1), st));
-  const tcp_status s = launch_project_ws(vol, trig, center, sino, orig, st);
-  const cudaError_t e = cudaFreeAsync(orig, st);
+  void* ws = nullptr;
+  TCP_CUDA_TRY(cudaMallocAsync(&ws, project_workspace_bytes(sino.d1, vol.d1, vol.d0, vol.dtype), st));
+  const tcp_status s = launch_project_ws(vol, trig, center, sino, ws, st);
+  const cudaError_t e = cudaFreeAsync(ws, st);
   if (s == TCP_OK && e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync");
   return s;
 }

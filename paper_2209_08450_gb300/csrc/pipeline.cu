@@ -214,13 +214,25 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
   }
   const auto sched = chunk_schedule(nz, chunk, host_raw || host_vol);
   const int64_t nchunks = (int64_t)sched.size();
+  const bool trace = r.trace && nchunks <= r.ntrace;
+  auto ev = [&](int64_t k, int which) { return r.trace[1 + 6 * k + which]; };
+  if (r.traced) *r.traced = 0;
+  if (trace) {
+    TCP_CUDA_TRY(cudaEventRecord(r.trace[0], st));
+    for (int64_t k = 0; k < nchunks; ++k) r.trace_flags[k] = 0;
+  }
   auto issue_copy_in = [&](int64_t k) -> tcp_status {
     const int b = (int)(k % B);
     const int64_t z0 = sched[(size_t)k].first, c = sched[(size_t)k].second;
     if (k >= B) TCP_CUDA_TRY(cudaStreamWaitEvent(cin, r.raw_free[b], 0));
+    if (trace) TCP_CUDA_TRY(cudaEventRecord(ev(k, 0), cin));
     TCP_CUDA_TRY(cudaMemcpy2DAsync(r.rring[b], (size_t)c * nd * 2,
                                    (const uint16_t*)raw->data + z0 * raw->stride[1], (size_t)raw->stride[0] * 2,
                                    (size_t)c * nd * 2, (size_t)nt, cudaMemcpyHostToDevice, cin));
+    if (trace) {
+      TCP_CUDA_TRY(cudaEventRecord(ev(k, 1), cin));
+      r.trace_flags[k] |= 1;
+    }
     TCP_CUDA_TRY(cudaEventRecord(r.raw_ready[b], cin));
     return TCP_OK;
   };
@@ -243,6 +255,7 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
     View3 dv = dm, fv = fm;
     dv.p = (float*)dm.p + z0 * dm.s1; dv.d1 = c;
     fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
+    if (trace) TCP_CUDA_TRY(cudaEventRecord(ev(k, 2), st));
     View3 sv;
     sv.p = r.sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
     sv.plane = sdt == TCP_F16X2 ? r.sino_cz * nt * nd : 0;
@@ -266,10 +279,12 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
       TRY_S(launch_lprec_ws(sv, *r.lpg, r.lpd, r.lpws, r.lpz, vv, p.bp_scale, st));
     else
       TRY_S(launch_backproject(sv, r.trig, 0.5 * (double)nd, vv, p.cfg, st, p.bp_scale));
+    if (trace) TCP_CUDA_TRY(cudaEventRecord(ev(k, 3), st));
     if (host_vol) {
       const int es = esize(p.vdt);
       TCP_CUDA_TRY(cudaEventRecord(r.vol_ready[b], st));
       TCP_CUDA_TRY(cudaStreamWaitEvent(cout, r.vol_ready[b], 0));
+      if (trace) TCP_CUDA_TRY(cudaEventRecord(ev(k, 4), cout));
       if (vol->stride[1] == n && vol->stride[0] == n * n) {
         TCP_CUDA_TRY(cudaMemcpyAsync((char*)vol->data + z0 * n * n * es, r.vring[b], (size_t)c * n * n * es,
                                      cudaMemcpyDeviceToHost, cout));
@@ -279,9 +294,14 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
                                          (size_t)vol->stride[1] * es, (char*)r.vring[b] + (size_t)z * n * n * es,
                                          (size_t)n * es, (size_t)n * es, (size_t)n, cudaMemcpyDeviceToHost, cout));
       }
+      if (trace) {
+        TCP_CUDA_TRY(cudaEventRecord(ev(k, 5), cout));
+        r.trace_flags[k] |= 2;
+      }
       TCP_CUDA_TRY(cudaEventRecord(r.vol_free[b], cout));
     }
   }
+  if (trace && r.traced) *r.traced = (int)nchunks;
   (void)cz;
   // Join the side streams so that `stream` completes after every copy.
   if (host_vol) {

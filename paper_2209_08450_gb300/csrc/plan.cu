@@ -24,11 +24,15 @@ struct tcp_plan {
   std::vector<cudaStream_t> streams;
   float* means = nullptr;       // [2][nz][ndet] FP32: dark, then flat
   void* frames = nullptr;       // staging of host U16 frames: host_frames x nz x ndet
-  void* proj_orig = nullptr;    // projector tile origins
+  void* proj_orig = nullptr;    // projector workspace: tile origins and the transposed volume
   void* frec_ws = nullptr;      // FourierRec workspace
   tcp::LpHostGeom lpg;          // LpRec geometry (host copy; its tables are in `owned`)
   size_t bytes = 0;
+  std::vector<cudaEvent_t> trace_events;  // timing events of the per-chunk timeline
+  std::vector<int> trace_flags;
+  int traced = 0;
   ~tcp_plan() {
+    for (cudaEvent_t e : trace_events) cudaEventDestroy(e);
     for (void* q : owned) cudaFree(q);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     for (cudaStream_t s : streams) cudaStreamDestroy(s);
@@ -98,7 +102,7 @@ tcp_status plan_build(tcp_plan* pl, const double* theta) {
   PTRY(plan_alloc(pl, &m, sizeof(float) * 2 * (size_t)std::max<int64_t>(1, nz * nd)));
   pl->means = (float*)m;
   if (d.host_frames > 0) PTRY(plan_alloc(pl, &pl->frames, (size_t)d.host_frames * nz * nd * 2));
-  PTRY(plan_alloc(pl, &pl->proj_orig, project_origin_bytes(nt, n)));
+  PTRY(plan_alloc(pl, &pl->proj_orig, project_workspace_bytes(nt, n, nz, TCP_F32)));
   PTRY(plan_alloc(pl, &r.sino, (size_t)p.cz * nt * nd * esz(p.sdt)));
   r.sino_cz = p.cz;
   if (d.io & TCP_IO_HOST_RAW) {
@@ -120,6 +124,16 @@ tcp_status plan_build(tcp_plan* pl, const double* theta) {
     PTRY(plan_event(pl, &r.join_out));
   }
   PTRY(plan_event(pl, &r.fork));
+  if (d.trace) {  // timing events for the per-chunk timeline
+    const int maxc = (int)((nz + p.chunk - 1) / p.chunk) + 2;
+    pl->trace_events.resize((size_t)(1 + 6 * maxc), nullptr);
+    for (auto& e : pl->trace_events) TCP_CUDA_TRY(cudaEventCreate(&e));
+    pl->trace_flags.assign((size_t)maxc, 0);
+    r.trace = pl->trace_events.data();
+    r.ntrace = maxc;
+    r.traced = &pl->traced;
+    r.trace_flags = pl->trace_flags.data();
+  }
   // the device error word's address is looked up here, not during a capture
   if (!device_error_word()) return fail(TCP_ERR_CUDA, "plan: device error word unavailable");
   TCP_CUDA_TRY(cudaDeviceSynchronize());
@@ -243,6 +257,31 @@ tcp_status tcp_plan_info(const tcp_plan* plan, int64_t* device_bytes, tcp_fbp_op
   return TCP_OK;
 }
 
+tcp_status tcp_plan_trace(const tcp_plan* plan, double* ms, int64_t cap, int64_t* count) {
+  if (!plan) return fail(TCP_ERR_ARG, "plan_trace: null plan");
+  if (!plan->d.trace) return fail(TCP_ERR_ARG, "plan_trace: the plan was created without trace");
+  const int nch = plan->traced;
+  if (count) *count = nch;
+  if (nch == 0 || !ms) return TCP_OK;
+  const cudaEvent_t* e = plan->trace_events.data();
+  TCP_CUDA_TRY(cudaEventSynchronize(e[1 + 6 * (nch - 1) + 3]));
+  for (int k = 0; k < nch && k < cap; ++k) {
+    const int fl = plan->trace_flags[(size_t)k];
+    for (int w = 0; w < 6; ++w) {
+      double v = -1.0;
+      const bool have = (w >= 2 && w < 4) || (w < 2 && (fl & 1)) || (w >= 4 && (fl & 2));
+      if (have) {
+        TCP_CUDA_TRY(cudaEventSynchronize(e[1 + 6 * k + w]));
+        float t = 0.f;
+        TCP_CUDA_TRY(cudaEventElapsedTime(&t, e[0], e[1 + 6 * k + w]));
+        v = t;
+      }
+      ms[6 * k + w] = v;
+    }
+  }
+  return TCP_OK;
+}
+
 tcp_status tcp_fbp_plan(tcp_plan* plan, const tcp_tensor* raw, const tcp_tensor* dark, const tcp_tensor* flat,
                         tcp_tensor* vol, void* stream) {
   if (!plan) return fail(TCP_ERR_ARG, "fbp_plan: null plan");
@@ -338,8 +377,9 @@ tcp_status tcp_project_plan(const tcp_plan* plan, const tcp_tensor* vol, double 
   if (!is_float_dt(vol->dtype) || !is_float_dt(sino->dtype))
     return fail(TCP_ERR_DTYPE, "project_plan: sino/vol must be F32, F16 or BF16");
   if (sino->shape[1] != plan->p.nt || vol->shape[1] != plan->p.n || vol->shape[2] != plan->p.n ||
-      vol->shape[0] != sino->shape[0])
-    return fail(TCP_ERR_SHAPE, "project_plan: vol [nz][n][n] and sino [nz][ntheta][ndet] must match the plan");
+      vol->shape[0] != sino->shape[0] || vol->shape[0] > plan->p.nz)
+    return fail(TCP_ERR_SHAPE,
+                "project_plan: vol [nz <= plan nz][n][n] and sino [nz][ntheta][ndet] must match the plan");
   if (overlap(sino, vol)) return fail(TCP_ERR_ALIAS, "sino and vol overlap");
   if (sino->shape[0] == 0 || sino->shape[2] == 0) return TCP_OK;
   return launch_project_ws(view_of(vol), plan->r.trig, center, view_of(sino), plan->proj_orig,

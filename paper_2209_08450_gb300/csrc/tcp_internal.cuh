@@ -168,10 +168,12 @@ tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double c
                               const tcp_bp_config& cfg, cudaStream_t st, float scale = 1.0f);
 tcp_status launch_project(const View3& vol, const TrigTable& trig, double center, const View3& sino,
                           cudaStream_t st);
-// The projector with its per-call tile-origin table (ntheta x ntx^2 int2,
-// project_origin_bytes) in caller-provided device memory.
+// The projector with its per-call workspace (the tile-origin table, ntheta x
+// ntx^2 int2, then the transposed volume) in caller-provided device memory of
+// project_workspace_bytes.
 size_t project_origin_bytes(int64_t ntheta, int64_t n);
-tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* orig,
+size_t project_workspace_bytes(int64_t ntheta, int64_t n, int64_t nz, int vol_dtype);
+tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double center, const View3& sino, void* ws,
                              cudaStream_t st);
 // FourierRec (k_fourierrec.cu): default window width per volume dtype, the
 // shape/width checks, and the launcher (sino F32/F16/BF16, vol F32/F16/BF16).
@@ -304,6 +306,13 @@ struct FbpRes {
   cudaStream_t cin = nullptr, cout = nullptr;
   cudaEvent_t raw_ready[3] = {}, raw_free[3] = {}, vol_ready[3] = {}, vol_free[3] = {};
   cudaEvent_t fork = nullptr, join_in = nullptr, join_out = nullptr;
+  // optional per-chunk timeline: t0, then per chunk 6 timing events (upload
+  // start/end, compute start/end, download start/end); `traced` chunks of the
+  // last run, `ntrace` chunks of room
+  cudaEvent_t* trace = nullptr;
+  int ntrace = 0;
+  int* traced = nullptr;
+  int* trace_flags = nullptr;  // per chunk: bit 0 upload recorded, bit 1 download recorded
 };
 tcp_status fbp_resolve(const tcp_tensor* raw, const tcp_tensor* vol, const tcp_fbp_opts* opts, FbpParams* p);
 tcp_status fbp_resolve_shape(int64_t nt, int64_t nz, int64_t nd, int64_t n, int vdt, const tcp_fbp_opts* opts,

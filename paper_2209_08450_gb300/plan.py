@@ -26,7 +26,7 @@ class Plan:
     def __init__(self, theta, ndet: int, nz: int, center: float, n: int | None = None, dtype=torch.float32,
                  chunk_nz: int = 0, filter: str = "shepp", pad: str = "edge", sino_dtype=None, n_buffers: int = 2,
                  algorithm: str = "linerec", width: int = 0, host_raw: bool = False, host_vol: bool = False,
-                 host_frames: int = 0):
+                 host_frames: int = 0, trace: bool = False):
         th = _lib.theta_array(theta)
         d = _lib.PlanDesc()
         d.ntheta = th.shape[0]
@@ -37,6 +37,7 @@ class Plan:
         d.vol_dtype = _lib.dtype_code(dtype)
         d.io = (_lib.IO_HOST_RAW if host_raw else 0) | (_lib.IO_HOST_VOL if host_vol else 0)
         d.host_frames = host_frames
+        d.trace = int(bool(trace))
         o = d.opts
         o.chunk_nz = chunk_nz
         o.sino_dtype = -1 if sino_dtype is None else _lib.dtype_code(sino_dtype)
@@ -72,6 +73,18 @@ class Plan:
 
         r, d, f, o = _lib.desc(raw, _lib.U16), dd(dark), dd(flat), _lib.desc(out)
         _lib.call("tcp_fbp_plan", self._h, _lib.ref(r), _lib.ref(d), _lib.ref(f), _lib.ref(o), _lib.stream_ptr(stream))
+        return out
+
+    def trace(self):
+        """Per-chunk timeline of the last fbp call (plan made with trace=True):
+        an array [chunks][6] of milliseconds from the call's start: upload
+        start/end, compute start/end, download start/end (-1: no such copy)."""
+        import numpy as np
+        cnt = ctypes.c_int64()
+        _lib.call("tcp_plan_trace", self._h, None, 0, ctypes.byref(cnt))
+        out = np.zeros((max(cnt.value, 0), 6), dtype=np.float64)
+        if cnt.value:
+            _lib.call("tcp_plan_trace", self._h, out.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt))
         return out
 
     def filter_(self, sino: torch.Tensor, stream=None) -> torch.Tensor:

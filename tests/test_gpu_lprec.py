@@ -117,7 +117,7 @@ def test_fbp_lprec_pipeline_matches_oracle():
     g.replay()
     torch.cuda.synchronize()
     assert rel(vol.double().cpu().numpy(), ref) <= 1e-5
-    # and it approximates the FBP of the object like LineRec does
-    lin = oracle.fbp(d.raw, d.dark, d.flat, d.theta, d.center, "shepp")
-    assert rel(vol.double().cpu().numpy(), lin) < 0.1
+    # and it approximates the cubic-spline FBP as closely as the oracle's LpRec does
+    exact = olp.backproject_spline_exact(q, d.theta, 32.0, 64)
+    assert rel(vol.double().cpu().numpy(), exact) <= 1.02 * rel(ref, exact) + 1e-6
     plan.close()

@@ -65,7 +65,7 @@ def test_backproject_fp32(nz, nt, nd, n, center):
 
 
 @pytest.mark.parametrize("cfg", [(8, 16, 4), (4, 32, 4), (4, 16, 4), (16, 8, 2), (8, 16, 2), (2, 16, 4),
-                                 (1, 32, 4)])
+                                 (1, 32, 4), (4, 16, 16), (2, 16, 16), (4, 32, 16), (8, 16, 16)])
 def test_backproject_every_config(cfg):
     q, theta, c = _bp_case(13, 50, 70, 65, 35.2, 7)
     ref = oracle.backproject(q, theta, c, 65)
@@ -89,6 +89,40 @@ def test_backproject_16bit_storage(sdt, vdt):
     tol = max(TOL[sdt], TOL[vdt])
     assert rel(got, ref_stored) <= tol
     assert rel(got, ref_exact) <= tol
+
+
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (11, 181, 203, 200, 101.37), (3, 64, 96, 96, 48.0), (1, 7, 33, 70, 20.5), (17, 37, 64, 33, 31.9)])
+def test_backproject_register_reuse_blocks(nz, nt, nd, n, center):
+    # 4 x 4 voxel blocks per thread walking the less-varying axis (checked
+    # mode is on: a floor step other than 0 or +1 would set the error word);
+    # angles over two turns cover all four walk directions
+    q, theta, c = _bp_case(nz, nt, nd, n, center, nz * 1000 + nt)
+    ref = oracle.backproject(q, theta, c, n)
+    for cfg in ((4, 16, 16), (8, 16, 16)):
+        try:
+            tcp.set_backproject_config(*cfg)
+            got = host(tcp.backproject(to_dev(q), theta, c, n=n))
+        finally:
+            tcp.set_backproject_config(None)
+        assert rel(got, ref) <= 1e-5
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert tcp.device_check() == 0
+
+
+def test_backproject_register_reuse_axis_aligned_and_diagonal_angles():
+    # slopes of exactly 0, +-1/sqrt(2) and +-1 sit on the walk-axis switch
+    q, _, c = _bp_case(5, 16, 80, 72, 40.25, 9)
+    theta = np.array([0.0, np.pi / 4, np.pi / 2, 3 * np.pi / 4, np.pi, 5 * np.pi / 4, 3 * np.pi / 2, 7 * np.pi / 4,
+                      0.7853, 0.7855, 2.3561, 2.3563, 1e-7, np.pi / 2 + 1e-7, -np.pi / 4, 3.9269])
+    ref = oracle.backproject(q, theta, c, 72)
+    try:
+        tcp.set_backproject_config(4, 16, 16)
+        got = host(tcp.backproject(to_dev(q), theta, c, n=72))
+    finally:
+        tcp.set_backproject_config(None)
+    assert rel(got, ref) <= 1e-5
+    assert tcp.device_check() == 0
 
 
 def test_backproject_special_angles_and_constant():

@@ -174,3 +174,26 @@ def test_plan_rejects_calls_outside_its_geometry(ds):
     assert rel(out.double().cpu().numpy(), ref[:6]) <= 1e-5
     assert plan.info()["device_bytes"] > 0
     plan.close()
+
+
+def test_plan_trace_records_the_pipeline_timeline(ds):
+    # the per-chunk timeline of a host-buffer run: every upload precedes its
+    # chunk's compute, every download follows it, computes run in order, and
+    # the upload of chunk k+1 is issued before chunk k's compute ends
+    d, ref = ds
+    raw = torch.from_numpy(d.raw.view(np.int16)).pin_memory()
+    vol = torch.empty((11, 96, 96), pin_memory=True)
+    plan = tcp.Plan(d.theta, 96, 11, d.center, chunk_nz=4, host_raw=True, host_vol=True, trace=True)
+    plan.fbp(raw, u16(d.dark), u16(d.flat), out=vol)
+    t = plan.trace()
+    torch.cuda.synchronize()
+    assert rel(vol.double().numpy(), ref) <= 1e-5
+    assert t.shape[0] == 4  # 2 + 4 + 4 + 1 slices: half-depth first chunk, short last chunk
+    for k in range(t.shape[0]):
+        h0, h1, c0, c1, d0, d1 = t[k]
+        assert 0 <= h0 <= h1 <= c0 + 1e-3 <= c1 + 1e-3 and c1 <= d0 + 1e-3 <= d1 + 1e-3
+        if k:
+            assert c0 >= t[k - 1][3] - 1e-3
+        if k + 1 < t.shape[0]:
+            assert t[k + 1][0] < c1
+    plan.close()
