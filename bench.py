@@ -327,6 +327,73 @@ def pipeline_trace(tcp, raw_h, dark_h, flat_h, theta, center, vol_h, chunk, sdt)
             "per_chunk_ms": [[round(float(x), 3) for x in r] for r in t]}
 
 
+def lprec_step2_fma(n: int, nt: int, os: float = 2.0) -> float:
+    """Multiply-adds of LpRec's span convolution (its dominant step) per slice:
+    4 per (log-polar grid point, angle of the span), three spans; grid sizes
+    as the library sets them (log-polar origin at 4 R, steps 1/os pixel at the
+    far radius, 12-point margins)."""
+    import math
+    R = n / math.sqrt(2.0) + 2.0
+    a = 4.0 * R
+    drho = 1.0 / (os * (a + R))
+    dth = math.pi / nt
+    p = math.ceil(os * (a + R) * dth)
+    dpsi = dth / p
+    nrho = math.ceil((math.log(a + R) - math.log(a - R)) / drho) + 25
+    npsi = 2 * math.ceil((math.asin(R / a) + 12 * dpsi) / dpsi) + 1
+    return 4.0 * nrho * npsi * nt
+
+
+def measure_lprec(tcp, raw, dark, flat, theta, center, n, nslices, steps=2) -> dict:
+    """LpRec FBP (oversampling 2) of `nslices` middle slices of the resident
+    stack (views, no copy): GVox/s, the span convolution's FMA rate against
+    the FP32 FMA ceiling, and the distance to the direct cubic-spline sums on
+    sampled voxels of one slice (the quantity LpRec approximates)."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle import lprec as olp
+    nz = raw.shape[1]
+    z0 = max(0, nz // 2 - nslices // 2)
+    z1 = min(nz, z0 + nslices)
+    r, d, f = raw[:, z0:z1], dark[:, z0:z1], flat[:, z0:z1]
+    vol = torch.empty((z1 - z0, n, n), dtype=torch.float32, device=raw.device)
+
+    def step():
+        tcp.fbp(r, d, f, theta, center, out=vol, algorithm="lprec")
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pk = _peaks()
+    sms = torch.cuda.get_device_properties(raw.device).multi_processor_count
+    fma_peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    fma = lprec_step2_fma(n, len(theta)) * (z1 - z0)
+    zc = (z1 - z0) // 2
+    rr = r[:, zc:zc + 1].cpu().numpy().view(np.uint16)
+    p = oracle.normalize(rr, oracle.frame_mean(d[:, zc:zc + 1].cpu().numpy().view(np.uint16)),
+                         oracle.frame_mean(f[:, zc:zc + 1].cpu().numpy().view(np.uint16)))
+    q = oracle.filter_sino(p, center, "shepp")[0]
+    rng = np.random.default_rng(2)
+    ix, iy = rng.integers(0, n, 200), rng.integers(0, n, 200)
+    ref = olp.backproject_spline_points(q, theta, n / 2.0, n, ix, iy)
+    got = vol[zc].double().cpu().numpy()[iy, ix]
+    return {"workload": "%d middle slices of the %d^3 workload, %d angles, LpRec FBP (oversampling 2), FP32"
+                        % (z1 - z0, n, len(theta)),
+            "ms_per_step": ms, "value": (z1 - z0) * n * n / (ms * 1e-3) / 1e9, "unit": "GVoxel/s",
+            "roofline": {"bound": "alu", "kernel": "k_lp_span (span convolution; whole call timed)",
+                         "achieved": fma / (ms * 1e-3) / 1e12, "peak": fma_peak / 1e12, "unit": "TFMA/s",
+                         "frac": fma / (ms * 1e-3) / fma_peak, "traffic": None,
+                         "peak_basis": "%d SMs x 128 FP32 lanes x max SM clock; 4 multiply-adds per (log-polar "
+                                       "grid point, angle)" % sms},
+            "rel_l2_vs_cubic_spline_sums": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+
+
 def measure_rows(dev) -> dict:
     """Differentiable least-squares pair (512 x 512 x 64, 720 angles, 512-pixel
     detector) and the uneven batch (6 stacks, one persistent graph replay)."""
@@ -443,6 +510,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-slices", type=int, default=16)
     ap.add_argument("--ref-slices", type=int, default=1)
+    ap.add_argument("--lprec-slices", type=int, default=32, help="slices of the LpRec variant (0: skip)")
     ap.add_argument("--parity-slices", type=int, default=2)
     ap.add_argument("--no-rows", action="store_true", help="skip the least-squares and batch rows")
     ap.add_argument("--split", default="replicas", choices=["replicas", "slab"],
@@ -661,6 +729,9 @@ def main():
             e2e["pipeline_trace"] = pipeline_trace(tcp, raw_h, dark_h, flat_h, theta, center, vol_h, chunk_for(hp),
                                                    sdt_of(hp))
         del raw_h, vol_h
+
+    if args.lprec_slices > 0 and not split:
+        variants["f32_lprec"] = measure_lprec(tcp, raw, dark, flat, theta, center, n, min(args.lprec_slices, nz))
 
     rows = None
     if not args.no_rows and world == 1 and not split:

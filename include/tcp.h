@@ -418,7 +418,11 @@ typedef struct {
 
 typedef struct {
   int32_t sino_dtype;   /* storage of the filtered sinograms (F16 when opts is NULL) */
-  int32_t autotune;     /* 1: time every backprojector configuration on this batch */
+  int32_t autotune;     /* 1: time every backprojector configuration on this batch (CUDA-core
+                           configurations in one persistent launch, and for 16-bit sinograms the
+                           tensor-core kernel, one launch per dataset) and keep the fastest;
+                           0: the configuration fixed by tcp_set_backproject_config, if any, else
+                           {8, 16, 4, 0} */
   int32_t reserved[2];
 } tcp_batch_opts;
 

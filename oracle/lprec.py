@@ -123,6 +123,20 @@ def backproject_spline_exact(sino: np.ndarray, theta: np.ndarray, center: float,
     return out
 
 
+def backproject_spline_points(sino_slice: np.ndarray, theta: np.ndarray, center: float, n: int,
+                              ix: np.ndarray, iy: np.ndarray) -> np.ndarray:
+    """backproject_spline_exact of one slice sino[theta][j] at the voxels
+    (ix[k], iy[k]) only (the same direct sums)."""
+    q = np.asarray(sino_slice, dtype=np.float64)
+    coef = bspline_coeffs(q, axis=1)
+    x = np.asarray(ix, dtype=np.float64) - n / 2.0
+    y = np.asarray(iy, dtype=np.float64) - n / 2.0
+    out = np.zeros(x.shape)
+    for t in range(q.shape[0]):
+        out += bspline_eval(coef[t], x * np.cos(theta[t]) + y * np.sin(theta[t]) + center + PAD)
+    return out
+
+
 def _check_equally_spaced(theta: np.ndarray) -> float:
     d = np.diff(theta)
     if theta.shape[0] < 3 or not np.allclose(d, d[0], rtol=0, atol=1e-9) or abs(d[0] * theta.shape[0] - np.pi) > 1e-9:

@@ -20,7 +20,7 @@ class Batch:
     theta (angles), center, and optionally filter ('shepp') and pad ('edge').
     The tensors must outlive the batch."""
 
-    def __init__(self, datasets, sino_dtype=torch.float16, autotune: bool = True, stream=None):
+    def __init__(self, datasets, sino_dtype=torch.float16, autotune: bool = True, stream=None, config=None):
         self._keep = []
         items = (_lib.BatchItem * len(datasets))()
         for i, d in enumerate(datasets):
@@ -39,8 +39,14 @@ class Batch:
         opts.sino_dtype = _lib._TORCH_DTYPE[_lib.DTYPES[sino_dtype]]
         opts.autotune = int(bool(autotune))
         h = ctypes.c_void_p()
-        _lib.call("tcp_batch_create", items, len(datasets), ctypes.byref(opts), _lib.stream_ptr(stream),
-                  ctypes.byref(h))
+        if config is not None:  # (k_slices, theta_stage, rows_per_thread, kernel), used without autotune
+            _lib.call("tcp_set_backproject_config", ctypes.byref(_lib.BpConfig(*config)))
+        try:
+            _lib.call("tcp_batch_create", items, len(datasets), ctypes.byref(opts), _lib.stream_ptr(stream),
+                      ctypes.byref(h))
+        finally:
+            if config is not None:
+                _lib.call("tcp_set_backproject_config", None)
         self._h = h
         self.datasets = datasets
 
@@ -61,7 +67,7 @@ class Batch:
         blocks = ctypes.c_int32()
         _lib.call("tcp_batch_info", self._h, ctypes.byref(c), ctypes.byref(ms), ctypes.byref(units),
                   ctypes.byref(blocks))
-        return {"config": (c.k_slices, c.theta_stage, c.rows_per_thread), "tuned_ms": ms.value,
+        return {"config": (c.k_slices, c.theta_stage, c.rows_per_thread), "kernel": c.kernel, "tuned_ms": ms.value,
                 "work_units": units.value, "grid_blocks": blocks.value}
 
     def close(self):

@@ -21,8 +21,12 @@
 namespace tcp {
 namespace {
 
-const tcp_bp_config kCandidates[] = {{8, 16, 4, 0}, {4, 32, 4, 0}, {4, 16, 4, 0}, {16, 8, 2, 0},
-                                     {8, 16, 2, 0}, {2, 16, 4, 0}, {1, 32, 4, 0}};
+// CUDA-core configurations (rows_per_thread 16: 4 x 4 voxel blocks, FP32
+// sinograms only), then the tensor-core kernel with 1 or 2 angles per stage
+// (16-bit sinograms whose strides suit TMA).
+const tcp_bp_config kCandidates[] = {{8, 16, 4, 0}, {4, 32, 4, 0}, {4, 16, 4, 0}, {16, 8, 2, 0}, {8, 16, 2, 0},
+                                     {2, 16, 4, 0}, {1, 32, 4, 0}, {4, 16, 16, 0}, {8, 16, 16, 0}, {4, 32, 16, 0},
+                                     {8, 2, 4, 1}, {8, 1, 4, 1}};
 
 int esize(int dt) { return dt == TCP_F32 ? 4 : 2; }
 
@@ -91,7 +95,24 @@ struct tcp_batch {
 
 namespace {
 
+// The tensor-core kernel takes 16-bit sinograms with TMA-friendly strides.
+bool tc_batch_ok(const tcp_batch* b) {
+  if (b->sdt != TCP_F16 && b->sdt != TCP_BF16) return false;
+  for (const ItemRt& it : b->items)
+    if (!tc_eligible(it.sino)) return false;
+  return true;
+}
+
 tcp_status set_config(tcp_batch* b, const tcp_bp_config& cfg) {
+  if (cfg.kernel == 1) {  // one tensor-core launch per dataset inside the run
+    if (!tc_batch_ok(b)) return fail(TCP_ERR_UNSUPPORTED, "batch: tensor-core kernel needs 16-bit TMA-friendly sinograms");
+    long long units = 0;
+    for (const ItemRt& it : b->items) units += ((it.vol.d1 + 15) / 16) * ((it.vol.d1 + 15) / 16);
+    b->cfg = cfg;
+    b->units = units;
+    b->blocks = 0;
+    return TCP_OK;
+  }
   std::vector<BpArgs> args;
   std::vector<long long> prefix(1, 0);
   for (const ItemRt& it : b->items) {
@@ -121,6 +142,15 @@ tcp_status prep(tcp_batch* b, cudaStream_t st) {
 }
 
 tcp_status backproject_all(tcp_batch* b, cudaStream_t st) {
+  if (b->cfg.kernel == 1) {
+    for (const ItemRt& it : b->items) {
+      const float scale = (float)(M_PI / (double)it.sino.d1 / storage_scale(b->sdt));
+      tcp_status s = launch_backproject_tc(it.sino, it.trig, 0.5 * (double)it.sino.d2, it.vol, scale,
+                                           b->cfg.theta_stage, st);
+      if (s != TCP_OK) return s;
+    }
+    return TCP_OK;
+  }
   TCP_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
   BpWork w;
   w.items = b->d_items;
@@ -262,6 +292,8 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
     if (e != cudaSuccess) s = cuda_fail(e, "batch: cudaMalloc");
   }
+  // without autotune: the configuration fixed by tcp_set_backproject_config, if any
+  if (s == TCP_OK && !o.autotune && bp_override().k_slices) b->cfg = bp_override();
   if (s == TCP_OK) s = set_config(b, b->cfg);
   if (s == TCP_OK && o.autotune) {
     s = prep(b, st);
@@ -271,6 +303,10 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
       if (s != TCP_OK) break;
       float ms = 0.f;
       s = time_config(b, c, st, &ms);
+      if (s == TCP_ERR_UNSUPPORTED) {  // not instantiated for this dtype pair: skip
+        s = TCP_OK;
+        continue;
+      }
       if (s == TCP_OK && ms < best) {
         best = ms;
         best_cfg = c;
@@ -358,10 +394,12 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
   TCP_CUDA_TRY(cudaEventCreate(&e0));
   TCP_CUDA_TRY(cudaEventCreate(&e1));
   tcp_status s = TCP_OK;
-  std::vector<tcp_bp_config> cands(std::begin(kCandidates), std::end(kCandidates));
-  if (sino->dtype == TCP_F16 || sino->dtype == TCP_BF16) {
-    cands.push_back(tcp_bp_config{8, 2, 4, 1});
-    cands.push_back(tcp_bp_config{8, 1, 4, 1});
+  std::vector<tcp_bp_config> cands;
+  for (const tcp_bp_config& c : kCandidates) {
+    const bool f32 = sino->dtype == TCP_F32;
+    if (c.kernel == 1 && f32) continue;                          // tensor cores: 16-bit sinograms
+    if (c.kernel == 0 && c.rows_per_thread == 16 && !f32) continue;  // 4 x 4 blocks: FP32 sinograms
+    cands.push_back(c);
   }
   for (const tcp_bp_config& c : cands) {
     if ((s = tcp_set_backproject_config(&c)) != TCP_OK) break;

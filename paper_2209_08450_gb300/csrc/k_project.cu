@@ -77,16 +77,23 @@ struct PjArgs {
   const double2* trig;
   const int2* orig;
   double center, half_n;
+  int zbase;  // first slice of blockIdx.z == 0
 };
 
-constexpr int kPjThreads = 128;
+// A block is 8 warps: 8 consecutive angles times the same 32 detector bins.
+// Neighbouring angles visit nearly the same voxels at each step of the walk,
+// so the block's warps share those rows through L1 instead of each streaming
+// them from L2.
+constexpr int kPjAngles = 8;
+constexpr int kPjThreads = 32 * kPjAngles;
 
-template <class TV, class TS, int K>
+// FULL: all K slices of the block exist (no per-slice bound check).
+template <class TV, class TS, int K, bool FULL>
 __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
-  const int t = blockIdx.y;
-  const int j = blockIdx.x * kPjThreads + threadIdx.x;
-  const int z0 = blockIdx.z * K;
-  if (j >= a.ndet) return;
+  const int t = blockIdx.y * kPjAngles + (threadIdx.x >> 5);
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int z0 = a.zbase + blockIdx.z * K;
+  if (j >= a.ndet || t >= a.ntheta) return;
   const double2 cs = a.trig[t];
   const float c = __double2float_rn(cs.x), s = __double2float_rn(cs.y);
   const bool ymajor = fabs(cs.x) >= fabs(cs.y);
@@ -96,8 +103,8 @@ __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
   const float jc = (float)((double)j - a.center);
   const int2* orig = a.orig + (int64_t)t * a.ntx * a.ntx;
   // x-major angles walk columns: read them as rows of the transposed copy
-  const TV* vol = reinterpret_cast<const TV*>(ymajor ? a.vol : a.volT);
   const int64_t vy = ymajor ? a.v_y : a.n, vz = ymajor ? a.v_z : (int64_t)a.n * a.n;
+  const TV* vol = reinterpret_cast<const TV*>(ymajor ? a.vol : a.volT) + (int64_t)z0 * vz;
 
   float acc[K];
 #pragma unroll
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
         const TV* p = vol + (int64_t)m * vy + u;  // (iy, ix) for y-major, (ix, iy) transposed otherwise
 #pragma unroll
         for (int k = 0; k < K; ++k)
-          if (z0 + k < a.nz) acc[k] = __fmaf_rn(wt, Store<TV>::load(p + (int64_t)(z0 + k) * vz), acc[k]);
+          if (FULL || z0 + k < a.nz) acc[k] = __fmaf_rn(wt, Store<TV>::load(p + (int64_t)k * vz), acc[k]);
       }
     }
   }
@@ -133,21 +140,22 @@ __global__ void __launch_bounds__(kPjThreads) k_project(PjArgs a) {
 }
 
 template <class TV, class TS>
-void (*pick(int K))(PjArgs) {
+void (*pick(int K, bool full))(PjArgs) {
   switch (K) {
-    case 1: return k_project<TV, TS, 1>;
-    case 2: return k_project<TV, TS, 2>;
-    case 4: return k_project<TV, TS, 4>;
-    default: return k_project<TV, TS, 8>;
+    case 1: return full ? k_project<TV, TS, 1, true> : k_project<TV, TS, 1, false>;
+    case 2: return full ? k_project<TV, TS, 2, true> : k_project<TV, TS, 2, false>;
+    case 4: return full ? k_project<TV, TS, 4, true> : k_project<TV, TS, 4, false>;
+    case 8: return full ? k_project<TV, TS, 8, true> : k_project<TV, TS, 8, false>;
+    default: return full ? k_project<TV, TS, 16, true> : k_project<TV, TS, 16, false>;
   }
 }
 
 template <class TV>
-void (*pick_s(int sdt, int K))(PjArgs) {
+void (*pick_s(int sdt, int K, bool full))(PjArgs) {
   switch (sdt) {
-    case TCP_F32: return pick<TV, float>(K);
-    case TCP_F16: return pick<TV, __half>(K);
-    case TCP_BF16: return pick<TV, __nv_bfloat16>(K);
+    case TCP_F32: return pick<TV, float>(K, full);
+    case TCP_F16: return pick<TV, __half>(K, full);
+    case TCP_BF16: return pick<TV, __nv_bfloat16>(K, full);
   }
   return nullptr;
 }
@@ -168,14 +176,19 @@ tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double cen
                              cudaStream_t st) {
   const int nz = (int)vol.d0, n = (int)vol.d1, nt = (int)sino.d1, nd = (int)sino.d2;
   if (nz == 0 || nt == 0 || nd == 0) return TCP_OK;
-  const int K = nz >= 8 ? 8 : (nz >= 4 ? 4 : (nz >= 2 ? 2 : 1));
-  void (*k)(PjArgs) = nullptr;
+  // slices per thread: the candidate search of a (theta, j, step) is shared by K slices
+  const int K = nz >= 16 ? 16 : (nz >= 8 ? 8 : (nz >= 4 ? 4 : (nz >= 2 ? 2 : 1)));
+  void (*kf)(PjArgs) = nullptr;  // blocks whose K slices all exist
+  void (*kt)(PjArgs) = nullptr;  // the ragged last block
   switch (vol.dtype) {
-    case TCP_F32: k = pick_s<float>(sino.dtype, K); break;
-    case TCP_F16: k = pick_s<__half>(sino.dtype, K); break;
-    case TCP_BF16: k = pick_s<__nv_bfloat16>(sino.dtype, K); break;
+    case TCP_F32: kf = pick_s<float>(sino.dtype, K, true); kt = pick_s<float>(sino.dtype, K, false); break;
+    case TCP_F16: kf = pick_s<__half>(sino.dtype, K, true); kt = pick_s<__half>(sino.dtype, K, false); break;
+    case TCP_BF16:
+      kf = pick_s<__nv_bfloat16>(sino.dtype, K, true);
+      kt = pick_s<__nv_bfloat16>(sino.dtype, K, false);
+      break;
   }
-  if (!k) return fail(TCP_ERR_UNSUPPORTED, "project: no kernel for this dtype pair");
+  if (!kf || !kt) return fail(TCP_ERR_UNSUPPORTED, "project: no kernel for this dtype pair");
   PjArgs a;
   a.vol = vol.p;
   a.v_z = vol.s0;
@@ -191,7 +204,9 @@ tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double cen
   a.trig = trig.dev;
   a.center = center;
   a.half_n = 0.5 * (double)n;
-  dim3 grid((unsigned)((nd + kPjThreads - 1) / kPjThreads), (unsigned)nt, (unsigned)((nz + K - 1) / K));
+  a.zbase = 0;
+  const int nfull = nz / K;
+  dim3 grid((unsigned)((nd + 31) / 32), (unsigned)((nt + kPjAngles - 1) / kPjAngles), (unsigned)std::max(nfull, 1));
   if (grid.y > 65535u || grid.z > 65535u)
     return fail(TCP_ERR_SHAPE, "project: too many angles or slice blocks for one launch");
   int2* orig = reinterpret_cast<int2*>(ws);
@@ -221,8 +236,16 @@ tcp_status launch_project_ws(const View3& vol, const TrigTable& trig, double cen
     k_origin_table<<<blocks, 256, 0, st>>>(trig.dev, nt, a.ntx, a.half_n, center, orig);
   }
   a.orig = orig;
-  k<<<grid, kPjThreads, 0, st>>>(a);
-  TCP_CUDA_TRY(cudaGetLastError());
+  if (nfull > 0) {
+    kf<<<grid, kPjThreads, 0, st>>>(a);
+    TCP_CUDA_TRY(cudaGetLastError());
+  }
+  if (nz % K) {
+    a.zbase = nfull * K;
+    grid.z = 1;
+    kt<<<grid, kPjThreads, 0, st>>>(a);
+    TCP_CUDA_TRY(cudaGetLastError());
+  }
   return TCP_OK;
 }
 

@@ -121,3 +121,27 @@ def test_fbp_lprec_pipeline_matches_oracle():
     exact = olp.backproject_spline_exact(q, d.theta, 32.0, 64)
     assert rel(vol.double().cpu().numpy(), exact) <= 1.02 * rel(ref, exact) + 1e-6
     plan.close()
+
+
+def test_lprec_2048_sampled_voxels_converge_to_the_spline_sums():
+    # a 2048^2 slice of the porous workload, 2048 angles, filtered rows: LpRec
+    # at oversampling 2 and 4 on sampled voxels against the direct cubic-spline
+    # sums (the quantity LpRec approximates); the error falls about tenfold
+    # per doubling, as in the oracle's own convergence pin
+    import synth.gpu as sgpu
+    raw, dark, flat, th, c, mu = sgpu.porous_frames(2048, 2048, 2048, seed=0, device=DEV, slices=np.array([1024]))
+    r = raw.cpu().numpy().view(np.uint16)
+    p = oracle.normalize(r, oracle.frame_mean(dark.cpu().numpy().view(np.uint16)),
+                         oracle.frame_mean(flat.cpu().numpy().view(np.uint16)))
+    q = oracle.filter_sino(p, c, "shepp")[0]
+    rng = np.random.default_rng(5)
+    ix, iy = rng.integers(200, 1848, 300), rng.integers(200, 1848, 300)
+    ref = olp.backproject_spline_points(q, th, 1024.0, 2048, ix, iy)
+    qd = torch.from_numpy(q[None]).float().to(DEV)
+    errs = []
+    for os in (2.0, 4.0):
+        got = tcp.lprec(qd, th, 1024.0, oversampling=os)[0].double().cpu().numpy()[iy, ix]
+        errs.append(rel(got, ref))
+    print("\n2048^2 LpRec vs spline sums: os 2 %.2e, os 4 %.2e" % tuple(errs))
+    assert errs[1] < errs[0] / 5
+    assert errs[1] < 1e-3

@@ -94,3 +94,13 @@ def test_lprec_fbp_of_smooth_bump_converges_to_the_function():
         assert abs(a - b) < 0.01 * b, (n, a, b)
         errs.append(a)
     assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5 and errs[2] < 1e-4, errs
+
+
+def test_spline_points_equal_the_full_image():
+    rng = np.random.default_rng(7)
+    q = rng.standard_normal((1, 9, 20))
+    th = rng.uniform(0, np.pi, 9)
+    full = lp.backproject_spline_exact(q, th, 9.6, 18)[0]
+    ix, iy = rng.integers(0, 18, 40), rng.integers(0, 18, 40)
+    np.testing.assert_allclose(lp.backproject_spline_points(q[0], th, 9.6, 18, ix, iy), full[iy, ix],
+                               rtol=0, atol=1e-12)
