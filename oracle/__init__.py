@@ -106,19 +106,20 @@ def padded_length(ndet: int, rule: str = "pow2") -> int:
     sizes: powers of two for FP16, products of small primes for FP32).
 
     pow2:   the next power of two >= 2*ndet (every precision, the default);
-    smooth: the smaller of that and the next 3 * 2^k >= 2*ndet, the latter
-            only from 48 on (1536 -> 3072 and 2560 -> 6144 instead of 4096 and
-            8192)."""
+    smooth: the smallest of that, the next 3 * 2^k >= 2*ndet (from 48 on) and
+            the next 5 * 2^k >= 2*ndet (from 80 on): 1536 -> 3072 and
+            2560 -> 5120 instead of 4096 and 8192."""
     if rule not in ("pow2", "smooth"):
         raise ValueError("unknown padding rule %r" % rule)
     n = 1
     while n < 2 * ndet:
         n *= 2
     if rule == "smooth":
-        m = 3
-        while m < 2 * ndet or m < 48:
-            m *= 2
-        n = min(n, m)
+        for base, least in ((3, 48), (5, 80)):
+            m = base
+            while m < 2 * ndet or m < least:
+                m *= 2
+            n = min(n, m)
     return n
 
 

@@ -67,7 +67,7 @@ def test_ramp_response_closed_form():
     s = sum(1.0 / (np.pi ** 2 * m * m) for m in (1, 3, 5, 7))
     assert abs(r[0] - (0.25 - 2 * s)) < 1e-15
     assert abs(r[-1] - (0.25 + 2 * s)) < 1e-15
-    for npad in (16, 256, 4096, 48, 3072):  # 3 x 2^k periods of the smooth padding too
+    for npad in (16, 256, 4096, 48, 3072, 80, 5120):  # 3 x 2^k and 5 x 2^k periods of the smooth padding too
         r = oracle.filter_response("ramp", npad)
         nu = np.arange(npad // 2 + 1) / npad
         assert np.max(np.abs(r - nu)) < 1.0 / npad
@@ -131,22 +131,24 @@ def test_filter_equals_direct_convolution(nd, center, kind, pad):
 
 
 def test_smooth_padded_lengths():
-    # the smaller of the next 2^k and the next 3 * 2^k (>= 48) at or above 2 ndet
-    cases = {12: 32, 20: 48, 24: 48, 40: 96, 100: 256, 200: 512, 300: 768, 1024: 2048, 1536: 3072, 2560: 6144,
-             2048: 4096, 4096: 8192}
+    # the smallest of the next 2^k, 3 * 2^k (>= 48) and 5 * 2^k (>= 80) at or above 2 ndet
+    cases = {12: 32, 20: 48, 24: 48, 40: 80, 45: 96, 100: 256, 200: 512, 300: 640, 1024: 2048, 1536: 3072,
+             2560: 5120, 2048: 4096, 4096: 8192, 30: 64, 38: 80, 76: 160}
     for nd, n in cases.items():
         assert oracle.padded_length(nd, "smooth") == n, nd
         assert oracle.padded_length(nd) == 1 << (2 * nd - 1).bit_length()
 
 
 @pytest.mark.parametrize("nd,center,kind,pad", [
-    (20, 11.25, "shepp", "edge"), (24, 12.0, "parzen", "zero"), (40, 17.6, "ramp", "edge")])
+    (20, 11.25, "shepp", "edge"), (24, 12.0, "parzen", "zero"), (45, 17.6, "ramp", "edge"),
+    (40, 19.3, "shepp", "edge"), (76, 40.1, "parzen", "zero")])
 def test_filter_on_smooth_padding_equals_direct_convolution(nd, center, kind, pad):
-    # padded lengths 48, 48 and 96 (3 x 2^k): the same definition, other period
+    # padded lengths 48, 48, 96 (3 x 2^k), 80 and 160 (5 x 2^k): the same
+    # definition, other period
     rng = np.random.default_rng(nd + 1)
     row = rng.normal(size=nd)
     npad = oracle.padded_length(nd, "smooth")
-    assert npad % 3 == 0
+    assert npad % 3 == 0 or npad % 5 == 0
     got = oracle.filter_sino(row[None, :], center, kind, pad, ntheta=5, rule="smooth")[0]
     ref = _brute_filter(row, center, kind, pad, 5, npad=npad)
     assert np.max(np.abs(got - ref)) < 1e-12
