@@ -106,9 +106,14 @@ typedef enum {
  * sizes; Sec. 3 pads to suppress artefacts from objects wider than the field
  * of view).  The padded length is the next power of two >= 2*ndet; with the
  * TCP_PAD_SMOOTH flag set (e.g. TCP_PAD_EDGE | TCP_PAD_SMOOTH) it is the
- * smaller of that and the next 3 * 2^k >= 2*ndet (counted from 48 on), e.g.
- * 3072 instead of 4096 for ndet = 1536 and 6144 instead of 8192 for 2560. */
+ * smallest of that, the next 3 * 2^k >= 2*ndet (counted from 48 on) and the
+ * next 5 * 2^k >= 2*ndet (from 80 on), e.g. 3072 instead of 4096 for
+ * ndet = 1536 and 5120 instead of 8192 for 2560. */
 typedef enum { TCP_PAD_EDGE = 0, TCP_PAD_ZERO = 1, TCP_PAD_SMOOTH = 2 } tcp_pad_mode;
+
+/* Padded row length the filter uses for ndet detector pixels and this
+ * padding mode (only the TCP_PAD_SMOOTH bit matters); -1 for ndet < 1. */
+int64_t tcp_padded_length(int64_t ndet, int32_t pad_mode);
 
 typedef struct {
   void* data;         /* device pointer unless the call says host */

@@ -33,17 +33,10 @@ def _as_u16(t: torch.Tensor) -> torch.Tensor:
 
 
 def padded_length(ndet: int, smooth: bool = False) -> int:
-    """Padded row length of the filter: the next power of two >= 2 ndet; with
-    `smooth`, the smaller of that and the next 3 * 2^k >= 2 ndet (from 48 on)."""
-    n = 1
-    while n < 2 * ndet:
-        n *= 2
-    if smooth:
-        m = 3
-        while m < 2 * ndet or m < 48:
-            m *= 2
-        n = min(n, m)
-    return n
+    """Padded row length of the filter (tcp_padded_length): the next power of
+    two >= 2 ndet; with `smooth`, the smallest of that, the next 3 * 2^k
+    (from 48 on) and the next 5 * 2^k (from 80 on) >= 2 ndet."""
+    return int(_lib.load().tcp_padded_length(int(ndet), _lib.PADS["edge_smooth" if smooth else "edge"]))
 
 
 def frame_mean(frames: torch.Tensor, stream=None) -> torch.Tensor:

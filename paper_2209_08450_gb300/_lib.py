@@ -80,6 +80,7 @@ SIGNATURES = {
     "tcp_status_string": ([_I32], ctypes.c_char_p),
     "tcp_last_error": ([], ctypes.c_char_p),
     "tcp_version": ([], ctypes.c_int),
+    "tcp_padded_length": ([_I64, _I32], _I64),
     "tcp_device_check": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I32),
     "tcp_set_checked": ([_I32], _I32),
     "tcp_cache_clear": ([], _I32),

@@ -147,10 +147,12 @@ tcp_status build_trig_owned(const double* theta, int64_t n, std::vector<void*>* 
 int64_t padded_length(int64_t ndet, bool smooth) {
   int64_t n = 1;
   while (n < 2 * ndet) n *= 2;
-  if (smooth) {  // the next 3 * 2^k >= 2 ndet, counted from 48 on
-    int64_t m = 3;
-    while (m < 2 * ndet || m < 48) m *= 2;
-    n = std::min(n, m);
+  if (smooth) {  // the next 3 * 2^k >= 2 ndet (from 48 on) and 5 * 2^k (from 80 on)
+    for (const int64_t base : {3, 5}) {
+      int64_t m = base;
+      while (m < 2 * ndet || m < 16 * base) m *= 2;
+      n = std::min(n, m);
+    }
   }
   return n;
 }
@@ -197,7 +199,7 @@ static std::vector<double> filter_response(int64_t npad, int32_t filter) {
   if ((npad & (npad - 1)) == 0) {
     fft64(h);
   } else {
-    // 3 * 2^k periods: the same DFT as a direct cosine sum (h is real and even)
+    // 3 * 2^k and 5 * 2^k periods: the same DFT as a direct cosine sum (h is real and even)
     std::vector<double> r((size_t)npad / 2 + 1);
     for (int64_t k = 0; k <= npad / 2; ++k) {
       double acc = 0.25;
@@ -497,6 +499,11 @@ const char* tcp_status_string(tcp_status s) {
 const char* tcp_last_error(void) { return g_last_error.c_str(); }
 
 int tcp_version(void) { return TCP_VERSION; }
+
+int64_t tcp_padded_length(int64_t ndet, int32_t pad_mode) {
+  if (ndet < 1) return -1;
+  return padded_length(ndet, pad_smooth(pad_mode));
+}
 
 tcp_status tcp_set_checked(int32_t on) {
   g_checked = on != 0;

@@ -9,7 +9,7 @@
 // without a separation step.  The FFT is a Stockham auto-sort transform
 // between two shared-memory buffers, one barrier per pass: radix-16 register
 // butterflies, then one pass of 8, 4 or 2 for the rest of the power of two,
-// then radix 3 for padded lengths 3 * 2^k.  The forward last pass, the
+// then radix 3 or 5 for padded lengths 3 * 2^k or 5 * 2^k.  The forward last pass, the
 // response and the inverse first pass run in registers (the inverse takes the
 // radices in reverse order), and the inverse last pass writes the output
 // rows.  Twiddles (a two-level table in shared memory) and the response are
@@ -91,9 +91,31 @@ __device__ __forceinline__ void dft3(float2& v0, float2& v1, float2& v2) {
   v2 = csub(m, r);
 }
 
+// 5-point DFT: with t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4, t4 = v2 - v3,
+// X0 = v0 + t1 + t2, X1,4 = v0 + c1 t1 + c2 t2 -+ i (s1 t3 + s2 t4),
+// X2,3 = v0 + c2 t1 + c1 t2 -+ i (s2 t3 - s1 t4) (forward; the inverse flips
+// the sign of i), c_m = cos(2 pi m / 5), s_m = sin(2 pi m / 5).
+template <bool INV>
+__device__ __forceinline__ void dft5(float2& v0, float2& v1, float2& v2, float2& v3, float2& v4) {
+  constexpr float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;
+  constexpr float s1 = 0.951056516295153572f, s2 = 0.587785252292473129f;
+  const float2 t1 = cadd(v1, v4), t2 = cadd(v2, v3), t3 = csub(v1, v4), t4 = csub(v2, v3);
+  const float2 b1 = make_float2(v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y);
+  const float2 b2 = make_float2(v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y);
+  const float2 d1 = rot<INV>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));  // -+ i (s1 t3 + s2 t4)
+  const float2 d2 = rot<INV>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+  v0 = cadd(v0, cadd(t1, t2));
+  v1 = cadd(b1, d1);
+  v4 = csub(b1, d1);
+  v2 = cadd(b2, d2);
+  v3 = csub(b2, d2);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-  if constexpr (R == 3) {
+  if constexpr (R == 5) {
+    dft5<INV>(v[0], v[1], v[2], v[3], v[4]);
+  } else if constexpr (R == 3) {
     dft3<INV>(v[0], v[1], v[2]);
   } else if constexpr (R == 2) {
     dft2<INV>(v[0], v[1]);
@@ -160,7 +182,7 @@ __device__ __forceinline__ void stockham_pass(const float2* in, float2* out, int
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[pi16(b + r * nb)];
-    const int k = P2 ? (b & (Ns - 1)) : b % Ns;  // P2: Ns is a power of two (else 3 * 2^i)
+    const int k = P2 ? (b & (Ns - 1)) : b % Ns;  // P2: Ns is a power of two (else 3 * 2^i or 5 * 2^i)
     if (Ns > 1) {
       float2 w[R];
       const int m1 = k * step;
@@ -311,9 +333,10 @@ __device__ __forceinline__ void pass_r(int r, const float2* in, float2* out, int
       case 8: stockham_pass<8, INV>(in, out, N, Ns, tw, gt, gs); break;
       case 4: stockham_pass<4, INV>(in, out, N, Ns, tw, gt, gs); break;
       case 3: stockham_pass<3, INV>(in, out, N, Ns, tw, gt, gs); break;
+      case 5: stockham_pass<5, INV>(in, out, N, Ns, tw, gt, gs); break;
       default: stockham_pass<2, INV>(in, out, N, Ns, tw, gt, gs); break;
     }
-  } else {  // after the inverse radix-3 pass: Ns = 3 * 2^i
+  } else {  // after the inverse radix-3 or radix-5 pass: Ns = 3 * 2^i or 5 * 2^i
     switch (r) {
       case 16: stockham_pass<16, INV, false>(in, out, N, Ns, tw, gt, gs); break;
       case 8: stockham_pass<8, INV, false>(in, out, N, Ns, tw, gt, gs); break;
@@ -367,6 +390,7 @@ __device__ void filter_pair(float2* a, float2* b, int N, const int* rad, int nra
     else if (rl == 8) fused_turn<8>(a, b, N, tw, resp, gt, gs);
     else if (rl == 4) fused_turn<4>(a, b, N, tw, resp, gt, gs);
     else if (rl == 3) fused_turn<3>(a, b, N, tw, resp, gt, gs);
+    else if (rl == 5) fused_turn<5>(a, b, N, tw, resp, gt, gs);
     else fused_turn<2>(a, b, N, tw, resp, gt, gs);
   }
   __syncthreads();
@@ -529,20 +553,21 @@ void (*pick_out(int dt))(FiltArgs) {
 tcp_status run(void (*k)(FiltArgs), FiltArgs& a, const FilterTable& ft, int pad_mode, cudaStream_t st) {
   a.npad = ft.npad;
   a.log2n = 0;
-  // radices: N = 16^p 2^q (3 if N % 3 == 0), forward order 16, .., 16, 2^q, 3
+  // radices: N = 16^p 2^q (times 3 or 5), forward order 16, .., 16, 2^q, 3 or 5
   {
-    const bool three = a.npad % 3 == 0;
-    int m = three ? a.npad / 3 : a.npad, l2 = 0;
+    const bool three = a.npad % 3 == 0, five = a.npad % 5 == 0;
+    const int odd = three ? 3 : (five ? 5 : 1);
+    int m = a.npad / odd, l2 = 0;
     while ((1 << l2) < m) ++l2;
     a.log2n = l2;
     a.nrad = 0;
-    if (!three && l2 <= 4) {
+    if (odd == 1 && l2 <= 4) {
       a.rad[a.nrad++] = a.npad;  // one butterfly
     } else {
       const int q = l2 % 4;
       for (int i = 0; i < l2 / 4; ++i) a.rad[a.nrad++] = 16;
       if (q) a.rad[a.nrad++] = 1 << q;
-      if (three) a.rad[a.nrad++] = 3;
+      if (odd > 1) a.rad[a.nrad++] = odd;
     }
     if (a.nrad > 8 || (a.nrad > 1 && a.rad[0] != 16))
       return fail(TCP_ERR_UNSUPPORTED, "filter: padded length " + std::to_string(a.npad) + " not supported");

@@ -284,3 +284,11 @@ def test_lprec_argument_checks(lib):
     o.width = 9
     assert lib.tcp_fbp(ctypes.byref(raw), ctypes.byref(dark), ctypes.byref(dark), eq, 8.0, ctypes.byref(vol),
                        ctypes.byref(o), None) == 1
+
+
+def test_padded_length_matches_the_oracle_rule(lib):
+    import oracle
+    for nd in (1, 12, 20, 24, 38, 40, 45, 76, 100, 200, 300, 1024, 1536, 2048, 2560, 4096):
+        assert lib.tcp_padded_length(nd, 0) == oracle.padded_length(nd)
+        assert lib.tcp_padded_length(nd, 2) == oracle.padded_length(nd, "smooth"), nd
+    assert lib.tcp_padded_length(0, 0) == -1

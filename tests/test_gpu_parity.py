@@ -482,10 +482,12 @@ def test_split_sinogram_rejections():
 
 # ------------------------------------------ smooth (3 x 2^k) filter padding --
 
-@pytest.mark.parametrize("nd,pad", [(40, "edge"), (300, "zero"), (24, "edge"), (1536, "edge")])
+@pytest.mark.parametrize("nd,pad", [(40, "edge"), (300, "zero"), (24, "edge"), (1536, "edge"), (45, "zero"),
+                                    (2560, "edge"), (76, "edge")])
 @pytest.mark.parametrize("dt", [torch.float32, torch.float16])
 def test_filter_on_smooth_padding(nd, pad, dt):
-    # padded lengths 96, 768, 48 and 3072 (radix-3 FFT pass), in place and fused
+    # padded lengths 80, 640, 5120, 160 (radix-5 FFT pass) and 48, 3072, 96
+    # (radix 3), in place and fused
     rng = np.random.default_rng(nd)
     nz, nt = 3, 5 if nd > 1000 else 17
     q = rng.normal(size=(nz, nt, nd))
