@@ -168,8 +168,11 @@ def test_backproject_large_detector_offsets():
 
 # ----------------------------------------------------------------- project --
 
-@pytest.mark.parametrize("nz,nt,nd,n,center", [(5, 67, 91, 80, 44.6), (9, 30, 40, 64, 33.0), (1, 5, 17, 9, 8.2)])
+@pytest.mark.parametrize("nz,nt,nd,n,center", [(5, 67, 91, 80, 44.6), (9, 30, 40, 64, 33.0), (1, 5, 17, 9, 8.2),
+                                               (21, 50, 70, 64, 33.3), (32, 19, 48, 40, 20.0), (16, 9, 24, 33, 12.5)])
 def test_project_fp32(nz, nt, nd, n, center):
+    # 16-slice groups read the slice-interleaved copies, the remainder the plain
+    # and transposed volume (21 = 16 + 4 + 1)
     rng = np.random.default_rng(nz + nt)
     vol = rng.normal(size=(nz, n, n))
     theta = rng.uniform(0, np.pi, nt)
@@ -178,9 +181,10 @@ def test_project_fp32(nz, nt, nd, n, center):
     assert rel(got, ref) <= 1e-5
 
 
-def test_project_is_exact_transpose_on_gpu():
+@pytest.mark.parametrize("nz", [4, 18])
+def test_project_is_exact_transpose_on_gpu(nz):
     rng = np.random.default_rng(1)
-    nz, n, nt, nd = 4, 100, 73, 111
+    n, nt, nd = 100, 73, 111
     theta = rng.uniform(0, np.pi, nt)
     x = to_dev(rng.normal(size=(nz, n, n)))
     y = to_dev(rng.normal(size=(nz, nt, nd)))
