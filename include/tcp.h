@@ -310,10 +310,14 @@ tcp_status tcp_lprec(const tcp_tensor* sino, const double* theta, double center,
 /* Backprojector launch configuration./* Backprojector launch configuration.  k_slices: slices per thread block
  * (1, 2, 4, 8 or 16); theta_stage: angles staged in shared memory per step
  * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4).
- * kernel: 0 = FP32 pipes (every dtype); 1 = tensor cores (tcgen05.mma with
- * TMEM accumulators, FP16/BF16 sinograms whose row and slice strides are
- * multiples of 8 elements; other inputs fall back to kernel 0; theta_stage 1
- * or 2 sets the angles per pipeline stage, the other fields are ignored).
+ * kernel: 0 = FP32 pipes (every dtype; rows_per_thread 16 on FP32 sinograms:
+ * 4 x 4 voxel blocks reusing samples along the walk); 1 = tensor cores
+ * (tcgen05.mma with TMEM accumulators, FP16/BF16 sinograms whose row and
+ * slice strides are multiples of 8 elements; other inputs fall back to
+ * kernel 0; theta_stage 1 or 2 sets the angles per pipeline stage, the other
+ * fields are ignored); 2 = FP32 pipes for FP32 sinograms with slice pairs
+ * (packed FP32x2 FMAs, one 8-byte shared load per slice pair and voxel after
+ * the first of each column; k_slices even).
  * The automatic choice is kernel 1 for 16-bit sinograms with at least 32
  * slices.  F16X2 sinograms always use the tensor cores. */
 typedef struct {

@@ -191,7 +191,9 @@ def cache_clear() -> None:
 def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, rows_per_thread: int = 4,
                            kernel: int = 0) -> None:
     """Fix the backprojector configuration (None: automatic).  kernel=1 selects
-    the tensor-core backprojector for FP16/BF16 sinograms."""
+    the tensor-core backprojector for FP16/BF16 sinograms, kernel=2 the
+    CUDA-core form for FP32 sinograms with slice pairs (packed FP32x2 FMAs,
+    sample reuse down each voxel column)."""
     if k_slices is None:
         _lib.load().tcp_set_backproject_config(None)
         return

@@ -491,6 +491,146 @@ __device__ __forceinline__ void bp_tile_16i(const BpArgs& a, int gx, int gy, int
   store_tile<TV, K, R>(a, gx, gy, z0, out);
 }
 
+// --- FP32, slice pairs: packed FP32x2 FMAs, sample reuse along the column ----
+//
+// kernel == 2 (FP32 sinograms, K even): the window holds slice pairs
+// win[t][p][i] = (q[z0 + 2p][i], q[z0 + 2p + 1][i]), so one 8-byte shared load
+// fetches sample i of two slices and one fma.rn.f32x2 accumulates both.  A
+// thread owns R consecutive rows of one voxel column; for angles with
+// |sin| <= 0.99 it walks them in the direction in which the ray coordinate
+// grows, where the canonical FP32 coordinate is monotone and rises by less than
+// one sample per row, so the floor index steps by 0 or +1 and the previous
+// voxel's sample pair is reused: one new 8-byte load per slice pair and voxel
+// after the first.  Other angles load both samples.  Lanes are consecutive
+// voxels of a row, so the loads of a warp are contiguous (no bank conflicts).
+// The result equals the other CUDA-core forms to FP32 rounding (same weights;
+// the same per-slice summation order).
+template <int K, int R, bool UP, bool REUSE, bool CHECK>
+__device__ __forceinline__ void pairs_column(const BpArgs& a, const Geo& g, const unsigned long long* wb, int lane,
+                                             int y0, unsigned long long (&acc)[R][K / 2]) {
+  constexpr int KP = K / 2;
+  unsigned long long va[KP], vb[KP];
+  int prev = 0;
+#pragma unroll
+  for (int v = 0; v < R; ++v) {
+    const int r = UP ? v : R - 1 - v;
+    float w;
+    const int idx = window_index<CHECK>(a, g, (float)lane, (float)(y0 + r), &w);
+    const unsigned long long w0 = pack2(1.f - w, 1.f - w), w1 = pack2(w, w);
+    if (!REUSE || v == 0) {
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        va[p] = wb[p * kWin + idx];
+        vb[p] = wb[p * kWin + idx + 1];
+      }
+    } else {
+      if (CHECK && idx != prev && idx != prev + 1) atomicOr(a.err, kErrBpWindow);
+      const bool moved = idx != prev;
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        const unsigned long long nb = wb[p * kWin + idx + 1];
+        va[p] = moved ? vb[p] : va[p];
+        vb[p] = nb;
+      }
+    }
+    prev = idx;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+      ffma2(acc[r][p], w0, va[p]);
+      ffma2(acc[r][p], w1, vb[p]);
+    }
+  }
+}
+
+template <class TV, int K, int T, int R, bool CHECK>
+__device__ __forceinline__ void bp_tile_f32_pairs(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
+  static_assert(K % 2 == 0, "slice pairs");
+  using L = BpLayout<float, K, T>;
+  constexpr int NW = 32 / R, NT = 32 * NW, KP = K / 2;
+  Geo* geo = reinterpret_cast<Geo*>(smem);
+  int* wst = reinterpret_cast<int*>(smem + L::kGeoBytes);
+  float* win = reinterpret_cast<float*>(smem + L::kGeoBytes + L::kWstBytes);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int y0 = warp * R;  // this thread's rows y0 .. y0 + R - 1 of the tile
+  const float* sino = reinterpret_cast<const float*>(a.sino);
+  const int nstages = (a.ntheta + T - 1) / T;
+
+  unsigned long long acc[R][KP];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int p = 0; p < KP; ++p) acc[r][p] = 0ull;
+
+  auto issue = [&](int s) {  // stage s into buffer s & 1: float index ((t KP + p) WIN + i) 2 + h
+    const int b = s & 1, t0 = s * T, nt = min(T, a.ntheta - t0);
+    float* wb = win + b * (T * K * kWin);
+    const int* ws = wst + (s % 3) * T;
+    for (int e = threadIdx.x; e < nt * K * kWin; e += NT) {
+      const int h = e & 1;
+      int rest = e >> 1;
+      const int i = rest % kWin;
+      rest /= kWin;
+      const int pp = rest % KP, t = rest / KP;
+      const int z = z0 + 2 * pp + h, j = ws[t] + i;
+      const bool ok = z < a.nz && j >= 0 && j < a.ndet;
+      const float* src = ok ? sino + (int64_t)z * a.s_z + (int64_t)(t0 + t) * a.s_t + j : sino;
+      cp_async4(wb + e, src, ok);
+    }
+    cp_async_commit();
+  };
+
+  if (threadIdx.x < min(T, a.ntheta)) tile_geometry(a, gx, gy, threadIdx.x, geo + threadIdx.x, wst + threadIdx.x);
+  __syncthreads();
+  issue(0);
+  for (int s = 0; s < nstages; ++s) {
+    const int b = s & 1;
+    if (s + 1 < nstages) {
+      const int t1 = (s + 1) * T;
+      const int gn = (s + 1) % 3;
+      if ((int)threadIdx.x < min(T, a.ntheta - t1))
+        tile_geometry(a, gx, gy, t1 + threadIdx.x, geo + gn * T + threadIdx.x, wst + gn * T + threadIdx.x);
+    }
+    __syncthreads();  // next geometry ready; window buffer (s+1)&1 no longer read
+    if (s + 1 < nstages) {
+      issue(s + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // stage s landed for every thread
+    const int nt = min(T, a.ntheta - s * T);
+    const unsigned long long* wbase = reinterpret_cast<const unsigned long long*>(win + b * (T * K * kWin));
+    for (int t = 0; t < nt; ++t) {
+      const Geo g = geo[(s % 3) * T + t];
+      const unsigned long long* wb = wbase + t * (KP * kWin);
+      if (fabsf(g.s) <= 0.99f) {  // uniform over the block (one angle)
+        if (g.s >= 0.f) pairs_column<K, R, true, true, CHECK>(a, g, wb, lane, y0, acc);
+        else pairs_column<K, R, false, true, CHECK>(a, g, wb, lane, y0, acc);
+      } else {
+        pairs_column<K, R, true, false, CHECK>(a, g, wb, lane, y0, acc);
+      }
+    }
+  }
+  __syncthreads();
+  TV* vol = reinterpret_cast<TV*>(a.vol);
+  const int ix = gx * kTile + lane;
+  if (ix < a.n) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int iy = gy * kTile + y0 + r;
+      if (iy >= a.n) continue;
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[r][p]));
+        if (z0 + 2 * p < a.nz) Store<TV>::put(vol + (int64_t)(z0 + 2 * p) * a.v_z + (int64_t)iy * a.v_y + ix, lo * a.scale);
+        if (z0 + 2 * p + 1 < a.nz)
+          Store<TV>::put(vol + (int64_t)(z0 + 2 * p + 1) * a.v_z + (int64_t)iy * a.v_y + ix, hi * a.scale);
+      }
+    }
+  }
+}
+
 // --- 16-bit, K == 1: (q[i], q[i+1]) pairs, mixed-precision FMAs -----------
 template <class TS, class TV, int K, int T, int R, bool CHECK>
 __device__ __forceinline__ void bp_tile_pairs(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
@@ -542,10 +682,13 @@ __device__ __forceinline__ void bp_tile_pairs(const BpArgs& a, int gx, int gy, i
 // One work unit: the aligned 32x32 voxel tile (gx, gy) times slices
 // [z0, z0 + K), summed over every angle.  Ends with a block barrier, so the
 // shared buffers may be reused by the next unit.
-template <class TS, class TV, int K, int T, int R, bool CHECK>
+// V: 0 the forms above by dtype and R (R == 16: 4 x 4 blocks), 2 the FP32
+// slice-pair form.
+template <class TS, class TV, int K, int T, int R, bool CHECK, int V>
 __device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0, unsigned char* smem) {
   using L = BpLayout<TS, K, T>;
-  if constexpr (L::kF32 && R == 16) bp_tile_f32_rr<TV, K, T, CHECK>(a, gx, gy, z0, smem);
+  if constexpr (L::kF32 && V == 2) bp_tile_f32_pairs<TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
+  else if constexpr (L::kF32 && R == 16) bp_tile_f32_rr<TV, K, T, CHECK>(a, gx, gy, z0, smem);
   else if constexpr (L::kF32) bp_tile_f32<TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
   else if constexpr (L::kInter) bp_tile_16i<TS, TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
   else bp_tile_pairs<TS, TV, K, T, R, CHECK>(a, gx, gy, z0, smem);
@@ -554,9 +697,9 @@ __device__ __forceinline__ void bp_tile(const BpArgs& a, int gx, int gy, int z0,
 
 extern __shared__ __align__(16) unsigned char bp_smem[];
 
-template <class TS, class TV, int K, int T, int R, bool CHECK>
+template <class TS, class TV, int K, int T, int R, bool CHECK, int V>
 __global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
-  bp_tile<TS, TV, K, T, R, CHECK>(a, blockIdx.x % a.ntx, blockIdx.x / a.ntx, blockIdx.y * K, bp_smem);
+  bp_tile<TS, TV, K, T, R, CHECK, V>(a, blockIdx.x % a.ntx, blockIdx.x / a.ntx, blockIdx.y * K, bp_smem);
 }
 
 // Persistent form for batches of datasets with uneven widths and angle
@@ -565,7 +708,7 @@ __global__ void __launch_bounds__(32 * (32 / R)) k_backproject(BpArgs a) {
 // prefix[i+1]; inside an item, units run over 32x32 tiles fastest, then slice
 // blocks.  No block ever waits on another (the counter is the only shared
 // state), so every launch completes regardless of scheduling.
-template <class TS, class TV, int K, int T, int R, bool CHECK>
+template <class TS, class TV, int K, int T, int R, bool CHECK, int V>
 __global__ void __launch_bounds__(32 * (32 / R)) k_backproject_persistent(BpWork w) {
   __shared__ long long s_unit;
   __shared__ int s_item;
@@ -590,7 +733,7 @@ __global__ void __launch_bounds__(32 * (32 / R)) k_backproject_persistent(BpWork
     const long long tiles = (long long)s_args.ntx * s_args.ntx;
     const int zb = (int)(local / tiles);
     const int tile = (int)(local - (long long)zb * tiles);
-    bp_tile<TS, TV, K, T, R, CHECK>(s_args, tile % s_args.ntx, tile / s_args.ntx, zb * K, bp_smem);
+    bp_tile<TS, TV, K, T, R, CHECK, V>(s_args, tile % s_args.ntx, tile / s_args.ntx, zb * K, bp_smem);
   }
 }
 
@@ -603,11 +746,12 @@ struct KernPair {
   size_t smem;  // dynamic shared memory per block
 };
 
-template <class TS, class TV, int K, int T, int R>
+template <class TS, class TV, int K, int T, int R, int V = 0>
 KernPair pick_check(bool check) {
   const size_t sm = BpLayout<TS, K, T>::kBytes;
-  if (check) return {k_backproject<TS, TV, K, T, R, true>, k_backproject_persistent<TS, TV, K, T, R, true>, sm};
-  return {k_backproject<TS, TV, K, T, R, false>, k_backproject_persistent<TS, TV, K, T, R, false>, sm};
+  if (check)
+    return {k_backproject<TS, TV, K, T, R, true, V>, k_backproject_persistent<TS, TV, K, T, R, true, V>, sm};
+  return {k_backproject<TS, TV, K, T, R, false, V>, k_backproject_persistent<TS, TV, K, T, R, false, V>, sm};
 }
 
 // Opt every kernel of a pair in to its dynamic shared memory once.
@@ -625,6 +769,18 @@ tcp_status prepare(const KernPair& kp) {
 // Instantiated configurations (k_slices, theta_stage, rows_per_thread).
 template <class TS, class TV>
 KernPair pick(const tcp_bp_config& c, bool check) {
+  if (c.kernel == 2) {  // FP32 slice pairs
+    if constexpr (std::is_same<TS, float>::value) {
+#define TCP_BP_CASE2(K, T, R) \
+  if (c.k_slices == K && c.theta_stage == T && c.rows_per_thread == R) return pick_check<TS, TV, K, T, R, 2>(check);
+      TCP_BP_CASE2(8, 16, 4)
+      TCP_BP_CASE2(16, 8, 4)
+      TCP_BP_CASE2(4, 16, 4)
+      TCP_BP_CASE2(8, 16, 8)
+#undef TCP_BP_CASE2
+    }
+    return {nullptr, nullptr, 0};
+  }
 #define TCP_BP_CASE(K, T, R) \
   if (c.k_slices == K && c.theta_stage == T && c.rows_per_thread == R) return pick_check<TS, TV, K, T, R>(check);
   TCP_BP_CASE(8, 16, 4)
@@ -666,7 +822,7 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
 }  // namespace
 
 bool valid_bp_config(const tcp_bp_config& c) {
-  if (c.kernel != 0 && c.kernel != 1) return false;
+  if (c.kernel < 0 || c.kernel > 2) return false;
   if (c.kernel == 1) return true;  // theta_stage 1 or 2 picks the stage size; the rest is ignored
   return pick<float, float>(c, false).direct != nullptr;
 }

@@ -20,8 +20,10 @@
 // would be down a column (one cache line per lane), so those angles read a
 // transposed copy volT[z][ix][iy] made once per call by a tiled transpose.
 // For FP32 volumes the slices are also interleaved in groups of 16
-// (volI[g][a][b][16], a row-major and a transposed copy), so that a hit reads
-// its 16 slices with four 16-byte loads instead of sixteen 4-byte ones.
+// (volI[g][a][q][b][4], slices 4q..4q+3 of voxel b adjacent; a row-major and a
+// transposed copy), so that a hit reads its 16 slices with four 16-byte loads
+// instead of sixteen 4-byte ones, while the lanes of a warp (neighbouring
+// voxels b) still read neighbouring 16-byte words.
 #include "tcp_internal.cuh"
 
 namespace tcp {
@@ -69,7 +71,7 @@ __global__ void k_transpose(const TV* vol, int64_t v_z, int64_t v_y, int n, TV* 
   }
 }
 
-// dst[g][a][b][0..16) = src[16 g + k][a][b] for slice groups g < G (FP32).
+// dst[g][a][q][b][r] = src[16 g + 4 q + r][a][b] for slice groups g < G (FP32).
 __global__ void k_interleave16(const float* src, int64_t s_z, int64_t s_row, int n, int G, float* dst) {
   const int64_t total = (int64_t)G * n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -77,12 +79,11 @@ __global__ void k_interleave16(const float* src, int64_t s_z, int64_t s_row, int
     const int64_t ab = e - (int64_t)g * n * n;
     const int a = (int)(ab / n), b = (int)(ab - (int64_t)a * n);
     const float* p = src + (int64_t)(16 * g) * s_z + (int64_t)a * s_row + b;
-    float v[16];
+    float4* q = reinterpret_cast<float4*>(dst) + ((int64_t)g * n + a) * 4 * n + b;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __ldg(p + (int64_t)k * s_z);
-    float4* q = reinterpret_cast<float4*>(dst + e * 16);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) q[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    for (int c = 0; c < 4; ++c)
+      q[(int64_t)c * n] = make_float4(__ldg(p + (int64_t)(4 * c) * s_z), __ldg(p + (int64_t)(4 * c + 1) * s_z),
+                                      __ldg(p + (int64_t)(4 * c + 2) * s_z), __ldg(p + (int64_t)(4 * c + 3) * s_z));
   }
 }
 
@@ -200,10 +201,10 @@ __global__ void __launch_bounds__(kPjThreads) k_project_i16(PjArgs a) {
       if (i == j) wt = WRound<TS>::r(1.f - w);
       else if (i + 1 == j) wt = WRound<TS>::r(w);
       if (wt != 0.f) {
-        const float4* p = reinterpret_cast<const float4*>(vol + ((int64_t)m * a.n + u) * 16);
+        const float4* p = reinterpret_cast<const float4*>(vol) + (int64_t)m * 4 * a.n + u;
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 v = __ldg(p + q4);
+          const float4 v = __ldg(p + (int64_t)q4 * a.n);
           acc[4 * q4] = __fmaf_rn(wt, v.x, acc[4 * q4]);
           acc[4 * q4 + 1] = __fmaf_rn(wt, v.y, acc[4 * q4 + 1]);
           acc[4 * q4 + 2] = __fmaf_rn(wt, v.z, acc[4 * q4 + 2]);

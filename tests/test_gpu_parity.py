@@ -110,6 +110,43 @@ def test_backproject_register_reuse_blocks(nz, nt, nd, n, center):
     assert tcp.device_check() == 0
 
 
+@pytest.mark.parametrize("cfg", [(8, 16, 4), (16, 8, 4), (4, 16, 4), (8, 16, 8)])
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (11, 181, 203, 200, 101.37), (3, 64, 96, 96, 48.0), (1, 7, 33, 70, 20.5), (17, 37, 64, 33, 31.9)])
+def test_backproject_slice_pairs(cfg, nz, nt, nd, n, center):
+    # kernel 2: FP32 slice pairs with packed FMAs and sample reuse down each
+    # column (checked mode is on: a floor step other than 0 or +1 along the
+    # walk sets the error word); odd slice counts leave half a pair
+    q, theta, c = _bp_case(nz, nt, nd, n, center, nz * 1000 + nt)
+    ref = oracle.backproject(q, theta, c, n)
+    try:
+        tcp.set_backproject_config(*cfg, kernel=2)
+        got = host(tcp.backproject(to_dev(q), theta, c, n=n))
+        got16 = host(tcp.backproject(to_dev(q), theta, c, n=n, dtype=torch.float16))
+    finally:
+        tcp.set_backproject_config(None)
+    assert rel(got, ref) <= 1e-5
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert rel(got16, ref) <= 5e-3
+    assert tcp.device_check() == 0
+
+
+def test_backproject_slice_pairs_special_angles():
+    # sin exactly 0, +-1, +-1/sqrt(2) and just inside / outside the 0.99 reuse bound
+    q, _, c = _bp_case(6, 18, 80, 72, 40.25, 9)
+    th = np.array([0.0, np.pi / 4, np.pi / 2, 3 * np.pi / 4, np.pi, 5 * np.pi / 4, 3 * np.pi / 2, 7 * np.pi / 4,
+                   np.arcsin(0.99) - 1e-6, np.arcsin(0.99) + 1e-6, np.pi - np.arcsin(0.99), -np.arcsin(0.99) + 1e-7,
+                   1e-7, np.pi / 2 + 1e-7, -np.pi / 4, 3.9269, 1.4, -1.4])
+    ref = oracle.backproject(q, th, c, 72)
+    try:
+        tcp.set_backproject_config(8, 16, 4, kernel=2)
+        got = host(tcp.backproject(to_dev(q), th, c, n=72))
+    finally:
+        tcp.set_backproject_config(None)
+    assert rel(got, ref) <= 1e-5
+    assert tcp.device_check() == 0
+
+
 def test_backproject_register_reuse_axis_aligned_and_diagonal_angles():
     # slopes of exactly 0, +-1/sqrt(2) and +-1 sit on the walk-axis switch
     q, _, c = _bp_case(5, 16, 80, 72, 40.25, 9)
