@@ -216,7 +216,6 @@ FOURIERREC = {"f32_frec": 7, "f16_frec": 5}  # path -> window width
 PROFILED_TRAFFIC = {
     "f32": ((256, 2048, 2048), 561.5e9 + 4.30e9, "profiles/k_backproject_tc_split_f32_2048sq_256slices.md"),
     "f16": ((256, 2048, 2048), 622.5e9 + 2.15e9, "profiles/k_backproject_tc_f16_2048sq_256slices.md"),
-    "f32_cuda": ((32, 2048, 2048), 8.01e9 + 0.53e9, "profiles/k_backproject_f32_2048sq_32slices.md"),
 }
 
 
@@ -270,7 +269,10 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     traffic, tsrc = _traffic(path, nz, nt, n)
     sd = "f16x2" if split else getattr(torch, sdt or vdt)
     kernel = tcp.get_backproject_config(nz, nt, n, n, sd, getattr(torch, vdt))[3]
-    per_clk = 16 if (sdt or vdt) == "float32" else 32
+    # shared-memory roof: 8 B per interpolation for FP32 samples (16 interp/clk),
+    # 4 B for 16-bit sample pairs and for the FP32 slice-pair form with its
+    # sample reuse (32 interp/clk)
+    per_clk = 16 if (sdt or vdt) == "float32" and kernel != 2 else 32
     smem_roof = sms * per_clk * clk_max * 1e6
     out = {"bound": "alu", "achieved": ach / 1e9, "peak": fma_ceiling / 1e9, "unit": "Ginterp/s",
            "frac": ach / fma_ceiling, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
@@ -293,7 +295,8 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
                                  "(MEASURED_PEAKS.json, of measured); 30 of the 32 weights in each operand row are "
                                  "zero" % fl})
     else:
-        out.update({"kernel": "k_backproject (LineRec, %s storage)" % (sdt or vdt),
+        out.update({"kernel": "k_backproject (LineRec, %s storage%s)" % (
+                        sdt or vdt, ", FP32 slice pairs, packed FMAs, sample reuse down columns" if kernel == 2 else ""),
                     "smem_roof_ginterp_s": smem_roof / 1e9, "frac_of_smem_roof": ach / smem_roof,
                     "smem_basis": "shared-memory pipe: %d SMs x %d interp/clk x %.0f MHz" % (sms, per_clk, clk_max)})
     return out

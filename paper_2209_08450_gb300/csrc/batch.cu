@@ -22,11 +22,11 @@ namespace tcp {
 namespace {
 
 // CUDA-core configurations (rows_per_thread 16: 4 x 4 voxel blocks, FP32
-// sinograms only), then the tensor-core kernel with 1 or 2 angles per stage
-// (16-bit sinograms whose strides suit TMA).
+// sinograms only), the FP32 slice-pair form (kernel 2), then the tensor-core
+// kernel with 1 or 2 angles per stage (16-bit sinograms whose strides suit TMA).
 const tcp_bp_config kCandidates[] = {{8, 16, 4, 0}, {4, 32, 4, 0}, {4, 16, 4, 0}, {16, 8, 2, 0}, {8, 16, 2, 0},
                                      {2, 16, 4, 0}, {1, 32, 4, 0}, {4, 16, 16, 0}, {8, 16, 16, 0}, {4, 32, 16, 0},
-                                     {8, 2, 4, 1}, {8, 1, 4, 1}};
+                                     {8, 16, 4, 2}, {16, 8, 4, 2}, {4, 16, 4, 2}, {8, 2, 4, 1}, {8, 1, 4, 1}};
 
 int esize(int dt) { return dt == TCP_F32 ? 4 : 2; }
 
@@ -399,6 +399,7 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
     const bool f32 = sino->dtype == TCP_F32;
     if (c.kernel == 1 && f32) continue;                          // tensor cores: 16-bit sinograms
     if (c.kernel == 0 && c.rows_per_thread == 16 && !f32) continue;  // 4 x 4 blocks: FP32 sinograms
+    if (c.kernel == 2 && !f32) continue;                         // slice pairs: FP32 sinograms
     cands.push_back(c);
   }
   for (const tcp_bp_config& c : cands) {

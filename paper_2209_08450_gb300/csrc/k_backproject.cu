@@ -858,6 +858,9 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
   if (nz <= 1) c = tcp_bp_config{1, 32, 4, 0};
   else if (nz <= 2) c = tcp_bp_config{2, 16, 4, 0};
   else if (nz <= 4) c = tcp_bp_config{4, 16, 4, 0};
+  // FP32 sinograms: the slice-pair form (1.21x the one-column-per-lane form at
+  // 2048^2 x 32 slices x 2048 angles)
+  if (sdt == TCP_F32 && nz >= 3) c = tcp_bp_config{nz >= 5 ? 8 : 4, 16, 4, 2};
   // 16-bit sinograms with enough slices to fill the MMA's N dimension go to
   // the tensor cores (inputs whose strides do not suit TMA fall back).
   if ((sdt == TCP_F16 || sdt == TCP_BF16) && nz >= 32) c.kernel = 1;
