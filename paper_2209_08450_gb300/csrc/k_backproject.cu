@@ -565,16 +565,21 @@ __device__ __forceinline__ void bp_tile_f32_pairs(const BpArgs& a, int gx, int g
     const int b = s & 1, t0 = s * T, nt = min(T, a.ntheta - t0);
     float* wb = win + b * (T * K * kWin);
     const int* ws = wst + (s % 3) * T;
-    for (int e = threadIdx.x; e < nt * K * kWin; e += NT) {
-      const int h = e & 1;
-      int rest = e >> 1;
-      const int i = rest % kWin;
-      rest /= kWin;
-      const int pp = rest % KP, t = rest / KP;
-      const int z = z0 + 2 * pp + h, j = ws[t] + i;
-      const bool ok = z < a.nz && j >= 0 && j < a.ndet;
-      const float* src = ok ? sino + (int64_t)z * a.s_z + (int64_t)(t0 + t) * a.s_t + j : sino;
-      cp_async4(wb + e, src, ok);
+    // one row (t, p) of 2 WIN floats per warp step: lane copies floats
+    // lane, lane + 32, lane + 64 (sample i = f / 2 of slice 2p + f % 2)
+    for (int row = warp; row < nt * KP; row += NW) {
+      const int t = row / KP, pp = row - t * KP;
+      const int64_t rbase = (int64_t)(t0 + t) * a.s_t;
+      float* dst = wb + row * (2 * kWin);
+#pragma unroll
+      for (int c = 0; c < (2 * kWin) / 32; ++c) {
+        const int f = lane + 32 * c;
+        const int h = f & 1, i = f >> 1;
+        const int z = z0 + 2 * pp + h, j = ws[t] + i;
+        const bool ok = z < a.nz && j >= 0 && j < a.ndet;
+        const float* src = ok ? sino + (int64_t)z * a.s_z + rbase + j : sino;
+        cp_async4(dst + f, src, ok);
+      }
     }
     cp_async_commit();
   };
