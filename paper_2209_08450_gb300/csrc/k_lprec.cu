@@ -33,10 +33,9 @@
 // z1 = sqrt(3) - 2, |m| <= 24 (the omitted tail is below 3e-14 relative;
 // every prefiltered signal carries 24 zero samples on each side, as the
 // reference's finite system does).  Step (2), the dominant one, runs with one
-// thread per (psi column, run of 32 rho rows, pair of slices): per angle it
-// reads the (base, weights) pair of its column once and slides a 4-sample
-// register window down G's coefficient column, whose two slices sit side by
-// side: 35 eight-byte loads and 128 packed fma.rn.f32x2 (256 FMAs) per angle.
+// thread per (psi column, run of 32 rho rows): per angle it reads the
+// (base, weights) pair of its column once and slides a 4-sample register
+// window down G's coefficient column: 35 loads and 128 FMAs per angle.
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -134,79 +133,56 @@ __global__ void k_lp_g(LpSpanDev sp, const float* C, int64_t c_z, int64_t c_t, i
     s[k] = v;
   }
   __syncthreads();
-  // slice pairs interleaved: G[z / 2][u][k][z % 2]
-  float* out = G + (z >> 1) * g_z + ((int64_t)u * sp.L) * 2 + (z & 1);
-  for (int k = threadIdx.x; k < sp.L; k += blockDim.x) out[2 * k] = fir_at(s, sp.L, k);
-}
-
-__device__ __forceinline__ unsigned long long lp_pack2(float x, float y) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-  return r;
-}
-__device__ __forceinline__ void lp_ffma2(unsigned long long& acc, unsigned long long w, unsigned long long x) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(x));
+  float* out = G + z * g_z + (int64_t)u * sp.L;
+  for (int k = threadIdx.x; k < sp.L; k += blockDim.x) out[k] = fir_at(s, sp.L, k);
 }
 
 // Step (2): F[z][24 + i][24 + k] = sum_u sum_d w_d(r) G[z][u][i + base(r) + d],
-// r = k - p u + p (nu - 1).  Thread: one column k, rows i0 .. i0 + 31, one
-// pair of slices (G holds them interleaved, so one 8-byte load fetches a
-// sample of both and one fma.rn.f32x2 accumulates both).
-__global__ void __launch_bounds__(256) k_lp_span(LpSpanDev sp, const float* G, int64_t g_z, float* F, int64_t f_z,
-                                                 int zc) {
+// r = k - p u + p (nu - 1).  Thread: one column k, rows i0 .. i0 + 31.
+__global__ void __launch_bounds__(256) k_lp_span(LpSpanDev sp, const float* G, int64_t g_z, float* F, int64_t f_z) {
   const int k = blockIdx.x * 32 + (threadIdx.x & 31);
   const int i0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * kRun;
-  const int zp = blockIdx.z;  // slice pair
+  const int z = blockIdx.z;
   if (k >= sp.npsi || i0 >= sp.nrho) return;
-  const unsigned long long* Gz = reinterpret_cast<const unsigned long long*>(G + zp * g_z);
-  unsigned long long acc[kRun];
+  const float* Gz = G + z * g_z;
+  float acc[kRun];
 #pragma unroll
-  for (int ii = 0; ii < kRun; ++ii) acc[ii] = 0ull;
+  for (int ii = 0; ii < kRun; ++ii) acc[ii] = 0.f;
   const int rofs = k + sp.p * (sp.nu - 1);
   for (int u = 0; u < sp.nu; ++u) {
     const int r = rofs - sp.p * u;
     const int base = __ldg(sp.dbase + r);
     const float4 w = __ldg(sp.dw + r);
-    const unsigned long long w0 = lp_pack2(w.x, w.x), w1 = lp_pack2(w.y, w.y), w2 = lp_pack2(w.z, w.z),
-                             w3 = lp_pack2(w.w, w.w);
-    const unsigned long long* g = Gz + (int64_t)u * sp.L;
+    const float* g = Gz + (int64_t)u * sp.L;
     const int lo = i0 + base;
     if (lo >= 0 && lo + kRun + 3 <= sp.L) {
-      unsigned long long a0 = __ldg(g + lo), a1 = __ldg(g + lo + 1), a2 = __ldg(g + lo + 2);
+      float a0 = __ldg(g + lo), a1 = __ldg(g + lo + 1), a2 = __ldg(g + lo + 2);
 #pragma unroll
       for (int ii = 0; ii < kRun; ++ii) {
-        const unsigned long long a3 = __ldg(g + lo + ii + 3);
-        lp_ffma2(acc[ii], w0, a0);
-        lp_ffma2(acc[ii], w1, a1);
-        lp_ffma2(acc[ii], w2, a2);
-        lp_ffma2(acc[ii], w3, a3);
+        const float a3 = __ldg(g + lo + ii + 3);
+        acc[ii] = __fmaf_rn(w.w, a3, __fmaf_rn(w.z, a2, __fmaf_rn(w.y, a1, __fmaf_rn(w.x, a0, acc[ii]))));
         a0 = a1;
         a1 = a2;
         a2 = a3;
       }
     } else {  // near the ends of G: zero outside [0, L)
-#pragma unroll
+#pragma unroll 4
       for (int ii = 0; ii < kRun; ++ii) {
-        const int idx = lo + ii;
-        if (idx >= 0 && idx < sp.L) lp_ffma2(acc[ii], w0, __ldg(g + idx));
-        if (idx + 1 >= 0 && idx + 1 < sp.L) lp_ffma2(acc[ii], w1, __ldg(g + idx + 1));
-        if (idx + 2 >= 0 && idx + 2 < sp.L) lp_ffma2(acc[ii], w2, __ldg(g + idx + 2));
-        if (idx + 3 >= 0 && idx + 3 < sp.L) lp_ffma2(acc[ii], w3, __ldg(g + idx + 3));
+        float v = 0.f;
+        const float wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const int idx = lo + ii + d;
+          if (idx >= 0 && idx < sp.L) v = __fmaf_rn(wd[d], __ldg(g + idx), v);
+        }
+        acc[ii] += v;
       }
     }
   }
-  const int z0 = 2 * zp;
-  float* out0 = F + z0 * f_z + (int64_t)(kPad + i0) * sp.frow + kPad + k;
-  float* out1 = out0 + f_z;
-  const bool has1 = z0 + 1 < zc;
+  float* out = F + z * f_z + (int64_t)(kPad + i0) * sp.frow + kPad + k;
 #pragma unroll
   for (int ii = 0; ii < kRun; ++ii)
-    if (i0 + ii < sp.nrho) {
-      float lo_v, hi_v;
-      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo_v), "=f"(hi_v) : "l"(acc[ii]));
-      out0[(int64_t)ii * sp.frow] = lo_v;
-      if (has1) out1[(int64_t)ii * sp.frow] = hi_v;
-    }
+    if (i0 + ii < sp.nrho) out[(int64_t)ii * sp.frow] = acc[ii];
 }
 
 // Zero the 24-wide borders of the padded f grid [fcol][frow] of each slice.
@@ -456,7 +432,7 @@ size_t lprec_workspace_bytes(const LpHostGeom& g, int zpass) {
   for (int m = 0; m < 3; ++m) gmax = std::max(gmax, (size_t)g.span[m].nu * lp_L(g.span[m]) * 4);
   gmax = std::max<size_t>(gmax, (size_t)lp_frow(g.span[0]) * lp_fcol(g.span[0]) * 4);
   for (int m = 1; m < 3; ++m) gmax = std::max<size_t>(gmax, (size_t)lp_frow(g.span[m]) * lp_fcol(g.span[m]) * 4);
-  b += up256((size_t)(zpass + 1) * gmax);
+  b += up256((size_t)zpass * gmax);
   b += up256((size_t)zpass * g.nt * (g.nd + 2 * kPad) * 4);
   return b;
 }
@@ -511,7 +487,7 @@ tcp_status launch_lprec_ws(const View3& sv, const LpHostGeom& g, const LpDevGeom
     gmax = std::max<size_t>(gmax, (size_t)fz[m] * 4);
   }
   float* Gbuf = (float*)p;  // G coefficients, then the row-filtered f of one span
-  p += up256((size_t)(zpass + 1) * gmax);
+  p += up256((size_t)zpass * gmax);
   const int clen = (int)nd + 2 * kPad;
   float* C = (float*)p;
   // step (4) geometry (FP64, once per call)
@@ -563,15 +539,14 @@ tcp_status launch_lprec_ws(const View3& sv, const LpHostGeom& g, const LpDevGeom
       // (1)
       const size_t smg = sizeof(float) * sp.L;
       cudaFuncSetAttribute(k_lp_g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
-      const int64_t g_z = (int64_t)sp.nu * sp.L * 2;  // floats per slice pair
-      const int npair = (zc + 1) / 2;
+      const int64_t g_z = (int64_t)sp.nu * sp.L;
       k_lp_g<<<dim3((unsigned)sp.nu, (unsigned)zc), 256, smg, st>>>(sp, C, (int64_t)nt * clen, clen, clen, Gbuf,
                                                                      g_z);
       TCP_CUDA_TRY(cudaGetLastError());
       // (2)
       k_lp_border<<<dim3(256, (unsigned)zc), 256, 0, st>>>(Fm[m], fz[m], sp.nrho, sp.npsi, sp.frow, sp.fcol);
-      dim3 gs((unsigned)((sp.npsi + 31) / 32), (unsigned)((sp.nrho + 8 * kRun - 1) / (8 * kRun)), (unsigned)npair);
-      k_lp_span<<<gs, 256, 0, st>>>(sp, Gbuf, g_z, Fm[m], fz[m], zc);
+      dim3 gs((unsigned)((sp.npsi + 31) / 32), (unsigned)((sp.nrho + 8 * kRun - 1) / (8 * kRun)), (unsigned)zc);
+      k_lp_span<<<gs, 256, 0, st>>>(sp, Gbuf, g_z, Fm[m], fz[m]);
       TCP_CUDA_TRY(cudaGetLastError());
       // (3): rows into the scratch buffer, columns back into Fm
       const size_t smr = sizeof(float) * sp.frow;
