@@ -360,21 +360,29 @@ __device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, con
 constexpr float kCoopRadius = 384.f;
 constexpr int kTile = 64;  // nodes per CTA tile side
 
+// CTAs run in the order of `order`: tiles sorted by their distance from the
+// zero frequency (nearest first), every slice pair of a tile in a row.  Near
+// the origin every angle contributes and a tile takes many times the work of
+// an outer one; started last, those tiles left most SMs idle at the end of
+// the launch.
 template <int R, int CW>
 __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __restrict__ P, int64_t p_pair, int ms,
                                                      const float4* __restrict__ geomS, const int2* __restrict__ meta,
                                                      const float* __restrict__ thS, int nt, int M, int lgL, float bl2,
-                                                     float2* __restrict__ G, int64_t g_pair) {
+                                                     float2* __restrict__ G, int64_t g_pair,
+                                                     const int2* __restrict__ order, int nb) {
   const int L = 1 << lgL;
-  const int pb = blockIdx.z;
+  const int rank = (int)(blockIdx.x / (unsigned)nb);
+  const int pb = (int)(blockIdx.x - (unsigned)rank * (unsigned)nb);
+  const int2 tile = __ldg(order + rank);
   const float2* Pp = P + (int64_t)pb * p_pair;
   float2* Gp = G + (int64_t)pb * g_pair;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // warp tile: 8 blocks across (8 CW columns), 4 blocks down (4 R rows)
   constexpr int kWarpCols = 8 * CW, kWarpRows = 4 * R;
   constexpr int kWarpsX = kTile / kWarpCols;
-  const int tx0 = blockIdx.x * kTile + (wid % kWarpsX) * kWarpCols;
-  const int ty0 = blockIdx.y * kTile + (wid / kWarpsX) * kWarpRows;
+  const int tx0 = tile.x * kTile + (wid % kWarpsX) * kWarpCols;
+  const int ty0 = tile.y * kTile + (wid / kWarpsX) * kWarpRows;
   const int gx0 = tx0 + (lane & 7) * CW, gy0 = ty0 + (lane >> 3) * R;
   const bool own = gx0 < L && gy0 < L;
   auto reachable = [&](int b0, int ext) { return !(2 * (b0 + ext - 1) <= -L - W || 2 * b0 >= L + W); };
@@ -516,6 +524,7 @@ struct HostTables {
   std::map<std::pair<int, int>, float2*> tw;                 // (dev, N) -> e^{-2 pi i j / N}
   std::map<std::tuple<int, int, int, int>, float*> dec;      // (dev, n, L, W) -> 1 / Phi(x / L)
   std::map<int, std::vector<SortedAngles>> ang;              // dev -> angle arrays seen
+  std::map<std::pair<int, int>, int2*> order;                // (dev, L) -> gather tile order
 };
 std::mutex g_frec_mu;
 HostTables g_frec;
@@ -674,11 +683,32 @@ void launch_rows(const View3& sv, int z0, int nb, int lgM, const float2* twM, co
 
 template <int R, int CW>
 void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4* geomS, const int2* meta,
-                   const float* thS, int nt, int M, int lgL, float2* G, int64_t g_pair, int nb, cudaStream_t st) {
+                   const float* thS, int nt, int M, int lgL, float2* G, int64_t g_pair, int nb, const int2* order,
+                   cudaStream_t st) {
   const int L = 1 << lgL;
   const unsigned tiles = (unsigned)((L + kTile - 1) / kTile);
-  k_frec_gather<R, CW><<<dim3(tiles, tiles, (unsigned)nb), 256, 0, st>>>(W, P, p_pair, ms, geomS, meta, thS, nt, M,
-                                                                        lgL, (float)(es_beta(W) / M_LN2), G, g_pair);
+  k_frec_gather<R, CW><<<dim3(tiles * tiles * (unsigned)nb), 256, 0, st>>>(
+      W, P, p_pair, ms, geomS, meta, thS, nt, M, lgL, (float)(es_beta(W) / M_LN2), G, g_pair, order, nb);
+}
+
+// Gather tiles of an L x L grid, nearest to the zero frequency (node 0 and
+// its image at L) first.
+std::vector<int2> gather_tile_order(int L) {
+  const int tiles = (L + kTile - 1) / kTile;
+  std::vector<std::pair<double, int2>> v;
+  v.reserve((size_t)tiles * tiles);
+  for (int ty = 0; ty < tiles; ++ty)
+    for (int tx = 0; tx < tiles; ++tx) {
+      const double cx = tx * kTile + 0.5 * kTile, cy = ty * kTile + 0.5 * kTile;
+      const double dx = std::min(cx, L - cx), dy = std::min(cy, L - cy);
+      v.push_back({dx * dx + dy * dy, make_int2(tx, ty)});
+    }
+  std::stable_sort(v.begin(), v.end(), [](const std::pair<double, int2>& a, const std::pair<double, int2>& b) {
+    return a.first < b.first;
+  });
+  std::vector<int2> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].second;
+  return out;
 }
 
 void launch_cols(const float2* G, int64_t g_pair, int lgL, int n, const float2* twL, const float* dec, float2* H,
@@ -709,6 +739,8 @@ void fourierrec_cache_clear() {
   g_frec.tw.clear();
   for (auto& kv : g_frec.dec) cudaFree(kv.second);
   g_frec.dec.clear();
+  for (auto& kv : g_frec.order) cudaFree(kv.second);
+  g_frec.order.clear();
   for (auto& kv : g_frec.ang)
     for (auto& e : kv.second) {
       cudaFree(e.meta);
@@ -788,6 +820,22 @@ tcp_status fourierrec_tables_cached(const double* theta, int64_t nt, int64_t nd,
   if ((s = get_twiddles(dev, 1 << lgM, &t->twM)) != TCP_OK) return s;
   if ((s = get_twiddles(dev, 1 << lgL, &t->twL)) != TCP_OK) return s;
   if ((s = get_deconv(dev, (int)n, 1 << lgL, width, &t->dec)) != TCP_OK) return s;
+  {
+    std::lock_guard<std::mutex> lk(g_frec_mu);
+    auto it = g_frec.order.find({dev, 1 << lgL});
+    if (it == g_frec.order.end()) {
+      const std::vector<int2> h = gather_tile_order(1 << lgL);
+      int2* d = nullptr;
+      TCP_CUDA_TRY(cudaMalloc(&d, h.size() * sizeof(int2)));
+      const cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(int2), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "upload FourierRec tile order");
+      }
+      it = g_frec.order.emplace(std::make_pair(dev, 1 << lgL), d).first;
+    }
+    t->order = it->second;
+  }
   return get_sorted_angles(dev, theta, (int)nt, &t->meta, &t->thS);
 }
 
@@ -823,6 +871,8 @@ tcp_status fourierrec_tables_owned(const double* theta, int64_t nt, int64_t nd, 
   std::vector<float> ht;
   sort_angles(theta, (int)nt, &hm, &ht);
   if ((s = upload(hm.data(), hm.size() * sizeof(int2), (const void**)&t->meta)) != TCP_OK) return s;
+  const std::vector<int2> ho = gather_tile_order(1 << lgL);
+  if ((s = upload(ho.data(), ho.size() * sizeof(int2), (const void**)&t->order)) != TCP_OK) return s;
   return upload(ht.data(), ht.size() * sizeof(float), (const void**)&t->thS);
 }
 
@@ -859,7 +909,7 @@ tcp_status launch_fourierrec_ws(const View3& sv, const FrecTables& tb, const Fre
     }
     TCP_CUDA_TRY(cudaGetLastError());
     launch_gather<4, 4>(width, (const float2*)w.P, p_pair, ms, (const float4*)w.geom, tb.meta, tb.thS, nt, M, lgL,
-                        (float2*)w.G, g_pair, b, st);
+                        (float2*)w.G, g_pair, b, tb.order, st);
     TCP_CUDA_TRY(cudaGetLastError());
     launch_cols((const float2*)w.G, g_pair, lgL, n, tb.twL, tb.dec, (float2*)w.H, h_pair, b, st);
     TCP_CUDA_TRY(cudaGetLastError());

@@ -192,6 +192,7 @@ struct FrecTables {
   const float* dec = nullptr;
   const int2* meta = nullptr;
   const float* thS = nullptr;
+  const int2* order = nullptr;  // gather tiles, nearest to the zero frequency first
 };
 struct FrecWorkspace {
   void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
