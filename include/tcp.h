@@ -307,7 +307,7 @@ tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double ce
 tcp_status tcp_lprec(const tcp_tensor* sino, const double* theta, double center, tcp_tensor* vol, double scale,
                      double oversampling, void* stream);
 
-/* Backprojector launch configuration./* Backprojector launch configuration.  k_slices: slices per thread block
+/* Backprojector launch configuration.  k_slices: slices per thread block
  * (1, 2, 4, 8 or 16); theta_stage: angles staged in shared memory per step
  * (8, 16 or 32); rows_per_thread: voxels per thread (2 or 4).
  * kernel: 0 = FP32 pipes (every dtype; rows_per_thread 16 on FP32 sinograms:

@@ -277,7 +277,7 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
     if (e != cudaSuccess) { s = cuda_fail(e, "batch: cudaMalloc"); break; }
     b->owned.push_back(w);
     it.sino.p = w; it.sino.dtype = b->sdt; it.sino.d0 = nz; it.sino.d1 = nt; it.sino.d2 = nd;
-    it.sino.s0 = nt * nd; it.sino.s1 = nd;
+    it.sino.s0 = nd; it.sino.s1 = nz * nd;  // angle-major storage, as in tcp_fbp's chunks
     // the batch owns its tables, so that its captured graph never depends on
     // the library's bounded caches
     if ((s = build_trig_owned(in.theta, nt, &b->owned, &it.trig)) != TCP_OK) break;

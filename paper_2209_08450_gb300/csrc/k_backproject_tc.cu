@@ -77,6 +77,8 @@ struct TcArgs {
   uint32_t* err;
   int check;
   int na, nbb;  // A and B ring depths (stages)
+  int vec4;     // FP32 volume with 16-byte aligned rows: 16-byte stores in the epilogue
+  int zfirst;   // tensor map dimensions (sample, slice, angle) instead of (sample, angle, slice)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -229,9 +231,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int kParts = SPLIT ? 2 : 1;
+  // Split mode swaps the operands: the sinogram rows (slices) are the MMA's
+  // M side and both weight halves its N = 256 side, so one MMA covers the
+  // whole tile and each K step reads 12 KB of operands instead of 16 KB.
+  // Its sinogram stages then hold 128 rows whatever N is (rows past N are
+  // never copied; their results are never stored).
+  constexpr bool SWAP = SPLIT;
   const int N = a.N;
-  const int bBytes = N * kTcRowBytes;  // B bytes per angle and plane
-  const int angleB = kParts * bBytes;  // B bytes per angle
+  const int rowsB = SWAP ? kTcM : N;       // sinogram rows per angle and plane in shared memory
+  const int bBytes = rowsB * kTcRowBytes;  // B bytes per angle and plane
+  const int angleB = kParts * bBytes;      // B bytes per angle
+  const int txB = kParts * N * kTcRowBytes;  // bytes the copies of one angle deliver
   constexpr int angleA = kParts * kTcAngleA;
   unsigned char* Abuf = smem;
   const int NA = a.na, NBB = a.nbb;  // ring depths (stages)
@@ -252,7 +262,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   const int gx = sub_x >> 1, gy = sub_y >> 1;
   const int ox = (sub_x & 1) * 16, oy = (sub_y & 1) * 16;
   // columns: [accumulator half 0][half 1], then in split mode [sum 0][sum 1]
-  const int ncols = (SPLIT ? 2 : 1) * kTcH * N;
+  const int colsH = SWAP ? kTcM : N;  // accumulator columns per half
+  const int ncols = (SPLIT ? 2 : 1) * kTcH * colsH;
   const uint32_t tmem_cols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
   const int nstages = (a.ntheta + kTcS2 - 1) / kTcS2;
 
@@ -311,13 +322,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
         if (lane == 0) {
           mbar_arrive(smem_u32(&bars->geo_full[ib]));
           const uint32_t fb = smem_u32(&bars->full[ib]);
-          mbar_expect_tx(fb, (uint32_t)(nt * angleB));
+          mbar_expect_tx(fb, (uint32_t)(nt * txB));
           for (int t = 0; t < nt; ++t) {
             const int th = s * kTcS2 + t;
             const int jb = geo[th % kTcGeoRing].bj >> 16;
             unsigned char* dst = Bbuf + (ib * kTcS2 + t) * angleB;
-            tma_load_3d(smem_u32(dst), &tmap, fb, jb, th, z0);
-            if (SPLIT) tma_load_3d(smem_u32(dst + bBytes), &tmap_lo, fb, jb, th, z0);
+            const int cy = a.zfirst ? z0 : th, cz = a.zfirst ? th : z0;
+            tma_load_3d(smem_u32(dst), &tmap, fb, jb, cy, cz);
+            if (SPLIT) tma_load_3d(smem_u32(dst + bBytes), &tmap_lo, fb, jb, cy, cz);
           }
         }
         __syncwarp();
@@ -356,13 +368,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-                for (int pr = 0; pr < (SPLIT ? 3 : 1); ++pr)  // (A_hi,B_hi), (A_hi,B_lo), (A_lo,B_hi)
+                for (int pr = 0; pr < (SPLIT ? 3 : 1); ++pr) {  // (W_hi,q_hi), (W_hi,q_lo), (W_lo,q_hi)
+                  const uint64_t dq = dB + (uint32_t)(t * bAngle + (pr == 1 ? bPlane : 0u) + ((32 * kk) >> 4));
+                  if (SWAP) {  // D[slice][voxel] = q (M = 128) x W^T (N = 256)
+                    mma_f16(tmem_d, dq, dA + (uint32_t)((t * angleA + (pr == 2 ? kTcAngleA : 0) + 32 * kk) >> 4),
+                            a.idesc, (seg0 && (t | kk | pr) == 0) ? 0u : 1u);
+                  } else {  // D[voxel][slice] = W (M = 128 per half) x q^T (N slices)
 #pragma unroll
-                  for (int h = 0; h < kTcH; ++h)
-                    mma_f16(tmem_d + (uint32_t)(h * N),
-                            dA + (uint32_t)((t * angleA + (pr == 2 ? kTcAngleA : 0) + h * kTcHalfA + 32 * kk) >> 4),
-                            dB + (uint32_t)(t * bAngle + (pr == 1 ? bPlane : 0u) + ((32 * kk) >> 4)), a.idesc,
-                            (seg0 && (t | kk | pr) == 0) ? 0u : 1u);
+                    for (int h = 0; h < kTcH; ++h)
+                      mma_f16(tmem_d + (uint32_t)(h * N),
+                              dA + (uint32_t)((t * angleA + (pr == 2 ? kTcAngleA : 0) + h * kTcHalfA + 32 * kk) >> 4),
+                              dq, a.idesc, (seg0 && (t | kk | pr) == 0) ? 0u : 1u);
+                  }
+                }
             }
           }
           mma_commit(smem_u32(&bars->empty[ib]));
@@ -432,15 +450,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
           if (!wait_or_abort(smem_u32(&bars->seg_done), (uint32_t)(k & 1), abort, a.err)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-          for (int c0 = 0; c0 < N; c0 += 16) {
+          for (int c0 = 0; c0 < colsH; c0 += 16) {
             uint32_t acc[16], sum[16];
-            tmem_ld16(tmem_d + lanes + (uint32_t)(h * N + c0), acc);
-            if (k > 0) tmem_ld16(tmem_d + lanes + (uint32_t)(kTcH * N + h * N + c0), sum);
+            tmem_ld16(tmem_d + lanes + (uint32_t)(h * colsH + c0), acc);
+            if (k > 0) tmem_ld16(tmem_d + lanes + (uint32_t)(kTcH * colsH + h * colsH + c0), sum);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int q = 0; q < 16; ++q)
               sum[q] = k > 0 ? __float_as_uint(__fadd_rn(__uint_as_float(sum[q]), __uint_as_float(acc[q]))) : acc[q];
-            tmem_st16(tmem_d + lanes + (uint32_t)(kTcH * N + h * N + c0), sum);
+            tmem_st16(tmem_d + lanes + (uint32_t)(kTcH * colsH + h * colsH + c0), sum);
           }
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -465,7 +483,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   if (live_tile && warp < kTcBuilders) {
     bool ok = !*abort && wait_or_abort(smem_u32(&bars->done), 0, abort, a.err);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+    if (ok && SWAP) {
+      // TMEM lane = slice, column = voxel (half h: columns 128 h ..): warp w
+      // reads slices 32 (w % 4) .. and the voxels of half w / 4, 16 columns
+      // (one row of 16 voxels) at a time
+      const int h = warp >> 2, zl = (warp & 3) * 32 + lane;
+      const int z = z0 + zl;
+      const bool zin = zl < N && z < a.nz;
+      const bool add_sums = (nstages + kTcSeg - 1) / kTcSeg > 1;
+      const int ix0 = gx * kTile + ox;
+      for (int c0 = 0; c0 < kTcM; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem_d + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * kTcM + c0);
+        tmem_ld16(taddr, r);
+        if (add_sums) {
+          uint32_t sm[16];
+          tmem_ld16(taddr + (uint32_t)(kTcH * kTcM), sm);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) r[q] = __float_as_uint(__fadd_rn(__uint_as_float(sm[q]), __uint_as_float(r[q])));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int iy = gy * kTile + oy + 8 * h + (c0 >> 4);
+        if (zin && iy < a.n) {
+          const int64_t off = (int64_t)z * a.v_z + (int64_t)iy * a.v_y + ix0;
+          if (a.vdt == TCP_F32 && ix0 + 16 <= a.n && a.vec4) {
+            float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(a.vol) + off);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(__uint_as_float(r[4 * q]) * a.scale, __uint_as_float(r[4 * q + 1]) * a.scale,
+                                   __uint_as_float(r[4 * q + 2]) * a.scale, __uint_as_float(r[4 * q + 3]) * a.scale);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              if (ix0 + q < a.n) {
+                const float v = __uint_as_float(r[q]) * a.scale;
+                if (a.vdt == TCP_F32) put<float>(a.vol, off + q, v);
+                else if (a.vdt == TCP_F16) put<__half>(a.vol, off + q, v);
+                else put<__nv_bfloat16>(a.vol, off + q, v);
+              }
+            }
+          }
+        }
+      }
+    } else if (ok) {
       // TMEM lane = voxel row of a half; warp w reads lanes 32 (w % 4) .. of half w / 4
       const int h = warp >> 2, m = tid & (kTcM - 1);
       const int ix = gx * kTile + ox + (m & 15), iy = gy * kTile + oy + 8 * h + (m >> 4);
@@ -578,9 +639,13 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   const bool split = sino.dtype == TCP_F16X2;
   const int N = tc_slices(nz, split);
   CUtensorMap map, map_lo;
-  const cuuint64_t dims[3] = {(cuuint64_t)nd, (cuuint64_t)nt, (cuuint64_t)nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)sino.s1 * 2, (cuuint64_t)sino.s0 * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kTcK, 1u, (cuuint32_t)N};
+  // The map's outer dimensions follow the memory order: an angle-major chunk
+  // ([angle][slice][sample], slice stride < angle stride) keeps the N rows of
+  // one copy within one angle's contiguous block instead of N slice planes.
+  const bool zfirst = sino.s0 < sino.s1;
+  const cuuint64_t dims[3] = {(cuuint64_t)nd, (cuuint64_t)(zfirst ? nz : nt), (cuuint64_t)(zfirst ? nt : nz)};
+  const cuuint64_t strides[2] = {(cuuint64_t)(zfirst ? sino.s0 : sino.s1) * 2, (cuuint64_t)(zfirst ? sino.s1 : sino.s0) * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)kTcK, zfirst ? (cuuint32_t)N : 1u, zfirst ? 1u : (cuuint32_t)N};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType tdt = sino.dtype == TCP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   for (int pl = 0; pl < (split ? 2 : 1); ++pl) {
@@ -608,17 +673,23 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   a.center = center;
   a.half_n = 0.5 * (double)n;
   a.scale = scale;
+  a.zfirst = zfirst ? 1 : 0;
+  a.vec4 = vol.dtype == TCP_F32 && (uintptr_t)vol.p % 16 == 0 && vol.s0 % 4 == 0 && vol.s1 % 4 == 0;
   // instruction descriptor: D FP32, A/B F16 or BF16, K-major, N >> 3, M >> 4
   const uint32_t fmt = sino.dtype == TCP_BF16 ? 1u : 0u;
-  a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  // split mode: M = 128 slices, N = 256 voxels (both halves); else M = 128
+  // voxels of one half, N = the CTA's slices
+  const uint32_t mmaN = split ? (uint32_t)(kTcH * kTcM) : (uint32_t)N;
+  a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((mmaN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   a.err = device_error_word();
   a.check = checked_mode() ? 1 : 0;
   // split mode: one angle per stage (its A and B are twice as large)
   const int S = (split || theta_stage == 1) ? 1 : 2;
   const int parts = split ? 2 : 1;
-  tc_rings(N, S, parts, &a.na, &a.nbb);
+  const int rowsB = split ? kTcM : N;  // sinogram rows per angle and plane in shared memory
+  tc_rings(rowsB, S, parts, &a.na, &a.nbb);
   if (a.nbb < 2) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
-  const size_t smem = tc_smem_bytes(N, S, parts, a.na, a.nbb);
+  const size_t smem = tc_smem_bytes(rowsB, S, parts, a.na, a.nbb);
   void (*k)(const CUtensorMap, const CUtensorMap, TcArgs) =
       split ? k_backproject_tc<__half, 1, true>
       : sino.dtype == TCP_F16

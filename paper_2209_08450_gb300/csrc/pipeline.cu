@@ -256,8 +256,13 @@ tcp_status fbp_run(const FbpParams& p, const FbpRes& r, const View3& dm, const V
     dv.p = (float*)dm.p + z0 * dm.s1; dv.d1 = c;
     fv.p = (float*)fm.p + z0 * fm.s1; fv.d1 = c;
     if (trace) TCP_CUDA_TRY(cudaEventRecord(ev(k, 2), st));
+    // the chunk sinogram is stored angle-major, [angle][slice][sample] (the
+    // order of the raw frames), and passed on as a [slice][angle][sample]
+    // view: one angle's rows of all the chunk's slices are then one
+    // contiguous block, which is what the tensor-core backprojector's copies
+    // (all slices of one angle's window at a time) read
     View3 sv;
-    sv.p = r.sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    sv.p = r.sino; sv.dtype = sdt; sv.d0 = c; sv.d1 = nt; sv.d2 = nd; sv.s0 = nd; sv.s1 = c * nd;
     sv.plane = sdt == TCP_F16X2 ? r.sino_cz * nt * nd : 0;
     TRY_S(launch_normalize_filter(rv, dv, fv, sv, r.ft, p.pad, st));
     if (host_raw) {
@@ -489,14 +494,14 @@ extern "C" tcp_status tcp_try_centers_ex(const tcp_tensor* raw, int64_t slice, c
     if ((s = get_filter_table(nd, filter, sscale, centers[k], &ft)) != TCP_OK) return s;
     View3 sv;
     sv.dtype = sdt;
-    sv.p = (char*)sino + (size_t)k * nt * nd * (sdt == TCP_F32 ? 4 : 2);
-    sv.d0 = 1; sv.d1 = nt; sv.d2 = nd; sv.s0 = nt * nd; sv.s1 = nd;
+    sv.p = (char*)sino + (size_t)k * nd * (sdt == TCP_F32 ? 4 : 2);  // angle-major stack
+    sv.d0 = 1; sv.d1 = nt; sv.d2 = nd; sv.s0 = ncenters * nd; sv.s1 = ncenters * nd;
     sv.plane = sdt == TCP_F16X2 ? plane : 0;
     TRY_S(launch_normalize_filter(rv, dv, fv, sv, ft, TCP_PAD_EDGE, st));
   }
   View3 stack;
   stack.p = sino; stack.dtype = sdt;
-  stack.d0 = ncenters; stack.d1 = nt; stack.d2 = nd; stack.s0 = nt * nd; stack.s1 = nd;
+  stack.d0 = ncenters; stack.d1 = nt; stack.d2 = nd; stack.s0 = nd; stack.s1 = ncenters * nd;
   stack.plane = sdt == TCP_F16X2 ? plane : 0;
   View3 vv;
   vv.p = vol->data; vv.dtype = vol->dtype; vv.d0 = ncenters; vv.d1 = n; vv.d2 = n;
