@@ -20,6 +20,13 @@
 //   D          two 128 x N FP32 accumulators in tensor memory (2N columns)
 //              for the whole angle loop; read back once with tcgen05.ld.
 //
+// Split mode (below) swaps the operands: D[z][v] = q W^T with the N = 128
+// sinogram rows as M and the 256 weight rows of both halves as N, one MMA
+// per K step.  The copy of one angle's window for all N slices reads one
+// contiguous block when the sinogram is stored angle-major ([theta][z][j],
+// the layout tcp_fbp's chunks use); the tensor map follows whichever of the
+// slice and angle strides is smaller.
+//
 // Pipeline per CTA: warp-specialised roles (weight builders, TMA producer,
 // MMA issuer) exchange stages of two angles through rings of shared buffers
 // guarded by mbarriers, so weight building, copies and MMAs overlap.
