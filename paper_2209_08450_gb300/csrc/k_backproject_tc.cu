@@ -612,11 +612,13 @@ size_t tc_smem_bytes(int N, int S, int parts, int na, int nbb) {
          (size_t)kTcGeoRing * sizeof(TcGeoP) + sizeof(TcBars);
 }
 
-// Ring depths for N slices and S angles per stage: NA = 3 (S = 1) or 2
-// (S = 2) weight buffers, then as many B buffers as fit (at most the
-// geometry ring's bound).
+// Ring depths for N slices and S angles per stage: NA weight buffers, 4 in
+// split mode (measured at 2048^2 x 256 slices x 2048 angles: 271, 258 and
+// 231 ms for NA = 2, 3, 4; the builders then run further ahead of the MMAs
+// and absorb the segment-sum pauses), else 3 (S = 1) or 2 (S = 2); then as
+// many B buffers as fit (at most the geometry ring's bound).
 void tc_rings(int N, int S, int parts, int* na, int* nbb) {
-  *na = (S == 1 && parts == 1) ? 3 : 2;
+  *na = parts == 2 ? 4 : ((S == 1) ? 3 : 2);
   const size_t fixed = tc_smem_bytes(N, S, parts, *na, 0);
   const size_t per = (size_t)S * parts * N * kTcRowBytes;
   const size_t avail = kTcSmemLimit > fixed ? kTcSmemLimit - fixed : 0;
