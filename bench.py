@@ -214,6 +214,7 @@ FOURIERREC = {"f32_frec": 7, "f16_frec": 5}  # path -> window width
 # exact launch shapes (slices, angles, n) -> bytes, file under profiles/.  Set
 # an entry to None when its kernel changes.
 PROFILED_TRAFFIC = {
+    "f32": ((256, 2048, 2048), 396.80e9 + 4.30e9, "profiles/k_backproject_tc_split_f32_2048sq_256slices.md"),
     "f16": ((256, 2048, 2048), 158.44e9 + 2.14e9, "profiles/k_backproject_tc_f16_2048sq_256slices.md"),
 }
 
