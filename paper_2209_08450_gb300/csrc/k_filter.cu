@@ -414,6 +414,61 @@ __device__ void filter_pair(float2* a, float2* b, int N, const int* rad, int nra
   if (active) last_to_rows<TOut>(a, N, tw, gt, gs, left, nd, o0, o1, has1, plane);
 }
 
+// filter_pair for a power-of-two padded length N >= 256 known at compile
+// time (radices 16, ..., 16 and a last 2, 4 or 8), with GS threads per row
+// pair: the same passes in the same order as filter_pair (bit-identical
+// results), but with N, every sub-transform size and the trip counts as
+// constants, so that the shared-memory index arithmetic folds into address
+// offsets.  The common padded lengths take this path.
+template <int N>
+__host__ __device__ constexpr int ct_log2() {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return l;
+}
+template <int N>
+__host__ __device__ constexpr int ct_group() {  // threads per row pair, as the launch computes it
+  return N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16);
+}
+template <int N, class TOut>
+__device__ void filter_pair_ct(float2* a, float2* b, const float2* tw, const float2* resp, int gt, bool active,
+                               int left, int nd, TOut* o0, TOut* o1, bool has1, int64_t plane) {
+  constexpr int L2 = ct_log2<N>();
+  static_assert((1 << L2) == N && L2 >= 8, "power-of-two padded length >= 256");
+  constexpr int P16 = L2 / 4, Q = 1 << (L2 % 4);
+  constexpr int NRAD = P16 + (Q > 1 ? 1 : 0);
+  constexpr int RL = Q > 1 ? Q : 16;  // the last forward radix (met by the inverse first pass)
+  constexpr int GS = ct_group<N>();
+  int Ns = 1;
+#pragma unroll
+  for (int i = 0; i < NRAD - 1; ++i) {
+    if (active) stockham_pass<16, false>(a, b, N, Ns, tw, gt, GS);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns *= 16;
+  }
+  if (active) fused_turn<RL>(a, b, N, tw, resp, gt, GS);
+  __syncthreads();
+  {
+    float2* t = a;
+    a = b;
+    b = t;
+  }
+  Ns = RL;
+#pragma unroll
+  for (int i = NRAD - 2; i >= 1; --i) {
+    if (active) stockham_pass<16, true>(a, b, N, Ns, tw, gt, GS);
+    __syncthreads();
+    float2* t = a;
+    a = b;
+    b = t;
+    Ns *= 16;
+  }
+  if (active) last_to_rows<TOut>(a, N, tw, gt, GS, left, nd, o0, o1, has1, plane);
+}
+
 struct FiltArgs {
   // source rows: filtered sinogram [d0][d1][nd] (in place) or raw projections
   const void* src;
@@ -450,7 +505,7 @@ __device__ __forceinline__ float load_sample(const FiltArgs& a, int64_t z, int64
 // per pair (gs = npad/16 clamped to [32, 256]): small transforms still fill the
 // block and share its barriers.
 template <bool RAW, class TIn, class TOut>
-__global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
+__global__ void __launch_bounds__(256, 3) k_filter(FiltArgs a) {
   extern __shared__ float2 smem[];
   const int gs = a.gs;
   const int G = blockDim.x / gs;
@@ -533,8 +588,15 @@ __global__ void __launch_bounds__(256) k_filter(FiltArgs a) {
     __syncthreads();
     TOut* o0 = reinterpret_cast<TOut*>(a.dst) + z0 * a.t0 + t0 * a.t1;
     TOut* o1 = reinterpret_cast<TOut*>(a.dst) + z1 * a.t0 + t1 * a.t1;
-    filter_pair<TOut>(bufA, bufB, a.npad, a.rad, a.nrad, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1,
-                      a.plane);
+    switch (a.npad) {
+      case 1024: filter_pair_ct<1024, TOut>(bufA, bufB, tw, a.resp, gt, active, a.left, a.nd, o0, o1, has1, a.plane); break;
+      case 2048: filter_pair_ct<2048, TOut>(bufA, bufB, tw, a.resp, gt, active, a.left, a.nd, o0, o1, has1, a.plane); break;
+      case 4096: filter_pair_ct<4096, TOut>(bufA, bufB, tw, a.resp, gt, active, a.left, a.nd, o0, o1, has1, a.plane); break;
+      case 8192: filter_pair_ct<8192, TOut>(bufA, bufB, tw, a.resp, gt, active, a.left, a.nd, o0, o1, has1, a.plane); break;
+      default:
+        filter_pair<TOut>(bufA, bufB, a.npad, a.rad, a.nrad, tw, a.resp, gt, gs, active, a.left, a.nd, o0, o1, has1,
+                          a.plane);
+    }
     __syncthreads();
   }
 }
