@@ -64,6 +64,60 @@ def test_backproject_fp32(nz, nt, nd, n, center):
     assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
 
 
+
+def _angle_major(x):
+    """The same values stored [theta][z][j] (planes first for F16X2), viewed [z][theta][j]."""
+    if x.dim() == 4:
+        return x.permute(0, 2, 1, 3).contiguous().permute(0, 2, 1, 3)
+    return x.permute(1, 0, 2).contiguous().permute(1, 0, 2)
+
+
+@pytest.mark.parametrize("kind,kernel,nz", [("f32", 0, 13), ("f32", 2, 13), ("f16", 1, 40), ("bf16", 1, 33),
+                                            ("f16x2", 1, 131), ("f16x2", 1, 20), ("f16", 0, 5)])
+def test_backproject_angle_major_sinograms_give_identical_volumes(kind, kernel, nz):
+    # tcp_backproject reads any strides; the angle-major layout (what tcp_fbp's
+    # chunks and normalize_filter use) changes the tensor-core kernel's copy
+    # shape, not its arithmetic: the volumes are bit-identical, and equal to
+    # the oracle within the path's tolerance
+    nt, nd, n, c = 67, 96, 90, 47.6
+    q, theta, _ = _bp_case(nz, nt, nd, n, c, 100 + nz)
+    if kind == "f16x2":
+        v = to_dev(q) * 1024.0
+        hi = v.half()
+        sino = torch.stack([hi, (v - hi.float()).half()])
+        scale, vdt, tol = 1.0 / 1024.0, torch.float32, 1e-5
+    else:
+        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[kind]
+        sino, scale, vdt = to_dev(q, dt), 1.0, torch.float32
+        tol = 1e-5 if kind == "f32" else 5e-3
+    try:
+        tcp.set_backproject_config(8 if kind == "f32" else 4, 16, 4, kernel=kernel)
+        a = tcp.backproject(sino, theta, c, n=n, dtype=vdt, scale=scale)
+        b = tcp.backproject(_angle_major(sino), theta, c, n=n, dtype=vdt, scale=scale)
+        torch.cuda.synchronize()
+    finally:
+        tcp.set_backproject_config(None)
+    assert torch.equal(a, b)
+    assert rel(host(b), oracle.backproject(q, theta, c, n)) <= tol
+
+
+def test_normalize_filter_output_is_angle_major_and_equals_a_contiguous_output():
+    ds = synth.shepp_logan_dataset(ntheta=48, ndet=80, nz=6, center=40.3, seed=9)
+    raw, dark, flat = u16(ds.raw), u16(ds.dark), u16(ds.flat)
+    for dt in (torch.float32, torch.float16, "f16x2"):
+        got = tcp.normalize_filter(raw, dark, flat, ds.center, dtype=dt)
+        split = dt == "f16x2"
+        if split:
+            assert got.stride() == (48 * 6 * 80, 80, 6 * 80, 1)
+            ref = torch.empty((2, 6, 48, 80), dtype=torch.float16, device=DEV)
+        else:
+            assert got.stride() == (80, 6 * 80, 1)
+            ref = torch.empty((6, 48, 80), dtype=dt, device=DEV)
+        tcp.normalize_filter(raw, dark, flat, ds.center, out=ref)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+
+
 @pytest.mark.parametrize("cfg", [(8, 16, 4), (4, 32, 4), (4, 16, 4), (16, 8, 2), (8, 16, 2), (2, 16, 4),
                                  (1, 32, 4), (4, 16, 16), (2, 16, 16), (4, 32, 16), (8, 16, 16)])
 def test_backproject_every_config(cfg):
