@@ -105,13 +105,6 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false after ~kTcBudget cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > kTcBudget) return false;
-  return true;
-}
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
   asm volatile(
@@ -618,7 +611,7 @@ size_t tc_smem_bytes(int N, int S, int parts, int na, int nbb) {
 // and absorb the segment-sum pauses), else 3 (S = 1) or 2 (S = 2); then as
 // many B buffers as fit (at most the geometry ring's bound).
 void tc_rings(int N, int S, int parts, int* na, int* nbb) {
-  *na = parts == 2 ? 4 : ((S == 1) ? 3 : 2);
+  *na = parts == 2 ? kTcMaxNA : ((S == 1) ? 3 : 2);
   const size_t fixed = tc_smem_bytes(N, S, parts, *na, 0);
   const size_t per = (size_t)S * parts * N * kTcRowBytes;
   const size_t avail = kTcSmemLimit > fixed ? kTcSmemLimit - fixed : 0;
