@@ -20,9 +20,9 @@
 //   D          two 128 x N FP32 accumulators in tensor memory (2N columns)
 //              for the whole angle loop; read back once with tcgen05.ld.
 //
-// Split mode (below) swaps the operands: D[z][v] = q W^T with the N = 128
-// sinogram rows as M and the 256 weight rows of both halves as N, one MMA
-// per K step.  The copy of one angle's window for all N slices reads one
+// Split mode (below) swaps the operands: D[z][v] = q W^T with the CTA's 128
+// sinogram rows (slices) as the MMA's M and the 256 weight rows of both
+// halves as its N, one MMA per K step and product.  The copy of one angle's window for all N slices reads one
 // contiguous block when the sinogram is stored angle-major ([theta][z][j],
 // the layout tcp_fbp's chunks use); the tensor map follows whichever of the
 // slice and angle strides is smaller.
@@ -262,6 +262,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_backproject_tc(const __grid_c
   const int gx = sub_x >> 1, gy = sub_y >> 1;
   const int ox = (sub_x & 1) * 16, oy = (sub_y & 1) * 16;
   // columns: [accumulator half 0][half 1], then in split mode [sum 0][sum 1]
+  // (split mode: 128 voxel columns per half, lanes = slices; else N slice
+  // columns per half, lanes = voxels)
   const int colsH = SWAP ? kTcM : N;  // accumulator columns per half
   const int ncols = (SPLIT ? 2 : 1) * kTcH * colsH;
   const uint32_t tmem_cols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
