@@ -360,6 +360,36 @@ __device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, con
 constexpr float kCoopRadius = 384.f;
 constexpr int kTile = 64;  // nodes per CTA tile side
 
+// Lane `lane` of warp `wid` in the CTA of tile `tile` owns the R x CW node
+// block at (gx0, gy0); `own` tells whether it lies inside the L x L grid, and
+// the return value whether that block, or its image shifted by -L in x or y,
+// lies within kCoopRadius of the zero frequency.  A warp is "near" when any of
+// its lanes is; the gather, the near-node table build and its application
+// all decide it with this function.
+template <int R, int CW>
+__device__ __forceinline__ bool lane_block_near(int2 tile, int wid, int lane, int L, int W, int* gx0, int* gy0,
+                                                bool* own) {
+  constexpr int kWarpCols = 8 * CW, kWarpRows = 4 * R;
+  constexpr int kWarpsX = kTile / kWarpCols;
+  const int tx0 = tile.x * kTile + (wid % kWarpsX) * kWarpCols;
+  const int ty0 = tile.y * kTile + (wid / kWarpsX) * kWarpRows;
+  *gx0 = tx0 + (lane & 7) * CW;
+  *gy0 = ty0 + (lane >> 3) * R;
+  *own = *gx0 < L && *gy0 < L;
+  bool near = false;
+  if (*own) {
+    for (int mx = 0; mx >= -1; --mx)
+      for (int my = 0; my >= -1; --my) {
+        const int bx0 = *gx0 + mx * L, by0 = *gy0 + my * L;
+        if ((2 * (bx0 + CW - 1) <= -L - W || 2 * bx0 >= L + W) || (2 * (by0 + R - 1) <= -L - W || 2 * by0 >= L + W))
+          continue;
+        const float xc = bx0 + 0.5f * (CW - 1), yc = by0 + 0.5f * (R - 1);
+        near |= xc * xc + yc * yc < kCoopRadius * kCoopRadius;
+      }
+  }
+  return near;
+}
+
 // CTAs run in the order of `order`: tiles sorted by their distance from the
 // zero frequency (nearest first), every slice pair of a tile in a row.  Near
 // the origin every angle contributes and a tile takes many times the work of
@@ -370,7 +400,7 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
                                                      const float4* __restrict__ geomS, const int2* __restrict__ meta,
                                                      const float* __restrict__ thS, int nt, int M, int lgL, float bl2,
                                                      float2* __restrict__ G, int64_t g_pair,
-                                                     const int2* __restrict__ order, int nb) {
+                                                     const int2* __restrict__ order, int nb, int skip_near) {
   const int L = 1 << lgL;
   const int rank = (int)(blockIdx.x / (unsigned)nb);
   const int pb = (int)(blockIdx.x - (unsigned)rank * (unsigned)nb);
@@ -383,21 +413,14 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
   constexpr int kWarpsX = kTile / kWarpCols;
   const int tx0 = tile.x * kTile + (wid % kWarpsX) * kWarpCols;
   const int ty0 = tile.y * kTile + (wid / kWarpsX) * kWarpRows;
-  const int gx0 = tx0 + (lane & 7) * CW, gy0 = ty0 + (lane >> 3) * R;
-  const bool own = gx0 < L && gy0 < L;
+  int gx0, gy0;
+  bool own;
+  const bool near = lane_block_near<R, CW>(tile, wid, lane, L, W, &gx0, &gy0, &own);
   auto reachable = [&](int b0, int ext) { return !(2 * (b0 + ext - 1) <= -L - W || 2 * b0 >= L + W); };
-  bool near = false;
-  if (own) {
-    for (int mx = 0; mx >= -1; --mx)
-      for (int my = 0; my >= -1; --my) {
-        const int bx0 = gx0 + mx * L, by0 = gy0 + my * L;
-        if (!reachable(bx0, CW) || !reachable(by0, R)) continue;
-        const float xc = bx0 + 0.5f * (CW - 1), yc = by0 + 0.5f * (R - 1);
-        near |= xc * xc + yc * yc < kCoopRadius * kCoopRadius;
-      }
-  }
+  const bool warp_near = __any_sync(0xffffffffu, near);
+  if (warp_near && skip_near) return;  // the near-node table covers this warp's nodes
   float2 acc[R][CW];
-  if (!__any_sync(0xffffffffu, near)) {
+  if (!warp_near) {
     if (!own) return;
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -449,6 +472,234 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
         }
         if (lane == (r * CW + c) % 32) Gp[(int64_t)(bx + c) * L + by + r] = make_float2(x, y);
       }
+  }
+}
+
+// ---------------------------------------------- near-node sparse table --
+//
+// The nodes of near warps (within ~kCoopRadius of the zero frequency, where
+// every angle contributes) take most of the gather's time, and their window
+// weights do not depend on the data: they are listed once per geometry as a
+// sparse table, row = node (16 rows per lane block, 8 warps x 32 lanes per
+// tile, tiles in gather order), entries (P offset within a slice pair,
+// weight wx * wy), in the gather's visiting order (images, sorted angles, k).
+// Applying the table to a batch reads each entry once for up to 8 slice pairs.
+
+// Calls f(P offset, weight) for every sample of sorted angle u whose window
+// reaches node (bx0, by0) with a non-zero weight, k ascending: the gather's
+// positions and weights for a one-node block.
+template <class F>
+__device__ __forceinline__ void node_angle(int W, int u, int bx0, int by0, int ms, int M,
+                                           const float4* __restrict__ geomS, const int2* __restrict__ meta,
+                                           float bl2, F&& f) {
+  const float tw = 2.f / (float)W;
+  const float4 g = __ldg(geomS + u);
+  int klo = -M / 2, khi = M / 2;
+  const float lim = (float)M;
+  clip_k(g.x, bx0 - 0.5f * W, bx0 + 0.5f * W, lim, &klo, &khi);
+  clip_k(g.z, by0 - 0.5f * W, by0 + 0.5f * W, lim, &klo, &khi);
+  if (klo > khi) return;
+  const int2 m = __ldg(meta + u);
+  const int row = m.x * ms + M / 2;
+  const float fk0 = (float)klo;
+  int gix, giy;
+  float frx, fry;
+  split_pos(fk0, g.x, g.y, &gix, &frx);
+  split_pos(fk0, g.z, g.w, &giy, &fry);
+  const float flx = floorf(g.x), fly = floorf(g.z);
+  const int sxi = (int)flx, syi = (int)fly;
+  const float sxf = (g.x - flx) + g.y, syf = (g.z - fly) + g.w;
+  for (int k = klo; k <= khi; ++k) {
+    const float dx = (float)(gix - bx0) + frx, dy = (float)(giy - by0) + fry;
+    const float w = es_weight(dx, bl2, tw) * es_weight(dy, bl2, tw);
+    if (w != 0.f) f(row + m.y * k, w);
+    frx += sxf;
+    gix += sxi;
+    if (frx >= 1.f) {
+      frx -= 1.f;
+      ++gix;
+    } else if (frx < 0.f) {
+      frx += 1.f;
+      --gix;
+    }
+    fry += syf;
+    giy += syi;
+    if (fry >= 1.f) {
+      fry -= 1.f;
+      ++giy;
+    } else if (fry < 0.f) {
+      fry += 1.f;
+      --giy;
+    }
+  }
+}
+
+// Count (FILL = false: counts[row]) or write (FILL: ent[off[row] ..]) the
+// entries of every node of the near warps of tiles order[0 .. gridDim.x).
+template <int R, int CW, bool FILL>
+__global__ void __launch_bounds__(256) k_frec_near_build(int W, const float4* __restrict__ geomS,
+                                                         const int2* __restrict__ meta, const float* __restrict__ thS,
+                                                         int nt, int M, int lgL, float bl2,
+                                                         const int2* __restrict__ order, int* __restrict__ counts,
+                                                         const int64_t* __restrict__ off, int2* __restrict__ ent) {
+  const int L = 1 << lgL, ms = M + 1;
+  const int rank = blockIdx.x;
+  const int2 tile = __ldg(order + rank);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int gx0, gy0;
+  bool own;
+  const bool near = lane_block_near<R, CW>(tile, wid, lane, L, W, &gx0, &gy0, &own);
+  if (!__any_sync(0xffffffffu, near) || !own) return;
+  const int64_t rowb = ((int64_t)(rank * 8 + wid) * 32 + lane) * (R * CW);
+  for (int r = 0; r < R; ++r)
+    for (int c = 0; c < CW; ++c) {
+      const int64_t row = rowb + r * CW + c;
+      int cnt = 0;
+      int64_t pos = FILL ? off[row] : 0;
+      for (int mx = 0; mx >= -1; --mx)
+        for (int my = 0; my >= -1; --my) {
+          const int bx = gx0 + c + mx * L, by = gy0 + r + my * L;
+          if ((2 * bx <= -L - W || 2 * bx >= L + W) || (2 * by <= -L - W || 2 * by >= L + W)) continue;
+          int2 rng[2];
+          const int nr = block_angles<1, 1>(W, bx, by, thS, nt, rng);
+          for (int q = 0; q < nr; ++q)
+            for (int u = rng[q].x; u < rng[q].y; ++u)
+              node_angle(W, u, bx, by, ms, M, geomS, meta, bl2, [&](int o, float w) {
+                if (FILL) ent[pos++] = make_int2(o, __float_as_int(w));
+                else ++cnt;
+              });
+        }
+      if (!FILL) counts[row] = cnt;
+    }
+}
+
+// G[pair][node] = sum of weight x P[pair][offset] over the node's entries,
+// for the nodes of near warps and slice pairs 0 .. nb - 1, at most kPairs at
+// a time.  One warp per row, the lanes splitting the row's entries, then a
+// shuffle reduction; rows with more than kHeavyRow entries (the nodes next to
+// the zero frequency, where every angle contributes) are left to
+// k_frec_near_heavy, one CTA each.
+constexpr int kNearPairs = 8;
+constexpr int kHeavyRow = 4096;
+
+// Node coordinates of table row `row` (16 rows per lane block, 32 lane blocks
+// per warp, 8 warps per tile in gather order).
+__device__ __forceinline__ void near_row_node(int64_t row, const int2* __restrict__ order, int* gx, int* gy, int* rank,
+                                              int* w, int* l) {
+  const int64_t blk = row >> 4;
+  const int rc = (int)(row & 15);
+  *rank = (int)(blk >> 8);
+  *w = (int)((blk >> 5) & 7);
+  *l = (int)(blk & 31);
+  const int2 tile = __ldg(order + *rank);
+  *gx = tile.x * kTile + (*w % 2) * 32 + (*l & 7) * 4 + (rc & 3);
+  *gy = tile.y * kTile + (*w / 2) * 16 + (*l >> 3) * 4 + (rc >> 2);
+}
+
+__device__ __forceinline__ void near_accumulate(const float2* __restrict__ Pp, int64_t p_pair, int np, int2 en,
+                                                float2 (&acc)[kNearPairs]) {
+  const float w = __int_as_float(en.y);
+#pragma unroll
+  for (int p = 0; p < kNearPairs; ++p)
+    if (p < np) {
+      const float2 v = __ldg(Pp + p * p_pair + en.x);
+      acc[p].x = fmaf(w, v.x, acc[p].x);
+      acc[p].y = fmaf(w, v.y, acc[p].y);
+    }
+}
+
+template <int R, int CW>
+__global__ void __launch_bounds__(256) k_frec_near_apply(int W, const float2* __restrict__ P, int64_t p_pair, int nb,
+                                                         const int64_t* __restrict__ off,
+                                                         const int2* __restrict__ ent, int lgL, int64_t rows,
+                                                         const int2* __restrict__ order, float2* __restrict__ G,
+                                                         int64_t g_pair) {
+  static_assert(R == 4 && CW == 4, "table rows are laid out for 4 x 4 node blocks");
+  const int L = 1 << lgL;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  int gx, gy, rank, w, l;
+  near_row_node(row, order, &gx, &gy, &rank, &w, &l);
+  // is the row's warp near (the lanes evaluate its 32 blocks)?
+  int bx0, by0;
+  bool own;
+  const bool near = lane_block_near<R, CW>(__ldg(order + rank), w, lane, L, W, &bx0, &by0, &own);
+  if (!__any_sync(0xffffffffu, near) || !__shfl_sync(0xffffffffu, (int)own, l)) return;
+  const int64_t e0 = __ldg(off + row), e1 = __ldg(off + row + 1);
+  if (e1 - e0 > kHeavyRow) return;
+  for (int p0 = 0; p0 < nb; p0 += kNearPairs) {
+    const int np = min(kNearPairs, nb - p0);
+    float2 acc[kNearPairs];
+#pragma unroll
+    for (int p = 0; p < kNearPairs; ++p) acc[p] = make_float2(0.f, 0.f);
+    const float2* Pp = P + (int64_t)p0 * p_pair;
+    int64_t e = e0 + lane;
+    for (; e + 32 < e1; e += 64) {  // two entries in flight per lane
+      const int2 a = __ldg(ent + e), b = __ldg(ent + e + 32);
+      near_accumulate(Pp, p_pair, np, a, acc);
+      near_accumulate(Pp, p_pair, np, b, acc);
+    }
+    if (e < e1) near_accumulate(Pp, p_pair, np, __ldg(ent + e), acc);
+#pragma unroll
+    for (int p = 0; p < kNearPairs; ++p) {
+      if (p >= np) break;  // uniform over the warp
+      float x = acc[p].x, y = acc[p].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == p) G[(int64_t)(p0 + p) * g_pair + (int64_t)gx * L + gy] = make_float2(x, y);
+    }
+  }
+}
+
+// The heavy rows, one CTA (256 threads) each: the threads split the entries,
+// warp shuffles then shared memory reduce them in a fixed order.
+__global__ void __launch_bounds__(256) k_frec_near_heavy(const float2* __restrict__ P, int64_t p_pair, int nb,
+                                                         const int64_t* __restrict__ off,
+                                                         const int2* __restrict__ ent,
+                                                         const int64_t* __restrict__ heavy, int lgL,
+                                                         const int2* __restrict__ order, float2* __restrict__ G,
+                                                         int64_t g_pair) {
+  __shared__ float2 red[8][kNearPairs];
+  const int L = 1 << lgL;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row = __ldg(heavy + blockIdx.x);
+  int gx, gy, rank, w, l;
+  near_row_node(row, order, &gx, &gy, &rank, &w, &l);
+  const int64_t e0 = __ldg(off + row), e1 = __ldg(off + row + 1);
+  for (int p0 = 0; p0 < nb; p0 += kNearPairs) {
+    const int np = min(kNearPairs, nb - p0);
+    float2 acc[kNearPairs];
+#pragma unroll
+    for (int p = 0; p < kNearPairs; ++p) acc[p] = make_float2(0.f, 0.f);
+    const float2* Pp = P + (int64_t)p0 * p_pair;
+    int64_t e = e0 + threadIdx.x;
+    for (; e + 256 < e1; e += 512) {
+      const int2 a = __ldg(ent + e), b = __ldg(ent + e + 256);
+      near_accumulate(Pp, p_pair, np, a, acc);
+      near_accumulate(Pp, p_pair, np, b, acc);
+    }
+    if (e < e1) near_accumulate(Pp, p_pair, np, __ldg(ent + e), acc);
+#pragma unroll
+    for (int p = 0; p < kNearPairs; ++p) {
+      float x = acc[p].x, y = acc[p].y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) red[wid][p] = make_float2(x, y);
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+      float2 t = red[0][threadIdx.x];
+      for (int q = 1; q < 8; ++q) t = make_float2(t.x + red[q][threadIdx.x].x, t.y + red[q][threadIdx.x].y);
+      G[(int64_t)(p0 + threadIdx.x) * g_pair + (int64_t)gx * L + gy] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -520,11 +771,13 @@ uint64_t bytes_hash(const void* p, size_t n) {  // FNV-1a
   for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
   return h;
 }
+struct NearEntry;  // near-node table of one geometry (defined with its builder)
 struct HostTables {
   std::map<std::pair<int, int>, float2*> tw;                 // (dev, N) -> e^{-2 pi i j / N}
   std::map<std::tuple<int, int, int, int>, float*> dec;      // (dev, n, L, W) -> 1 / Phi(x / L)
   std::map<int, std::vector<SortedAngles>> ang;              // dev -> angle arrays seen
   std::map<std::pair<int, int>, int2*> order;                // (dev, L) -> gather tile order
+  std::vector<NearEntry*> nearT;                             // near-node tables (least recently used freed)
 };
 std::mutex g_frec_mu;
 HostTables g_frec;
@@ -684,11 +937,187 @@ void launch_rows(const View3& sv, int z0, int nb, int lgM, const float2* twM, co
 template <int R, int CW>
 void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4* geomS, const int2* meta,
                    const float* thS, int nt, int M, int lgL, float2* G, int64_t g_pair, int nb, const int2* order,
-                   cudaStream_t st) {
+                   const FrecTables& tb, cudaStream_t st) {
   const int L = 1 << lgL;
   const unsigned tiles = (unsigned)((L + kTile - 1) / kTile);
+  const int skip = tb.t_near > 0 ? 1 : 0;
   k_frec_gather<R, CW><<<dim3(tiles * tiles * (unsigned)nb), 256, 0, st>>>(
-      W, P, p_pair, ms, geomS, meta, thS, nt, M, lgL, (float)(es_beta(W) / M_LN2), G, g_pair, order, nb);
+      W, P, p_pair, ms, geomS, meta, thS, nt, M, lgL, (float)(es_beta(W) / M_LN2), G, g_pair, order, nb, skip);
+  if (skip) {
+    const int64_t rows = (int64_t)tb.t_near * 4096;
+    k_frec_near_apply<R, CW><<<dim3((unsigned)((rows + 7) / 8)), 256, 0, st>>>(W, P, p_pair, nb, tb.near_off,
+                                                                                tb.near_ent, lgL, rows, order, G,
+                                                                                g_pair);
+    if (tb.n_heavy > 0)
+      k_frec_near_heavy<<<dim3((unsigned)tb.n_heavy), 256, 0, st>>>(P, p_pair, nb, tb.near_off, tb.near_ent,
+                                                                     tb.near_heavy, lgL, order, G, g_pair);
+  }
+}
+
+std::vector<int2> gather_tile_order(int L);
+
+// Near-node table of one geometry: tiles order[0 .. t_near) (every tile with
+// a near warp: their centres lie within kCoopRadius + 64 of the zero
+// frequency), 4096 rows each.  Sample positions as k_frec_geom makes them
+// (FP64 cos/sin times L/M, split into FP32 hi + lo).  Returns t_near = 0
+// without a table when the device memory for it is not available.
+struct NearTable {
+  int t_near = 0;
+  int64_t* off = nullptr;
+  int2* ent = nullptr;
+  int64_t n_heavy = 0;
+  int64_t* heavy = nullptr;  // rows above kHeavyRow entries
+  size_t bytes = 0;
+};
+tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W, const std::vector<int2>& hmeta,
+                            const int2* d_meta, const float* d_thS, const int2* d_order,
+                            const std::vector<int2>& horder, NearTable* out) {
+  const int M = 1 << lgM, L = 1 << lgL;
+  *out = NearTable();
+  int t_near = 0;
+  for (const int2& t : horder) {
+    const double cx = t.x * kTile + 0.5 * kTile, cy = t.y * kTile + 0.5 * kTile;
+    const double dx = std::min(cx, L - cx), dy = std::min(cy, L - cy);
+    if (std::sqrt(dx * dx + dy * dy) >= (double)kCoopRadius + 64.0) break;
+    ++t_near;
+  }
+  // entries hold the P offset of a sample as an int: the spectra of one slice
+  // pair must stay below 2^31 samples
+  if (t_near == 0 || nt == 0 || (int64_t)nt * (M + 1) >= (int64_t(1) << 31)) return TCP_OK;
+  std::vector<float4> hg((size_t)nt);
+  const double ratio = (double)L / (double)M;
+  for (int u = 0; u < nt; ++u) {
+    const int2 m = hmeta[(size_t)u];
+    const double cx = std::cos(theta[m.x]) * ratio * m.y, sy = std::sin(theta[m.x]) * ratio * m.y;
+    const float chi = (float)cx, shi = (float)sy;
+    hg[(size_t)u] = make_float4(chi, (float)(cx - (double)chi), shi, (float)(sy - (double)shi));
+  }
+  const int64_t rows = (int64_t)t_near * 4096;
+  float4* dg = nullptr;
+  int* dc = nullptr;
+  int64_t* doff = nullptr;
+  int2* dent = nullptr;
+  int64_t* dheavy = nullptr;
+  auto release = [&]() {
+    cudaFree(dg);
+    cudaFree(dc);
+    cudaFree(doff);
+    cudaFree(dent);
+    cudaFree(dheavy);
+  };
+  if (cudaMalloc(&dg, sizeof(float4) * (size_t)nt) != cudaSuccess ||
+      cudaMalloc(&dc, sizeof(int) * (size_t)rows) != cudaSuccess ||
+      cudaMalloc(&doff, sizeof(int64_t) * (size_t)(rows + 1)) != cudaSuccess) {
+    release();
+    cudaGetLastError();  // an allocation failure is not sticky; the gather keeps these nodes
+    return TCP_OK;
+  }
+  cudaError_t e = cudaMemcpy(dg, hg.data(), sizeof(float4) * (size_t)nt, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dc, 0, sizeof(int) * (size_t)rows);
+  const float bl2 = (float)(es_beta(W) / M_LN2);
+  if (e == cudaSuccess) {
+    k_frec_near_build<4, 4, false><<<dim3((unsigned)t_near), 256>>>(W, dg, d_meta, d_thS, nt, M, lgL, bl2, d_order,
+                                                                    dc, nullptr, nullptr);
+    e = cudaGetLastError();
+  }
+  std::vector<int> hc((size_t)rows);
+  if (e == cudaSuccess) e = cudaMemcpy(hc.data(), dc, sizeof(int) * (size_t)rows, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "FourierRec near-node table (count)");
+  }
+  std::vector<int64_t> ho((size_t)rows + 1), hh;
+  ho[0] = 0;
+  for (int64_t i = 0; i < rows; ++i) {
+    ho[(size_t)i + 1] = ho[(size_t)i] + hc[(size_t)i];
+    if (hc[(size_t)i] > kHeavyRow) hh.push_back(i);
+  }
+  const int64_t total = ho[(size_t)rows];
+  if (total > (int64_t(1) << 29)) {  // above 4 GB the gather keeps these nodes
+    release();
+    return TCP_OK;
+  }
+  if (cudaMalloc(&dent, sizeof(int2) * (size_t)std::max<int64_t>(total, 1)) != cudaSuccess ||
+      cudaMalloc(&dheavy, sizeof(int64_t) * std::max<size_t>(hh.size(), 1)) != cudaSuccess) {
+    release();
+    cudaGetLastError();
+    return TCP_OK;
+  }
+  e = cudaMemcpy(doff, ho.data(), sizeof(int64_t) * (size_t)(rows + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !hh.empty())
+    e = cudaMemcpy(dheavy, hh.data(), sizeof(int64_t) * hh.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_frec_near_build<4, 4, true><<<dim3((unsigned)t_near), 256>>>(W, dg, d_meta, d_thS, nt, M, lgL, bl2, d_order,
+                                                                   nullptr, doff, dent);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dg);
+  cudaFree(dc);
+  if (e != cudaSuccess) {
+    cudaFree(doff);
+    cudaFree(dent);
+    cudaFree(dheavy);
+    return cuda_fail(e, "FourierRec near-node table (fill)");
+  }
+  out->t_near = t_near;
+  out->off = doff;
+  out->ent = dent;
+  out->n_heavy = (int64_t)hh.size();
+  out->heavy = dheavy;
+  out->bytes = sizeof(int64_t) * (size_t)(rows + 1) + sizeof(int2) * (size_t)std::max<int64_t>(total, 1) +
+               sizeof(int64_t) * std::max<size_t>(hh.size(), 1);
+  return TCP_OK;
+}
+
+// Cached near-node tables: a few geometries (each up to ~1 GB at 2048^2),
+// the least recently used freed beyond the cap.
+struct NearEntry {
+  int dev = 0, M = 0, L = 0, W = 0;
+  std::vector<double> theta;
+  uint64_t hash = 0, used = 0;
+  NearTable t;
+};
+constexpr size_t kNearCacheCap = 4;
+
+tcp_status get_near_table(int dev, const double* theta, int nt, int lgM, int lgL, int W, const int2* d_meta,
+                          const float* d_thS, const int2* d_order, NearTable* out) {
+  std::lock_guard<std::mutex> lk(g_frec_mu);
+  const uint64_t h = bytes_hash(theta, sizeof(double) * (size_t)nt);
+  for (NearEntry* e : g_frec.nearT)
+    if (e->dev == dev && e->M == (1 << lgM) && e->L == (1 << lgL) && e->W == W && e->hash == h &&
+        (int)e->theta.size() == nt && std::equal(e->theta.begin(), e->theta.end(), theta)) {
+      e->used = ++g_frec_stamp;
+      *out = e->t;
+      return TCP_OK;
+    }
+  if (g_frec.nearT.size() >= kNearCacheCap) {
+    auto lru = std::min_element(g_frec.nearT.begin(), g_frec.nearT.end(),
+                                [](const NearEntry* a, const NearEntry* b) { return a->used < b->used; });
+    cudaFree((*lru)->t.off);  // cudaFree waits for the device: no queued kernel still reads it
+    cudaFree((*lru)->t.ent);
+    cudaFree((*lru)->t.heavy);
+    delete *lru;
+    g_frec.nearT.erase(lru);
+  }
+  std::vector<int2> hm;
+  std::vector<float> ht;
+  sort_angles(theta, nt, &hm, &ht);
+  NearTable t;
+  tcp_status s = build_near_table(theta, nt, lgM, lgL, W, hm, d_meta, d_thS, d_order, gather_tile_order(1 << lgL), &t);
+  if (s != TCP_OK) return s;
+  NearEntry* e = new NearEntry;
+  e->dev = dev;
+  e->M = 1 << lgM;
+  e->L = 1 << lgL;
+  e->W = W;
+  e->theta.assign(theta, theta + nt);
+  e->hash = h;
+  e->used = ++g_frec_stamp;
+  e->t = t;
+  g_frec.nearT.push_back(e);
+  *out = t;
+  return TCP_OK;
 }
 
 // Gather tiles of an L x L grid, nearest to the zero frequency (node 0 and
@@ -747,6 +1176,13 @@ void fourierrec_cache_clear() {
       cudaFree(e.thS);
     }
   g_frec.ang.clear();
+  for (NearEntry* e : g_frec.nearT) {
+    cudaFree(e->t.off);
+    cudaFree(e->t.ent);
+    cudaFree(e->t.heavy);
+    delete e;
+  }
+  g_frec.nearT.clear();
 }
 
 // Cartesian grid side: the next power of two >= 2n, at least 16 (oversampling
@@ -836,7 +1272,15 @@ tcp_status fourierrec_tables_cached(const double* theta, int64_t nt, int64_t nd,
     }
     t->order = it->second;
   }
-  return get_sorted_angles(dev, theta, (int)nt, &t->meta, &t->thS);
+  if ((s = get_sorted_angles(dev, theta, (int)nt, &t->meta, &t->thS)) != TCP_OK) return s;
+  NearTable nt_;
+  if ((s = get_near_table(dev, theta, (int)nt, lgM, lgL, width, t->meta, t->thS, t->order, &nt_)) != TCP_OK) return s;
+  t->t_near = nt_.t_near;
+  t->near_off = nt_.off;
+  t->near_ent = nt_.ent;
+  t->n_heavy = nt_.n_heavy;
+  t->near_heavy = nt_.heavy;
+  return TCP_OK;
 }
 
 // Tables owned by the caller (a plan): cudaMalloc and synchronous upload, the
@@ -873,7 +1317,21 @@ tcp_status fourierrec_tables_owned(const double* theta, int64_t nt, int64_t nd, 
   if ((s = upload(hm.data(), hm.size() * sizeof(int2), (const void**)&t->meta)) != TCP_OK) return s;
   const std::vector<int2> ho = gather_tile_order(1 << lgL);
   if ((s = upload(ho.data(), ho.size() * sizeof(int2), (const void**)&t->order)) != TCP_OK) return s;
-  return upload(ht.data(), ht.size() * sizeof(float), (const void**)&t->thS);
+  if ((s = upload(ht.data(), ht.size() * sizeof(float), (const void**)&t->thS)) != TCP_OK) return s;
+  NearTable nt_;
+  if ((s = build_near_table(theta, (int)nt, lgM, lgL, width, hm, t->meta, t->thS, t->order, ho, &nt_)) != TCP_OK)
+    return s;
+  if (nt_.t_near > 0) {
+    owned->push_back(nt_.off);
+    owned->push_back(nt_.ent);
+    owned->push_back(nt_.heavy);
+  }
+  t->t_near = nt_.t_near;
+  t->near_off = nt_.off;
+  t->near_ent = nt_.ent;
+  t->n_heavy = nt_.n_heavy;
+  t->near_heavy = nt_.heavy;
+  return TCP_OK;
 }
 
 tcp_status launch_fourierrec_ws(const View3& sv, const FrecTables& tb, const FrecWorkspace& w, const TrigTable& trig,
@@ -909,7 +1367,7 @@ tcp_status launch_fourierrec_ws(const View3& sv, const FrecTables& tb, const Fre
     }
     TCP_CUDA_TRY(cudaGetLastError());
     launch_gather<4, 4>(width, (const float2*)w.P, p_pair, ms, (const float4*)w.geom, tb.meta, tb.thS, nt, M, lgL,
-                        (float2*)w.G, g_pair, b, tb.order, st);
+                        (float2*)w.G, g_pair, b, tb.order, tb, st);
     TCP_CUDA_TRY(cudaGetLastError());
     launch_cols((const float2*)w.G, g_pair, lgL, n, tb.twL, tb.dec, (float2*)w.H, h_pair, b, st);
     TCP_CUDA_TRY(cudaGetLastError());

@@ -193,6 +193,13 @@ struct FrecTables {
   const int2* meta = nullptr;
   const float* thS = nullptr;
   const int2* order = nullptr;  // gather tiles, nearest to the zero frequency first
+  // near-node sparse table (t_near = 0: none, the gather does those nodes):
+  // rows of the first t_near tiles of `order`, 4096 per tile
+  int t_near = 0;
+  const int64_t* near_off = nullptr;  // row starts, t_near * 4096 + 1
+  const int2* near_ent = nullptr;     // (P offset, weight bits)
+  int64_t n_heavy = 0;                // rows with more than 4096 entries, one CTA each
+  const int64_t* near_heavy = nullptr;
 };
 struct FrecWorkspace {
   void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
