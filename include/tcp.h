@@ -282,8 +282,11 @@ tcp_status tcp_project(const tcp_tensor* vol, const double* theta, double center
  * over the limits, TCP_ERR_ARG for a width outside 2..16,
  * TCP_ERR_DTYPE for F16X2 or U16 sinograms.
  * The first call for a new size, width or angle set builds cached tables
- * (twiddles, deconvolution factors, sorted angles) with synchronous uploads,
- * so that call must not be inside CUDA graph capture. */
+ * (twiddles, deconvolution factors, sorted angles, and the sparse table of
+ * window weights of the grid nodes within 128 points of the zero frequency:
+ * about 0.2 GB at 2048^2 and 2048 angles, four geometries kept, least
+ * recently used freed beyond that) with synchronous uploads, so that call
+ * must not be inside CUDA graph capture. */
 tcp_status tcp_fourierrec(const tcp_tensor* sino, const double* theta, double center,
                           tcp_tensor* vol, double scale, int32_t width, void* stream);
 

@@ -354,10 +354,15 @@ __device__ __forceinline__ void gather_angle(int W, int u, int bx0, int by0, con
 // coordinates and their images shifted by -L (samples lie in [-L/2, L/2]),
 // and adds every sample whose window reaches the block -- no atomics, no
 // shared memory.  Warps with a block within kCoopRadius of the zero
-// frequency (where every angle contributes) take their blocks one at a time
-// and share each block's angles among the lanes, reducing with shuffles.
+// frequency (where every angle contributes) are "near": their nodes come
+// from the near-node sparse table when the geometry has one (skip_near);
+// without it they take their blocks one at a time and share each block's
+// angles among the lanes, reducing with shuffles.
 // Output: the grid G[pair][gx][gy] (column-major), written from registers.
-constexpr float kCoopRadius = 384.f;
+// The radius was measured at 2048^2 x 64 slices, window 7: 64, 96, 128, 192,
+// 256, 384, 512 gave 24.8, 24.6, 24.4, 24.6, 24.9, 25.9, 27.2 ms per call
+// (the table's 0.21 GB at 128).
+constexpr float kCoopRadius = 128.f;
 constexpr int kTile = 64;  // nodes per CTA tile side
 
 // Lane `lane` of warp `wid` in the CTA of tile `tile` owns the R x CW node
@@ -596,6 +601,18 @@ __device__ __forceinline__ void near_row_node(int64_t row, const int2* __restric
   *gy = tile.y * kTile + (*w / 2) * 16 + (*l >> 3) * 4 + (rc >> 2);
 }
 
+// nearw[rank * 8 + warp] = 1 for the near warps of tiles order[0 .. gridDim.x).
+template <int R, int CW>
+__global__ void __launch_bounds__(256) k_frec_near_flags(int W, int lgL, const int2* __restrict__ order,
+                                                         unsigned char* __restrict__ nearw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int gx0, gy0;
+  bool own;
+  const bool near = lane_block_near<R, CW>(__ldg(order + blockIdx.x), wid, lane, 1 << lgL, W, &gx0, &gy0, &own);
+  const bool any = __any_sync(0xffffffffu, near);
+  if (lane == 0) nearw[blockIdx.x * 8 + wid] = any ? 1 : 0;
+}
+
 __device__ __forceinline__ void near_accumulate(const float2* __restrict__ Pp, int64_t p_pair, int np, int2 en,
                                                 float2 (&acc)[kNearPairs]) {
   const float w = __int_as_float(en.y);
@@ -608,24 +625,19 @@ __device__ __forceinline__ void near_accumulate(const float2* __restrict__ Pp, i
     }
 }
 
-template <int R, int CW>
-__global__ void __launch_bounds__(256) k_frec_near_apply(int W, const float2* __restrict__ P, int64_t p_pair, int nb,
+__global__ void __launch_bounds__(256) k_frec_near_apply(const float2* __restrict__ P, int64_t p_pair, int nb,
                                                          const int64_t* __restrict__ off,
-                                                         const int2* __restrict__ ent, int lgL, int64_t rows,
-                                                         const int2* __restrict__ order, float2* __restrict__ G,
-                                                         int64_t g_pair) {
-  static_assert(R == 4 && CW == 4, "table rows are laid out for 4 x 4 node blocks");
+                                                         const int2* __restrict__ ent,
+                                                         const unsigned char* __restrict__ nearw, int lgL,
+                                                         int64_t rows, const int2* __restrict__ order,
+                                                         float2* __restrict__ G, int64_t g_pair) {
   const int L = 1 << lgL;
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= rows) return;
+  if (row >= rows || !__ldg(nearw + (row >> 9))) return;  // 512 rows per gather warp
   int gx, gy, rank, w, l;
   near_row_node(row, order, &gx, &gy, &rank, &w, &l);
-  // is the row's warp near (the lanes evaluate its 32 blocks)?
-  int bx0, by0;
-  bool own;
-  const bool near = lane_block_near<R, CW>(__ldg(order + rank), w, lane, L, W, &bx0, &by0, &own);
-  if (!__any_sync(0xffffffffu, near) || !__shfl_sync(0xffffffffu, (int)own, l)) return;
+  if (gx - (int)(row & 3) >= L || gy - (int)((row >> 2) & 3) >= L) return;  // block outside the grid
   const int64_t e0 = __ldg(off + row), e1 = __ldg(off + row + 1);
   if (e1 - e0 > kHeavyRow) return;
   for (int p0 = 0; p0 < nb; p0 += kNearPairs) {
@@ -945,9 +957,8 @@ void launch_gather(int W, const float2* P, int64_t p_pair, int ms, const float4*
       W, P, p_pair, ms, geomS, meta, thS, nt, M, lgL, (float)(es_beta(W) / M_LN2), G, g_pair, order, nb, skip);
   if (skip) {
     const int64_t rows = (int64_t)tb.t_near * 4096;
-    k_frec_near_apply<R, CW><<<dim3((unsigned)((rows + 7) / 8)), 256, 0, st>>>(W, P, p_pair, nb, tb.near_off,
-                                                                                tb.near_ent, lgL, rows, order, G,
-                                                                                g_pair);
+    k_frec_near_apply<<<dim3((unsigned)((rows + 7) / 8)), 256, 0, st>>>(P, p_pair, nb, tb.near_off, tb.near_ent,
+                                                                         tb.near_warps, lgL, rows, order, G, g_pair);
     if (tb.n_heavy > 0)
       k_frec_near_heavy<<<dim3((unsigned)tb.n_heavy), 256, 0, st>>>(P, p_pair, nb, tb.near_off, tb.near_ent,
                                                                      tb.near_heavy, lgL, order, G, g_pair);
@@ -967,6 +978,7 @@ struct NearTable {
   int2* ent = nullptr;
   int64_t n_heavy = 0;
   int64_t* heavy = nullptr;  // rows above kHeavyRow entries
+  unsigned char* warps = nullptr;  // near flag per gather warp of the t_near tiles
   size_t bytes = 0;
 };
 tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W, const std::vector<int2>& hmeta,
@@ -998,12 +1010,14 @@ tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W
   int64_t* doff = nullptr;
   int2* dent = nullptr;
   int64_t* dheavy = nullptr;
+  unsigned char* dwarps = nullptr;
   auto release = [&]() {
     cudaFree(dg);
     cudaFree(dc);
     cudaFree(doff);
     cudaFree(dent);
     cudaFree(dheavy);
+    cudaFree(dwarps);
   };
   if (cudaMalloc(&dg, sizeof(float4) * (size_t)nt) != cudaSuccess ||
       cudaMalloc(&dc, sizeof(int) * (size_t)rows) != cudaSuccess ||
@@ -1038,7 +1052,8 @@ tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W
     return TCP_OK;
   }
   if (cudaMalloc(&dent, sizeof(int2) * (size_t)std::max<int64_t>(total, 1)) != cudaSuccess ||
-      cudaMalloc(&dheavy, sizeof(int64_t) * std::max<size_t>(hh.size(), 1)) != cudaSuccess) {
+      cudaMalloc(&dheavy, sizeof(int64_t) * std::max<size_t>(hh.size(), 1)) != cudaSuccess ||
+      cudaMalloc(&dwarps, (size_t)t_near * 8) != cudaSuccess) {
     release();
     cudaGetLastError();
     return TCP_OK;
@@ -1049,6 +1064,7 @@ tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W
   if (e == cudaSuccess) {
     k_frec_near_build<4, 4, true><<<dim3((unsigned)t_near), 256>>>(W, dg, d_meta, d_thS, nt, M, lgL, bl2, d_order,
                                                                    nullptr, doff, dent);
+    k_frec_near_flags<4, 4><<<dim3((unsigned)t_near), 256>>>(W, lgL, d_order, dwarps);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -1058,6 +1074,7 @@ tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W
     cudaFree(doff);
     cudaFree(dent);
     cudaFree(dheavy);
+    cudaFree(dwarps);
     return cuda_fail(e, "FourierRec near-node table (fill)");
   }
   out->t_near = t_near;
@@ -1065,6 +1082,7 @@ tcp_status build_near_table(const double* theta, int nt, int lgM, int lgL, int W
   out->ent = dent;
   out->n_heavy = (int64_t)hh.size();
   out->heavy = dheavy;
+  out->warps = dwarps;
   out->bytes = sizeof(int64_t) * (size_t)(rows + 1) + sizeof(int2) * (size_t)std::max<int64_t>(total, 1) +
                sizeof(int64_t) * std::max<size_t>(hh.size(), 1);
   return TCP_OK;
@@ -1097,6 +1115,7 @@ tcp_status get_near_table(int dev, const double* theta, int nt, int lgM, int lgL
     cudaFree((*lru)->t.off);  // cudaFree waits for the device: no queued kernel still reads it
     cudaFree((*lru)->t.ent);
     cudaFree((*lru)->t.heavy);
+    cudaFree((*lru)->t.warps);
     delete *lru;
     g_frec.nearT.erase(lru);
   }
@@ -1180,6 +1199,7 @@ void fourierrec_cache_clear() {
     cudaFree(e->t.off);
     cudaFree(e->t.ent);
     cudaFree(e->t.heavy);
+    cudaFree(e->t.warps);
     delete e;
   }
   g_frec.nearT.clear();
@@ -1280,6 +1300,7 @@ tcp_status fourierrec_tables_cached(const double* theta, int64_t nt, int64_t nd,
   t->near_ent = nt_.ent;
   t->n_heavy = nt_.n_heavy;
   t->near_heavy = nt_.heavy;
+  t->near_warps = nt_.warps;
   return TCP_OK;
 }
 
@@ -1325,12 +1346,14 @@ tcp_status fourierrec_tables_owned(const double* theta, int64_t nt, int64_t nd, 
     owned->push_back(nt_.off);
     owned->push_back(nt_.ent);
     owned->push_back(nt_.heavy);
+    owned->push_back(nt_.warps);
   }
   t->t_near = nt_.t_near;
   t->near_off = nt_.off;
   t->near_ent = nt_.ent;
   t->n_heavy = nt_.n_heavy;
   t->near_heavy = nt_.heavy;
+  t->near_warps = nt_.warps;
   return TCP_OK;
 }
 

@@ -200,6 +200,7 @@ struct FrecTables {
   const int2* near_ent = nullptr;     // (P offset, weight bits)
   int64_t n_heavy = 0;                // rows with more than 4096 entries, one CTA each
   const int64_t* near_heavy = nullptr;
+  const unsigned char* near_warps = nullptr;  // near flag per gather warp (512 rows each)
 };
 struct FrecWorkspace {
   void *geom = nullptr, *phase = nullptr, *P = nullptr, *H = nullptr, *G = nullptr;
