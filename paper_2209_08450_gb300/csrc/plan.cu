@@ -7,7 +7,11 @@
 // input or output, the staging rings with their copy streams and events.
 // Calls that take a plan allocate nothing, never synchronise and only
 // enqueue work, so their first use may be captured into a CUDA graph.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "tcp_internal.cuh"
@@ -64,6 +68,29 @@ tcp_status plan_stream(tcp_plan* pl, cudaStream_t* s) {
   if (r != cudaSuccess) return cuda_fail(r, "plan: cudaStreamCreate");
   pl->streams.push_back(*s);
   return TCP_OK;
+}
+
+// Bytes of the device allocations in `owned` (each pointer starts one
+// cudaMalloc allocation), from the driver's address ranges; 0 where the entry
+// point is unavailable.
+size_t owned_bytes(const std::vector<void*>& owned) {
+  static std::once_flag once;
+  static PFN_cuMemGetAddressRange_v3020 range = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 3020, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      range = reinterpret_cast<PFN_cuMemGetAddressRange_v3020>(f);
+  });
+  size_t total = 0;
+  if (!range) return 0;
+  for (void* p : owned) {
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    if (p && range(&base, &size, (CUdeviceptr)p) == CUDA_SUCCESS) total += size;
+  }
+  return total;
 }
 
 #define PTRY(x)                    \
@@ -137,6 +164,10 @@ tcp_status plan_build(tcp_plan* pl, const double* theta) {
   // the device error word's address is looked up here, not during a capture
   if (!device_error_word()) return fail(TCP_ERR_CUDA, "plan: device error word unavailable");
   TCP_CUDA_TRY(cudaDeviceSynchronize());
+  // every device allocation of the plan, its buffers (counted as they were
+  // made) and its tables (angles, filters, FourierRec and LpRec geometry)
+  const size_t all = owned_bytes(pl->owned);
+  if (all > pl->bytes) pl->bytes = all;
   return TCP_OK;
 }
 
