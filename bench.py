@@ -421,6 +421,9 @@ def measure_rows(dev) -> dict:
         return a.elapsed_time(b) / reps
 
     out = {}
+    # LineRec's ceiling (interpolations/s), as in bp_roofline: FP32 lanes x max clock / 2
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_ceiling = sms * 128 * float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 2
     # a7: gradient descent on ||P x - y||^2 through the autograd pair
     n, nz, nt = 512, 64, 720
     theta = synth.uniform_theta(nt)
@@ -443,7 +446,9 @@ def measure_rows(dev) -> dict:
         "workload": "512x512x64 ellipsoids, 720 angles, 512-pixel detector, sigma 1e-2, 50 GD iterations",
         "seconds_50_iterations": wall, "loss_ratio_50": losses[-1] / losses[0],
         "project_ms": pj, "backproject_ms": bj, "project_ginterp_s": interps / pj / 1e6,
-        "backproject_ginterp_s": interps / bj / 1e6}
+        "backproject_ginterp_s": interps / bj / 1e6,
+        "project_frac_of_fma_ceiling": interps / (pj * 1e-3) / fma_ceiling,
+        "backproject_frac_of_fma_ceiling": interps / (bj * 1e-3) / fma_ceiling}
     del x_true, y, x
     # a8: six uneven stacks, FP16 storage, one graph replay
     widths = (512, 768, 1024, 1536, 2048, 2560)
@@ -475,6 +480,7 @@ def measure_rows(dev) -> dict:
     out["a8_uneven_batch"] = {
         "workload": "6 stacks x 32 slices, widths 512-2560, 400-3000 angles, FP16 sinograms, one graph replay",
         "ms_per_replay": ms, "gvoxel_s": vox / ms / 1e6, "ginterp_s": interps / ms / 1e6,
+        "frac_of_fma_ceiling": interps / (ms * 1e-3) / fma_ceiling,
         "config": info["config"], "tuned_ms": info["tuned_ms"], "grid_blocks": info["grid_blocks"],
         "work_units": info["work_units"]}
     b.close()
