@@ -67,6 +67,19 @@ def test_fourierrec_fp32_many_strips(nz, nt, nd, n, center):
     assert rel(got, fr.backproject_gridding(q, theta, center, n, width=7)) <= 5e-6
 
 
+
+def test_fourierrec_ten_pairs_in_one_batch_with_a_partial_near_region():
+    # 19 slices = 10 slice pairs in one batch (the near-node table's pairs are
+    # applied 8 at a time: two passes, an unpaired last slice), and a 1024-point
+    # grid whose nodes within 128 of the zero frequency come from the table
+    # while the rest are gathered
+    nz, nt, nd, n, c = 19, 90, 300, 300, 151.3
+    q, theta = _case(nz, nt, nd, 77)
+    got = host(tcp.fourierrec(to_dev(q), theta, c, n=n))
+    for z in (0, 9, 18):
+        want = fr.backproject_gridding(q[z:z + 1], theta, c, n, width=10)
+        assert rel(got[z:z + 1], want) <= 1e-5
+
 def test_fourierrec_width_controls_error():
     q, theta = _case(2, 24, 32, 11)
     exact = fr.backproject_exact(q, theta, 16.3, 32)
