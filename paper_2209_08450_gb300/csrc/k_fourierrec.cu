@@ -483,8 +483,9 @@ __global__ void __launch_bounds__(256) k_frec_gather(int W, const float2* __rest
 // ---------------------------------------------- near-node sparse table --
 //
 // The nodes of near warps (within ~kCoopRadius of the zero frequency, where
-// every angle contributes) take most of the gather's time, and their window
-// weights do not depend on the data: they are listed once per geometry as a
+// every angle contributes) cost the gather far more per node than any other,
+// and their window weights do not depend on the data: they are listed once
+// per geometry as a
 // sparse table, row = node (16 rows per lane block, 8 warps x 32 lanes per
 // tile, tiles in gather order), entries (P offset within a slice pair,
 // weight wx * wy), in the gather's visiting order (images, sorted angles, k).
