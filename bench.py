@@ -277,6 +277,7 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     out = {"bound": "alu", "achieved": ach / 1e9, "peak": fma_ceiling / 1e9, "unit": "Ginterp/s",
            "frac": ach / fma_ceiling, "traffic": traffic, "traffic_source": tsrc, "ms_per_launch": ms,
            "interps_per_launch": interps, "algorithmic_bytes_per_launch": None,
+           "kernel_only_gvoxel_s": nz * n * n / (ms * 1e-3) / 1e9,
            "peak_basis": "FP32 FMA ceiling of LineRec: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock) / 2 "
                          "operations per interpolation (derived from the lane count and clock; no measured FP32 "
                          "peak exists)" % (sms, clk_max)}
