@@ -27,8 +27,18 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+# Units that instantiate many kernel templates (measured 30-75 s each); they
+# start first so that parallel compilation does not wait on one started last.
+SLOW_FIRST = ("k_filter", "k_backproject_f32_", "k_backproject_f16", "k_backproject_bf16", "k_fourierrec")
+
+
 def sources() -> list[str]:
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    """Every .cu file, the slow units first, then by size."""
+    def key(path: str):
+        name = os.path.basename(path)
+        rank = next((i for i, p in enumerate(SLOW_FIRST) if name.startswith(p)), len(SLOW_FIRST))
+        return (rank, -os.path.getsize(path), name)
+    return sorted((os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu")), key=key)
 
 
 def _deps() -> list[str]:

@@ -1,0 +1,9 @@
+// CUDA-core LineRec backprojector kernels for FP16 sinograms (every
+// configuration and volume dtype), instantiated in a unit of their own.
+#include "k_backproject_impl.cuh"
+
+namespace tcp {
+
+KernPair bp_pick_f16(int vdt, const tcp_bp_config& c, bool check) { return pick_vol<__half>(vdt, c, check); }
+
+}  // namespace tcp
