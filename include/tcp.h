@@ -138,8 +138,9 @@ tcp_status tcp_device_check(void* stream, uint32_t* word);
 /* Turn per-access index checks on (1) or off (0) for later launches. */
 tcp_status tcp_set_checked(int32_t on);
 
-/* Free every cached angle table, filter response and FourierRec table
- * (twiddles, deconvolution factors, sorted angles); synchronises the device. */
+/* Free every cached angle table, filter response, FourierRec table
+ * (twiddles, deconvolution factors, sorted angles, near-node weight tables)
+ * and LpRec geometry; synchronises the device. */
 tcp_status tcp_cache_clear(void);
 
 /* ------------------------------------------------------------- normalise -- */
