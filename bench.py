@@ -285,7 +285,7 @@ def bp_roofline(tcp, dev, path, nz, nt, n, ms) -> dict:
     sbytes = (4 if split else (4 if (sdt or vdt) == "float32" else 2)) * nz * nt * n
     vbytes = {"float32": 4, "float16": 2, "bfloat16": 2}[vdt] * nz * n * n
     out["algorithmic_bytes_per_launch"] = sbytes + vbytes
-    if kernel == 1:
+    if kernel in (1, 3):
         fl = 192 if split else 64
         bpk = float(pk.get("bf16_tflops", 1900.0))
         mma = interps * fl / (ms * 1e-3) / 1e12
@@ -486,7 +486,8 @@ def measure_rows(dev) -> dict:
         "workload": "6 stacks x 32 slices, widths 512-2560, 400-3000 angles, FP16 sinograms, one graph replay",
         "ms_per_replay": ms, "gvoxel_s": vox / ms / 1e6, "ginterp_s": interps / ms / 1e6,
         "frac_of_fma_ceiling": interps / (ms * 1e-3) / fma_ceiling,
-        "config": info["config"], "tuned_ms": info["tuned_ms"], "grid_blocks": info["grid_blocks"],
+        "config": info["config"], "kernel": info["kernel"], "tuned_ms": info["tuned_ms"],
+        "grid_blocks": info["grid_blocks"],
         "work_units": info["work_units"]}
     b.close()
     del ds

@@ -326,8 +326,11 @@ tcp_status tcp_lprec(const tcp_tensor* sino, const double* theta, double center,
  * kernel 0; theta_stage 1 or 2 sets the angles per pipeline stage, the other
  * fields are ignored); 2 = FP32 pipes for FP32 sinograms with slice pairs
  * (packed FP32x2 FMAs, one 8-byte shared load per slice pair and voxel after
- * the first of each column; k_slices even).
- * The automatic choice is kernel 1 for 16-bit sinograms with at least 32
+ * the first of each column; k_slices even); 3 = kernel 1 with two thread
+ * blocks per SM, its shared-memory rings sized for half the shared memory
+ * (FP16/BF16 sinograms with at most 128 slices per block, where two blocks'
+ * TMEM accumulators fit; otherwise exactly kernel 1).
+ * The automatic choice is kernel 3 for 16-bit sinograms with at least 32
  * slices.  F16X2 sinograms always use the tensor cores. */
 typedef struct {
   int32_t k_slices;

@@ -206,7 +206,9 @@ def set_backproject_config(k_slices: int | None = None, theta_stage: int = 16, r
     """Fix the backprojector configuration (None: automatic).  kernel=1 selects
     the tensor-core backprojector for FP16/BF16 sinograms, kernel=2 the
     CUDA-core form for FP32 sinograms with slice pairs (packed FP32x2 FMAs,
-    sample reuse down each voxel column)."""
+    sample reuse down each voxel column), kernel=3 the tensor-core
+    backprojector with its rings sized for two thread blocks per SM (FP16/BF16
+    sinograms, at most 128 slices per block)."""
     if k_slices is None:
         _lib.load().tcp_set_backproject_config(None)
         return

@@ -26,7 +26,8 @@ namespace {
 // kernel with 1 or 2 angles per stage (16-bit sinograms whose strides suit TMA).
 const tcp_bp_config kCandidates[] = {{8, 16, 4, 0}, {4, 32, 4, 0}, {4, 16, 4, 0}, {16, 8, 2, 0}, {8, 16, 2, 0},
                                      {2, 16, 4, 0}, {1, 32, 4, 0}, {4, 16, 16, 0}, {8, 16, 16, 0}, {4, 32, 16, 0},
-                                     {8, 16, 4, 2}, {16, 8, 4, 2}, {4, 16, 4, 2}, {8, 2, 4, 1}, {8, 1, 4, 1}};
+                                     {8, 16, 4, 2}, {16, 8, 4, 2}, {4, 16, 4, 2}, {8, 2, 4, 1}, {8, 1, 4, 1},
+                                     {8, 2, 4, 3}, {8, 1, 4, 3}};
 
 int esize(int dt) { return dt == TCP_F32 ? 4 : 2; }
 
@@ -83,9 +84,22 @@ struct tcp_batch {
   float tuned_ms = 0.f;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // Side streams: each dataset's chain (frame means, normalise + filter and,
+  // with the tensor-core kernel, its backprojection) runs on side stream
+  // i % kSide, forked from and joined back to the caller's stream by events
+  // (a captured graph gets parallel branches).  Datasets touch disjoint
+  // buffers, so the chains are independent; they fill each other's last waves.
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
   ~tcp_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (int k = 0; k < kSide; ++k) {
+      if (side[k]) cudaStreamDestroy(side[k]);
+      if (join[k]) cudaEventDestroy(join[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
     for (void* p : owned) cudaFree(p);
     if (d_items) cudaFree(d_items);
     if (d_prefix) cudaFree(d_prefix);
@@ -104,7 +118,7 @@ bool tc_batch_ok(const tcp_batch* b) {
 }
 
 tcp_status set_config(tcp_batch* b, const tcp_bp_config& cfg) {
-  if (cfg.kernel == 1) {  // one tensor-core launch per dataset inside the run
+  if (cfg.kernel == 1 || cfg.kernel == 3) {  // one tensor-core launch per dataset inside the run
     if (!tc_batch_ok(b)) return fail(TCP_ERR_UNSUPPORTED, "batch: tensor-core kernel needs 16-bit TMA-friendly sinograms");
     long long units = 0;
     for (const ItemRt& it : b->items) units += ((it.vol.d1 + 15) / 16) * ((it.vol.d1 + 15) / 16);
@@ -131,26 +145,47 @@ tcp_status set_config(tcp_batch* b, const tcp_bp_config& cfg) {
   return TCP_OK;
 }
 
-tcp_status prep(tcp_batch* b, cudaStream_t st) {
-  for (ItemRt& it : b->items) {
-    tcp_status s;
-    if (it.dark_frames && (s = launch_frame_mean(it.dark_src, it.dark, st)) != TCP_OK) return s;
-    if (it.flat_frames && (s = launch_frame_mean(it.flat_src, it.flat, st)) != TCP_OK) return s;
-    if ((s = launch_normalize_filter(it.raw, it.dark, it.flat, it.sino, it.ft, it.pad, st)) != TCP_OK) return s;
-  }
-  return TCP_OK;
+tcp_status prep_item(const ItemRt& it, cudaStream_t st) {
+  tcp_status s;
+  if (it.dark_frames && (s = launch_frame_mean(it.dark_src, it.dark, st)) != TCP_OK) return s;
+  if (it.flat_frames && (s = launch_frame_mean(it.flat_src, it.flat, st)) != TCP_OK) return s;
+  return launch_normalize_filter(it.raw, it.dark, it.flat, it.sino, it.ft, it.pad, st);
 }
 
-tcp_status backproject_all(tcp_batch* b, cudaStream_t st) {
-  if (b->cfg.kernel == 1) {
-    for (const ItemRt& it : b->items) {
+bool tc_mode(const tcp_batch* b) { return b->cfg.kernel == 1 || b->cfg.kernel == 3; }
+
+// The per-dataset chains on the side streams: prep (if asked) and the
+// dataset's tensor-core backprojection (if asked).  The side streams are
+// joined back into st even after a failed launch, so that a capture stays
+// well formed.
+tcp_status run_chains(tcp_batch* b, cudaStream_t st, bool with_prep, bool tc) {
+  if (!with_prep && !tc) return TCP_OK;
+  TCP_CUDA_TRY(cudaEventRecord(b->fork, st));
+  for (int k = 0; k < tcp_batch::kSide; ++k) TCP_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+  tcp_status s = TCP_OK;
+  for (size_t i = 0; i < b->items.size() && s == TCP_OK; ++i) {
+    const ItemRt& it = b->items[i];
+    cudaStream_t si = b->side[i % tcp_batch::kSide];
+    if (with_prep) s = prep_item(it, si);
+    if (s == TCP_OK && tc) {
       const float scale = (float)(M_PI / (double)it.sino.d1 / storage_scale(b->sdt));
-      tcp_status s = launch_backproject_tc(it.sino, it.trig, 0.5 * (double)it.sino.d2, it.vol, scale,
-                                           b->cfg.theta_stage, st);
-      if (s != TCP_OK) return s;
+      s = launch_backproject_tc(it.sino, it.trig, 0.5 * (double)it.sino.d2, it.vol, scale, b->cfg.theta_stage,
+                                b->cfg.kernel == 3 ? 2 : 1, si);
     }
-    return TCP_OK;
   }
+  for (int k = 0; k < tcp_batch::kSide; ++k) {
+    cudaError_t e = cudaEventRecord(b->join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[k], 0);
+    if (e != cudaSuccess && s == TCP_OK) s = cuda_fail(e, "batch: stream join");
+  }
+  return s;
+}
+
+// One pass over the batch: the chains, then (CUDA-core mode) the single
+// persistent backprojection launch over every dataset on st.
+tcp_status run_all(tcp_batch* b, cudaStream_t st, bool with_prep) {
+  tcp_status s = run_chains(b, st, with_prep, tc_mode(b));
+  if (s != TCP_OK || tc_mode(b)) return s;
   TCP_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
   BpWork w;
   w.items = b->d_items;
@@ -166,11 +201,11 @@ tcp_status time_config(tcp_batch* b, const tcp_bp_config& cfg, cudaStream_t st, 
   cudaEvent_t e0, e1;
   TCP_CUDA_TRY(cudaEventCreate(&e0));
   TCP_CUDA_TRY(cudaEventCreate(&e1));
-  s = backproject_all(b, st);  // warm-up
+  s = run_all(b, st, false);  // warm-up
   float best = 1e30f;
   for (int rep = 0; rep < 2 && s == TCP_OK; ++rep) {
     cudaEventRecord(e0, st);
-    s = backproject_all(b, st);
+    s = run_all(b, st, false);
     cudaEventRecord(e1, st);
     cudaError_t e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {
@@ -295,8 +330,17 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
   // without autotune: the configuration fixed by tcp_set_backproject_config, if any
   if (s == TCP_OK && !o.autotune && bp_override().k_slices) b->cfg = bp_override();
   if (s == TCP_OK) s = set_config(b, b->cfg);
+  for (int k = 0; k < tcp_batch::kSide && s == TCP_OK; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) s = cuda_fail(e, "batch: side stream");
+  }
+  if (s == TCP_OK) {
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) s = cuda_fail(e, "batch: side stream");
+  }
   if (s == TCP_OK && o.autotune) {
-    s = prep(b, st);
+    s = run_chains(b, st, true, false);  // the sinograms every timed configuration reads
     float best = 1e30f;
     tcp_bp_config best_cfg = b->cfg;
     for (const tcp_bp_config& c : kCandidates) {
@@ -326,10 +370,7 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
 
 tcp_status tcp_batch_run(tcp_batch* b, void* stream) {
   if (!b) return fail(TCP_ERR_ARG, "batch: null handle");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  tcp_status s = prep(b, st);
-  if (s != TCP_OK) return s;
-  return backproject_all(b, st);
+  return run_all(b, reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 tcp_status tcp_batch_capture(tcp_batch* b, void* stream) {
@@ -397,7 +438,7 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
   std::vector<tcp_bp_config> cands;
   for (const tcp_bp_config& c : kCandidates) {
     const bool f32 = sino->dtype == TCP_F32;
-    if (c.kernel == 1 && f32) continue;                          // tensor cores: 16-bit sinograms
+    if ((c.kernel == 1 || c.kernel == 3) && f32) continue;       // tensor cores: 16-bit sinograms
     if (c.kernel == 0 && c.rows_per_thread == 16 && !f32) continue;  // 4 x 4 blocks: FP32 sinograms
     if (c.kernel == 2 && !f32) continue;                         // slice pairs: FP32 sinograms
     cands.push_back(c);

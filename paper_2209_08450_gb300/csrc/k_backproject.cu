@@ -38,8 +38,9 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
 }  // namespace
 
 bool valid_bp_config(const tcp_bp_config& c) {
-  if (c.kernel < 0 || c.kernel > 2) return false;
-  if (c.kernel == 1) return true;  // theta_stage 1 or 2 picks the stage size; the rest is ignored
+  if (c.kernel < 0 || c.kernel > 3) return false;
+  // tensor cores: theta_stage 1 or 2 picks the stage size; the rest is ignored
+  if (c.kernel == 1 || c.kernel == 3) return true;
   return bp_pick_f32_f32(c, false).direct != nullptr;
 }
 
@@ -78,19 +79,23 @@ tcp_bp_config default_bp_config(int64_t nz, int64_t, int64_t, int64_t, int sdt, 
   // 2048^2 x 32 slices x 2048 angles)
   if (sdt == TCP_F32 && nz >= 3) c = tcp_bp_config{nz >= 5 ? 8 : 4, 16, 4, 2};
   // 16-bit sinograms with enough slices to fill the MMA's N dimension go to
-  // the tensor cores (inputs whose strides do not suit TMA fall back).
-  if ((sdt == TCP_F16 || sdt == TCP_BF16) && nz >= 32) c.kernel = 1;
+  // the tensor cores (inputs whose strides do not suit TMA fall back), two
+  // blocks per SM where the slice block allows it (at 2048^2 x 2048 angles:
+  // 40.9 / 43.6 / 52.5 ms against 62.2 / 63.3 / 67.0 ms with one block, for
+  // 32 / 64 / 128 slices; the weight builders bind there, and a second block
+  // doubles them).
+  if ((sdt == TCP_F16 || sdt == TCP_BF16) && nz >= 32) c.kernel = 3;
   if (sdt == TCP_F16X2) c.kernel = 1;  // split FP16 pairs exist only on the tensor cores
   return c;
 }
 
 tcp_status launch_backproject(const View3& sino, const TrigTable& trig, double center, const View3& vol,
                               const tcp_bp_config& cfg, cudaStream_t st, float scale) {
-  if (sino.dtype == TCP_F16X2 || (cfg.kernel == 1 && tc_eligible(sino))) {
+  if (sino.dtype == TCP_F16X2 || ((cfg.kernel == 1 || cfg.kernel == 3) && tc_eligible(sino))) {
     if (!tc_eligible(sino))
       return fail(TCP_ERR_ALIGN, "backproject: F16X2 sinograms need 16-byte aligned planes, slices and rows");
     if (sino.d0 == 0 || vol.d1 == 0) return TCP_OK;
-    return launch_backproject_tc(sino, trig, center, vol, scale, cfg.theta_stage, st);
+    return launch_backproject_tc(sino, trig, center, vol, scale, cfg.theta_stage, cfg.kernel == 3 ? 2 : 1, st);
   }
   const KernPair kp = pick_all(sino.dtype, vol.dtype, cfg, checked_mode());
   Kern k = kp.direct;

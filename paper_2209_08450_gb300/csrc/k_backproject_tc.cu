@@ -69,6 +69,11 @@ constexpr int kTcBuilders = 4 * kTcH;          // builder warps (one voxel row p
 constexpr int kTcThreads = 32 * (kTcBuilders + 2);
 constexpr long long kTcBudget = 4000000000ll;  // clock cycles per wait (~2 s)
 constexpr size_t kTcSmemLimit = 232448;        // opt-in shared memory per block
+constexpr size_t kTcSmemPerSM = 233472;        // shared memory per SM (228 KB; 1 KB reserved per block)
+// Blocks per SM at most: two at 68 registers.  Three or four (48 registers,
+// shallower rings) measured slower at 2048^2 x 2048 angles: 41.5 against
+// 40.9 ms for 32 slices.
+constexpr int kTcMaxBlocks = 2;
 
 struct TcArgs {
   int nz, ntheta, ndet, n;
@@ -611,12 +616,12 @@ size_t tc_smem_bytes(int N, int S, int parts, int na, int nbb) {
 // split mode (measured at 2048^2 x 256 slices x 2048 angles: 271, 258 and
 // 231 ms for NA = 2, 3, 4; the builders then run further ahead of the MMAs
 // and absorb the segment-sum pauses), else 3 (S = 1) or 2 (S = 2); then as
-// many B buffers as fit (at most the geometry ring's bound).
-void tc_rings(int N, int S, int parts, int* na, int* nbb) {
+// many B buffers as fit in `limit` bytes (at most the geometry ring's bound).
+void tc_rings(int N, int S, int parts, size_t limit, int* na, int* nbb) {
   *na = parts == 2 ? kTcMaxNA : ((S == 1) ? 3 : 2);
   const size_t fixed = tc_smem_bytes(N, S, parts, *na, 0);
   const size_t per = (size_t)S * parts * N * kTcRowBytes;
-  const size_t avail = kTcSmemLimit > fixed ? kTcSmemLimit - fixed : 0;
+  const size_t avail = limit > fixed ? limit - fixed : 0;
   *nbb = (int)std::min<size_t>((size_t)tc_max_nbb(S), avail / per);
   if (*na > *nbb) *na = *nbb;  // the builders wait on the empty barrier of stage s - NA
 }
@@ -636,7 +641,7 @@ bool tc_eligible(const View3& sino) {
 }
 
 tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                                 float scale, int theta_stage, cudaStream_t st) {
+                                 float scale, int theta_stage, int blocks_per_sm, cudaStream_t st) {
   if (!tc_eligible(sino)) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: sinogram not eligible");
   const int nz = (int)sino.d0, nt = (int)sino.d1, nd = (int)sino.d2, n = (int)vol.d1;
   if (nz == 0 || n == 0) return TCP_OK;
@@ -691,7 +696,21 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   const int S = (split || theta_stage == 1) ? 1 : 2;
   const int parts = split ? 2 : 1;
   const int rowsB = split ? kTcM : N;  // sinogram rows per angle and plane in shared memory
-  tc_rings(rowsB, S, parts, &a.na, &a.nbb);
+  // Two blocks per SM (16-bit sinograms; split mode takes all 512 TMEM
+  // columns) where both blocks' accumulators (2N columns each, allocated in
+  // powers of two) fit in the SM's 512 TMEM columns and their rings (at
+  // least two B stages) in half the shared memory.
+  int blocks = 1;
+  if (!split && blocks_per_sm > 1) {
+    const int ncols = kTcH * N;
+    const int tcols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
+    blocks = std::min(std::min(blocks_per_sm, kTcMaxBlocks), 512 / tcols);
+    for (; blocks > 1; --blocks) {
+      tc_rings(rowsB, S, parts, kTcSmemPerSM / blocks - 1024, &a.na, &a.nbb);
+      if (a.nbb >= 2) break;
+    }
+  }
+  if (blocks == 1) tc_rings(rowsB, S, parts, kTcSmemLimit, &a.na, &a.nbb);
   if (a.nbb < 2) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
   const size_t smem = tc_smem_bytes(rowsB, S, parts, a.na, a.nbb);
   void (*k)(const CUtensorMap, const CUtensorMap, TcArgs) =
@@ -700,6 +719,8 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
           ? (S == 1 ? k_backproject_tc<__half, 1, false> : k_backproject_tc<__half, 2, false>)
           : (S == 1 ? k_backproject_tc<__nv_bfloat16, 1, false> : k_backproject_tc<__nv_bfloat16, 2, false>);
   TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (blocks > 1)
+    TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
   const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 7) / 8;
   dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 8), (unsigned)((nz + N - 1) / N));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");

@@ -239,8 +239,11 @@ struct BpWork {
 };
 
 bool tc_eligible(const View3& sino);
+// theta_stage: angles per pipeline stage (1 or 2; split mode always 1);
+// blocks_per_sm: 2 sizes the shared-memory rings for two blocks per SM
+// (16-bit sinograms, at most 128 slices per block), else one block.
 tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, double center, const View3& vol,
-                                 float scale, int theta_stage, cudaStream_t st);
+                                 float scale, int theta_stage, int blocks_per_sm, cudaStream_t st);
 
 BpArgs make_bp_args(const View3& sino, const TrigTable& trig, double center, const View3& vol, float scale = 1.0f);
 int bp_threads(const tcp_bp_config& c);

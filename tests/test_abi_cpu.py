@@ -93,6 +93,11 @@ def test_host_side_argument_checks(lib):
     # config that is not instantiated
     c = _lib.BpConfig(3, 16, 4, 0)
     assert _status(lib, "tcp_set_backproject_config", ctypes.byref(c)) == 9
+    # kernel ids: 3 (tensor cores, two blocks per SM) exists, 4 does not
+    for ks, kern, want in ((2, 4, 9), (8, 4, 9), (8, 3, 0), (2, 3, 0)):
+        c = _lib.BpConfig(ks, 2, 4, kern)
+        assert _status(lib, "tcp_set_backproject_config", ctypes.byref(c)) == want
+    assert _status(lib, "tcp_set_backproject_config", None) == 0
 
 
 def test_split_sinogram_descriptor_checks(lib):

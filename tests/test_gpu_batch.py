@@ -68,12 +68,13 @@ def test_uneven_batch_graph_replay_matches_oracle():
     b = Batch(ds, sino_dtype=torch.float16, autotune=True)
     info = b.info()
     # the autotuner picks among the CUDA-core configurations (one persistent
-    # launch) and the tensor-core kernel (one launch per dataset)
+    # launch) and the tensor-core kernel (one launch per dataset, one or two
+    # blocks per SM)
     if info["kernel"] == 0:
         assert info["config"] in {(8, 16, 4), (4, 32, 4), (4, 16, 4), (16, 8, 2), (8, 16, 2), (2, 16, 4), (1, 32, 4)}
         assert info["grid_blocks"] >= 152
     else:
-        assert info["kernel"] == 1 and info["config"][1] in (1, 2)
+        assert info["kernel"] in (1, 3) and info["config"][1] in (1, 2)
     assert info["tuned_ms"] > 0
     print("\nbatch autotune: kernel %d config %s, %.1f ms" % (info["kernel"], info["config"], info["tuned_ms"]))
     s = torch.cuda.Stream()
@@ -112,9 +113,10 @@ def test_batch_of_one_equals_fbp_and_fp32_sinogram():
 
 def test_uneven_batch_on_each_kernel_matches_oracle():
     # both backprojectors of a batch, forced: the persistent CUDA-core launch
-    # and the tensor-core launches, on three of the uneven shapes
+    # and the tensor-core launches (one and two blocks per SM), on three of
+    # the uneven shapes
     ds = _datasets((512, 1536, 2560), (400, 1800, 3000), 32, seed0=20)
-    for cfg in ((8, 16, 4, 0), (8, 2, 4, 1)):
+    for cfg in ((8, 16, 4, 0), (8, 2, 4, 1), (8, 1, 4, 3)):
         b = Batch(ds, sino_dtype=torch.float16, autotune=False, config=cfg)
         assert b.info()["kernel"] == cfg[3]
         b.run()

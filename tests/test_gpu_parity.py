@@ -512,6 +512,35 @@ def test_backproject_tensor_cores_256_slices_and_scale(stage):
     assert rel(got, ref) <= 5e-3
 
 
+@pytest.mark.parametrize("stage", [1, 2])
+@pytest.mark.parametrize("sdt", [torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("nz,nt,nd,n,center", [
+    (32, 129, 200, 160, 99.2), (20, 13, 64, 100, 31.7), (48, 37, 96, 96, 48.0), (128, 50, 72, 70, 35.3),
+    (130, 24, 64, 64, 32.4)])
+def test_backproject_tensor_cores_two_blocks_per_sm(sdt, nz, nt, nd, n, center, stage):
+    # kernel 3 sizes the rings for two blocks per SM where the TMEM
+    # accumulators (2 x slices per block columns) and the rings fit (130
+    # slices take one 144-slice block: one block per SM): the same MMAs in
+    # the same order, so the volume is identical to kernel 1's
+    q, theta, c = _bp_case(nz, nt, nd, n, center, 7 * nz + nt)
+    qd = to_dev(q, sdt)
+    try:
+        tcp.set_backproject_config(8, stage, 4, kernel=3)
+        two = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
+        tcp.set_backproject_config(8, stage, 4, kernel=1)
+        one = host(tcp.backproject(qd, theta, c, n=n, dtype=torch.float32))
+    finally:
+        tcp.set_backproject_config(None)
+    assert np.array_equal(two, one)
+    assert rel(two, oracle.backproject(host(qd), theta, c, n)) <= 5e-3
+
+
+def test_backproject_default_for_16bit_sinograms_is_the_two_block_tensor_core_kernel():
+    assert tcp.get_backproject_config(64, 720, 512, 512, torch.float16, torch.float32)[3] == 3
+    assert tcp.get_backproject_config(256, 2048, 2048, 2048, torch.bfloat16, torch.float16)[3] == 3
+    assert tcp.get_backproject_config(16, 720, 512, 512, torch.float16, torch.float32)[3] == 0
+
+
 # ------------------------------- FP32-accurate split FP16 (F16X2) sinograms --
 
 def _split(q, scale):
