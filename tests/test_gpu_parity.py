@@ -260,10 +260,12 @@ def test_backproject_large_detector_offsets():
 # ----------------------------------------------------------------- project --
 
 @pytest.mark.parametrize("nz,nt,nd,n,center", [(5, 67, 91, 80, 44.6), (9, 30, 40, 64, 33.0), (1, 5, 17, 9, 8.2),
-                                               (21, 50, 70, 64, 33.3), (32, 19, 48, 40, 20.0), (16, 9, 24, 33, 12.5)])
+                                               (21, 50, 70, 64, 33.3), (32, 19, 48, 40, 20.0), (16, 9, 24, 33, 12.5),
+                                               (16, 11, 31, 40, 15.2), (16, 13, 62, 50, 30.9), (16, 7, 63, 48, -3.0)])
 def test_project_fp32(nz, nt, nd, n, center):
     # 16-slice groups read the slice-interleaved copies, the remainder the plain
-    # and transposed volume (21 = 16 + 4 + 1)
+    # and transposed volume (21 = 16 + 4 + 1); widths 31, 62 and 63 end in a
+    # partial 32-bin warp, and a centre of -3 puts bin 0 inside the object
     rng = np.random.default_rng(nz + nt)
     vol = rng.normal(size=(nz, n, n))
     theta = rng.uniform(0, np.pi, nt)
