@@ -345,6 +345,27 @@ tcp_status tcp_set_backproject_config(const tcp_bp_config* cfg);
 tcp_status tcp_get_backproject_config(int64_t nz, int64_t ntheta, int64_t ndet, int64_t n,
                                       int32_t sino_dtype, int32_t vol_dtype, tcp_bp_config* cfg);
 
+/* Launch shape of the tensor-core backprojector (kernels 1 and 3) for nz
+ * slices of FP16, BF16 or F16X2 sinograms: host arithmetic only, no device
+ * work.  theta_stage 1 or 2 (angles per pipeline stage; F16X2 always 1),
+ * blocks_per_sm 1 or 2 (kernel 1 or 3).  Fills slices_per_block (the MMA's
+ * slice dimension, a multiple of 16, at most 256, 128 for F16X2),
+ * angles_per_stage, blocks_per_sm (2 only where two blocks' TMEM
+ * accumulators, 2 x slices_per_block columns each, fit in 512 columns and
+ * their rings in half the shared memory), weight_stages, sinogram_stages and
+ * smem_bytes (dynamic shared memory per block).  TCP_ERR_ARG for a null
+ * shape or nz < 1, TCP_ERR_DTYPE for other sinogram dtypes. */
+typedef struct {
+  int32_t slices_per_block;
+  int32_t angles_per_stage;
+  int32_t blocks_per_sm;
+  int32_t weight_stages;
+  int32_t sinogram_stages;
+  int64_t smem_bytes;
+} tcp_tc_shape;
+tcp_status tcp_tc_launch_shape(int64_t nz, int32_t sino_dtype, int32_t theta_stage, int32_t blocks_per_sm,
+                               tcp_tc_shape* shape);
+
 /* ------------------------------------------------------------- pipeline -- */
 
 typedef struct {

@@ -23,7 +23,7 @@ from ._lib import TcpError, load  # noqa: F401
 
 __all__ = ["frame_mean", "normalize", "normalize_filter", "angle_major", "filter_", "backproject", "project", "fourierrec", "device_check",
            "set_checked", "cache_clear", "set_backproject_config", "get_backproject_config",
-           "TcpError", "load", "padded_length"]
+           "TcpError", "load", "padded_length", "tc_launch_shape"]
 
 
 def _as_u16(t: torch.Tensor) -> torch.Tensor:
@@ -37,6 +37,16 @@ def padded_length(ndet: int, smooth: bool = False) -> int:
     two >= 2 ndet; with `smooth`, the smallest of that, the next 3 * 2^k
     (from 48 on) and the next 5 * 2^k (from 80 on) >= 2 ndet."""
     return int(_lib.load().tcp_padded_length(int(ndet), _lib.PADS["edge_smooth" if smooth else "edge"]))
+
+
+def tc_launch_shape(nz: int, sino_dtype=torch.float16, theta_stage: int = 2, blocks_per_sm: int = 2) -> dict:
+    """Launch shape of the tensor-core backprojector (tcp_tc_launch_shape) for
+    nz slices: slices per block, angles per stage, blocks per SM, ring depths
+    and shared memory per block.  sino_dtype: float16, bfloat16 or "f16x2"."""
+    sh = _lib.TcShape()
+    _lib.call("tcp_tc_launch_shape", int(nz), _lib.dtype_code(sino_dtype), int(theta_stage), int(blocks_per_sm),
+              ctypes.byref(sh))
+    return {f: getattr(sh, f) for f, _ in _lib.TcShape._fields_}
 
 
 def frame_mean(frames: torch.Tensor, stream=None) -> torch.Tensor:

@@ -58,6 +58,12 @@ class BpConfig(ctypes.Structure):
                 ("rows_per_thread", ctypes.c_int32), ("kernel", ctypes.c_int32)]
 
 
+class TcShape(ctypes.Structure):
+    _fields_ = [("slices_per_block", ctypes.c_int32), ("angles_per_stage", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("weight_stages", ctypes.c_int32),
+                ("sinogram_stages", ctypes.c_int32), ("smem_bytes", ctypes.c_int64)]
+
+
 class FbpOpts(ctypes.Structure):
     _fields_ = [("chunk_nz", ctypes.c_int32), ("sino_dtype", ctypes.c_int32), ("filter", ctypes.c_int32),
                 ("pad_mode", ctypes.c_int32), ("n_buffers", ctypes.c_int32), ("algorithm", ctypes.c_int32),
@@ -97,6 +103,7 @@ SIGNATURES = {
     "tcp_lprec": ([_T, _P, _D, _T, _D, _D, _P], _I32),
     "tcp_set_backproject_config": ([ctypes.POINTER(BpConfig)], _I32),
     "tcp_get_backproject_config": ([_I64, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(BpConfig)], _I32),
+    "tcp_tc_launch_shape": ([_I64, _I32, _I32, _I32, ctypes.POINTER(TcShape)], _I32),
     "tcp_fbp": ([_T, _T, _T, _P, _D, _T, ctypes.POINTER(FbpOpts), _P], _I32),
     "tcp_try_centers": ([_T, _I64, _T, _T, _P, _P, _I64, _T, _I32, _P], _I32),
     "tcp_try_centers_ex": ([_T, _I64, _T, _T, _P, _P, _I64, _T, _I32, _I32, _I32, _P], _I32),

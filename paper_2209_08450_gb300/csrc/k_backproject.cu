@@ -37,6 +37,28 @@ KernPair pick_all(int sdt, int vdt, const tcp_bp_config& c, bool check) {
 
 }  // namespace
 
+}  // namespace tcp
+
+extern "C" tcp_status tcp_tc_launch_shape(int64_t nz, int32_t sino_dtype, int32_t theta_stage, int32_t blocks_per_sm,
+                                          tcp_tc_shape* shape) {
+  using namespace tcp;
+  if (!shape || nz < 1) return fail(TCP_ERR_ARG, "tc_launch_shape: null shape or nz < 1");
+  if (sino_dtype != TCP_F16 && sino_dtype != TCP_BF16 && sino_dtype != TCP_F16X2)
+    return fail(TCP_ERR_DTYPE, "tc_launch_shape: sinogram dtype must be F16, BF16 or F16X2");
+  TcShape sh;
+  if (!tc_shape(nz, sino_dtype == TCP_F16X2, theta_stage, blocks_per_sm, &sh))
+    return fail(TCP_ERR_UNSUPPORTED, "tc_launch_shape: shared memory too small for the rings");
+  shape->slices_per_block = sh.N;
+  shape->angles_per_stage = sh.S;
+  shape->blocks_per_sm = sh.blocks;
+  shape->weight_stages = sh.na;
+  shape->sinogram_stages = sh.nbb;
+  shape->smem_bytes = (int64_t)sh.smem;
+  return TCP_OK;
+}
+
+namespace tcp {
+
 bool valid_bp_config(const tcp_bp_config& c) {
   if (c.kernel < 0 || c.kernel > 3) return false;
   // tensor cores: theta_stage 1 or 2 picks the stage size; the rest is ignored

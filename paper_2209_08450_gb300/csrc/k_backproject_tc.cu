@@ -631,6 +631,32 @@ int tc_slices(int64_t nz, bool split) {
   return (int)std::min<int64_t>(split ? 128 : 256, std::max<int64_t>(16, r));
 }
 
+// Launch shape of one call: slices per block N, angles per stage S, blocks
+// per SM and ring depths, and the dynamic shared memory per block.  Two
+// blocks per SM (16-bit sinograms; split mode takes all 512 TMEM columns)
+// where both blocks' accumulators (2N columns each, allocated in powers of
+// two) fit in the SM's 512 TMEM columns and their rings (at least two B
+// stages) in half the shared memory.  False if no ring of two B stages fits.
+bool tc_shape(int64_t nz, bool split, int theta_stage, int blocks_per_sm, TcShape* sh) {
+  sh->N = tc_slices(nz, split);
+  sh->S = (split || theta_stage == 1) ? 1 : 2;  // split mode: one angle per stage (its A and B are twice as large)
+  const int parts = split ? 2 : 1;
+  const int rowsB = split ? kTcM : sh->N;  // sinogram rows per angle and plane in shared memory
+  sh->blocks = 1;
+  if (!split && blocks_per_sm > 1) {
+    const int ncols = kTcH * sh->N;
+    const int tcols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
+    sh->blocks = std::min(std::min(blocks_per_sm, kTcMaxBlocks), 512 / tcols);
+    for (; sh->blocks > 1; --sh->blocks) {
+      tc_rings(rowsB, sh->S, parts, kTcSmemPerSM / sh->blocks - 1024, &sh->na, &sh->nbb);
+      if (sh->nbb >= 2) break;
+    }
+  }
+  if (sh->blocks == 1) tc_rings(rowsB, sh->S, parts, kTcSmemLimit, &sh->na, &sh->nbb);
+  sh->smem = tc_smem_bytes(rowsB, sh->S, parts, sh->na, sh->nbb);
+  return sh->nbb >= 2;
+}
+
 bool tc_eligible(const View3& sino) {
   if (sino.dtype != TCP_F16 && sino.dtype != TCP_BF16 && sino.dtype != TCP_F16X2) return false;
   if ((uintptr_t)sino.p % 16 != 0) return false;
@@ -646,7 +672,10 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   const int nz = (int)sino.d0, nt = (int)sino.d1, nd = (int)sino.d2, n = (int)vol.d1;
   if (nz == 0 || n == 0) return TCP_OK;
   const bool split = sino.dtype == TCP_F16X2;
-  const int N = tc_slices(nz, split);
+  TcShape sh;
+  if (!tc_shape(nz, split, theta_stage, blocks_per_sm, &sh))
+    return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
+  const int N = sh.N, S = sh.S;
   CUtensorMap map, map_lo;
   // The map's outer dimensions follow the memory order: an angle-major chunk
   // ([angle][slice][sample], slice stride < angle stride) keeps the N rows of
@@ -692,27 +721,10 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
   a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((mmaN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   a.err = device_error_word();
   a.check = checked_mode() ? 1 : 0;
-  // split mode: one angle per stage (its A and B are twice as large)
-  const int S = (split || theta_stage == 1) ? 1 : 2;
-  const int parts = split ? 2 : 1;
-  const int rowsB = split ? kTcM : N;  // sinogram rows per angle and plane in shared memory
-  // Two blocks per SM (16-bit sinograms; split mode takes all 512 TMEM
-  // columns) where both blocks' accumulators (2N columns each, allocated in
-  // powers of two) fit in the SM's 512 TMEM columns and their rings (at
-  // least two B stages) in half the shared memory.
-  int blocks = 1;
-  if (!split && blocks_per_sm > 1) {
-    const int ncols = kTcH * N;
-    const int tcols = ncols <= 32 ? 32 : (ncols <= 64 ? 64 : (ncols <= 128 ? 128 : (ncols <= 256 ? 256 : 512)));
-    blocks = std::min(std::min(blocks_per_sm, kTcMaxBlocks), 512 / tcols);
-    for (; blocks > 1; --blocks) {
-      tc_rings(rowsB, S, parts, kTcSmemPerSM / blocks - 1024, &a.na, &a.nbb);
-      if (a.nbb >= 2) break;
-    }
-  }
-  if (blocks == 1) tc_rings(rowsB, S, parts, kTcSmemLimit, &a.na, &a.nbb);
-  if (a.nbb < 2) return fail(TCP_ERR_UNSUPPORTED, "tensor-core backprojector: shared memory too small for its rings");
-  const size_t smem = tc_smem_bytes(rowsB, S, parts, a.na, a.nbb);
+  a.na = sh.na;
+  a.nbb = sh.nbb;
+  const int blocks = sh.blocks;
+  const size_t smem = sh.smem;
   void (*k)(const CUtensorMap, const CUtensorMap, TcArgs) =
       split ? k_backproject_tc<__half, 1, true>
       : sino.dtype == TCP_F16

@@ -239,6 +239,14 @@ struct BpWork {
 };
 
 bool tc_eligible(const View3& sino);
+// Launch shape of the tensor-core backprojector for nz slices: slices per
+// block N, angles per stage S, blocks per SM, weight (na) and sinogram (nbb)
+// ring depths, dynamic shared memory per block.  False if no ring fits.
+struct TcShape {
+  int N = 0, S = 0, blocks = 0, na = 0, nbb = 0;
+  size_t smem = 0;
+};
+bool tc_shape(int64_t nz, bool split, int theta_stage, int blocks_per_sm, TcShape* sh);
 // theta_stage: angles per pipeline stage (1 or 2; split mode always 1);
 // blocks_per_sm: 2 sizes the shared-memory rings for two blocks per SM
 // (16-bit sinograms, at most 128 slices per block), else one block.

@@ -297,3 +297,51 @@ def test_padded_length_matches_the_oracle_rule(lib):
         assert lib.tcp_padded_length(nd, 0) == oracle.padded_length(nd)
         assert lib.tcp_padded_length(nd, 2) == oracle.padded_length(nd, "smooth"), nd
     assert lib.tcp_padded_length(0, 0) == -1
+
+
+def _tc_shape(lib, nz, sdt, stage, blocks):
+    sh = _lib.TcShape()
+    st = lib.tcp_tc_launch_shape(nz, sdt, stage, blocks, ctypes.byref(sh))
+    return st, (sh.slices_per_block, sh.angles_per_stage, sh.blocks_per_sm, sh.weight_stages,
+                sh.sinogram_stages, sh.smem_bytes)
+
+
+@pytest.mark.parametrize("nz,sdt,stage,blocks,want", [
+    # FP16, 32 slices, two angles per stage: two blocks per SM fit (2 x 64
+    # TMEM columns; rings in half of the 228 KB: 2 weight + 11 sinogram
+    # stages, 113440 bytes), one block takes 16 sinogram stages
+    (32, _lib.F16, 2, 2, (32, 2, 2, 2, 11, 113440)),
+    (32, _lib.F16, 2, 1, (32, 2, 1, 2, 16, 133920)),
+    (20, _lib.BF16, 2, 2, (32, 2, 2, 2, 11, 113440)),
+    (1, _lib.F16, 1, 2, (16, 1, 2, 3, 32, 84768)),
+    # 128 slices: 256 TMEM columns each, two blocks with two sinogram stages
+    (128, _lib.F16, 2, 2, (128, 2, 2, 2, 2, 101152)),
+    # 144- and 256-slice blocks need more than half the TMEM: one block
+    (130, _lib.F16, 1, 2, (144, 1, 1, 3, 19, 227104)),
+    (256, _lib.F16, 2, 2, (256, 2, 1, 2, 5, 232224)),
+    # FP16 hi/lo pairs: 128 slices, one angle per stage, 4 weight + 6 sinogram
+    # stages of both planes, always one block (accumulators and sums fill TMEM)
+    (256, _lib.F16X2, 2, 2, (128, 1, 1, 4, 6, 232224)),
+])
+def test_tensor_core_launch_shape(lib, nz, sdt, stage, blocks, want):
+    st, got = _tc_shape(lib, nz, sdt, stage, blocks)
+    assert st == 0 and got == want
+    assert got[5] <= 232448  # opt-in shared memory per block
+    if got[2] == 2:
+        assert 2 * (got[5] + 1024) <= 233472  # two blocks per SM, 1 KB reserved each
+        assert 2 * (2 * got[0]) <= 512        # both blocks' TMEM accumulators
+
+
+def test_tensor_core_launch_shape_errors(lib):
+    assert _tc_shape(lib, 0, _lib.F16, 2, 2)[0] == 1
+    assert _tc_shape(lib, 32, _lib.F32, 2, 2)[0] == 3
+    assert lib.tcp_tc_launch_shape(32, _lib.F16, 2, 2, None) == 1
+
+
+def test_tensor_core_launch_shape_from_python():
+    import torch
+
+    import paper_2209_08450_gb300 as tcp
+    sh = tcp.tc_launch_shape(32, torch.float16)
+    assert (sh["slices_per_block"], sh["blocks_per_sm"], sh["smem_bytes"]) == (32, 2, 113440)
+    assert tcp.tc_launch_shape(256, "f16x2")["sinogram_stages"] == 6
