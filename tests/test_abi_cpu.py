@@ -345,3 +345,29 @@ def test_tensor_core_launch_shape_from_python():
     sh = tcp.tc_launch_shape(32, torch.float16)
     assert (sh["slices_per_block"], sh["blocks_per_sm"], sh["smem_bytes"]) == (32, 2, 113440)
     assert tcp.tc_launch_shape(256, "f16x2")["sinogram_stages"] == 6
+
+
+def test_tensor_core_launch_shape_limits_hold_for_every_slice_count(lib):
+    # every shape the launcher can pick fits the SM: shared memory per block
+    # within the opt-in limit (and two blocks with their reserved 1 KB within
+    # the SM's 228 KB), both blocks' TMEM accumulators within 512 columns,
+    # at least two sinogram stages and no more weight stages than sinogram
+    # stages, slices per block a multiple of 16 covering nz or capped
+    for sdt in (_lib.F16, _lib.BF16, _lib.F16X2):
+        for stage in (1, 2):
+            for blocks in (1, 2):
+                for nz in range(1, 601):
+                    st, (N, S, b, na, nbb, smem) = _tc_shape(lib, nz, sdt, stage, blocks)
+                    assert st == 0
+                    split = sdt == _lib.F16X2
+                    assert N % 16 == 0 and N >= min(nz, 16) and N <= (128 if split else 256)
+                    assert N >= nz or N == (128 if split else 256)
+                    assert S == (1 if split or stage == 1 else 2)
+                    assert 1 <= b <= (1 if split else blocks)
+                    assert 2 <= nbb and na <= nbb and na >= 2
+                    assert smem <= 232448
+                    if b == 2:
+                        assert 2 * (smem + 1024) <= 233472
+                        cols = 2 * N
+                        alloc = 32 if cols <= 32 else 1 << (cols - 1).bit_length()
+                        assert 2 * alloc <= 512
