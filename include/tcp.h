@@ -440,11 +440,16 @@ tcp_status tcp_autotune_backproject(const tcp_tensor* sino, const double* theta,
 /* -------------------------------------------------------------- batching -- */
 
 /* A batch reconstructs many datasets of uneven width and angle count: per
- * dataset the fused normalise+filter kernel, then ONE persistent
- * backprojection launch whose blocks pull (dataset, slice block, 32x32 tile)
- * work units from an atomic counter, longest angle count first.  No block
- * waits on another.  The run can be captured into a CUDA graph and replayed
- * (the counter is reset by a memset node inside the graph). */
+ * dataset the fused normalise+filter kernel, then either ONE persistent
+ * CUDA-core backprojection launch whose blocks pull (dataset, slice block,
+ * 32x32 tile) work units from an atomic counter, longest angle count first,
+ * or (tensor-core configurations, kernels 1 and 3) one tensor-core launch per
+ * dataset.  Each dataset's chain (frame means, normalise+filter and, on the
+ * tensor cores, its backprojection) runs on one of three side streams the
+ * batch owns, forked from and joined back to the caller's stream by events,
+ * so datasets overlap; results do not depend on the overlap.  No block waits
+ * on another.  The run can be captured into a CUDA graph (the chains become
+ * parallel branches; the counter is reset by a memset node) and replayed. */
 typedef struct tcp_batch tcp_batch;
 
 typedef struct {
@@ -462,7 +467,8 @@ typedef struct {
   int32_t sino_dtype;   /* storage of the filtered sinograms (F16 when opts is NULL) */
   int32_t autotune;     /* 1: time every backprojector configuration on this batch (CUDA-core
                            configurations in one persistent launch, and for 16-bit sinograms the
-                           tensor-core kernel, one launch per dataset) and keep the fastest;
+                           tensor-core kernel at one and two blocks per SM, one launch per
+                           dataset) and keep the fastest;
                            0: the configuration fixed by tcp_set_backproject_config, if any, else
                            {8, 16, 4, 0} */
   int32_t reserved[2];
