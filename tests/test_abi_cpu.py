@@ -371,3 +371,23 @@ def test_tensor_core_launch_shape_limits_hold_for_every_slice_count(lib):
                         cols = 2 * N
                         alloc = 32 if cols <= 32 else 1 << (cols - 1).bit_length()
                         assert 2 * alloc <= 512
+
+
+def test_tensor_core_blocks_that_share_an_sm_fit_its_tensor_memory(lib):
+    # Blocks of any tensor-core launches (side streams can run several at
+    # once) that fit one SM's shared memory together (each + 1 KB reserved)
+    # also fit its 512 TMEM columns, so no block's allocation waits on another.
+    import itertools
+    shapes = set()
+    for sdt in (_lib.F16, _lib.BF16, _lib.F16X2):
+        for stage in (1, 2):
+            for blocks in (1, 2):
+                for nz in range(1, 300):
+                    st, (N, S, b, na, nbb, smem) = _tc_shape(lib, nz, sdt, stage, blocks)
+                    assert st == 0
+                    cols = 512 if sdt == _lib.F16X2 else 2 * N
+                    shapes.add((smem, 32 if cols <= 32 else 1 << (cols - 1).bit_length()))
+    for k in (2, 3, 4):
+        for combo in itertools.combinations_with_replacement(sorted(shapes), k):
+            if sum(s + 1024 for s, _ in combo) <= 233472:
+                assert sum(a for _, a in combo) <= 512, combo
