@@ -29,7 +29,11 @@
 //
 // Pipeline per CTA: warp-specialised roles (weight builders, TMA producer,
 // MMA issuer) exchange stages of two angles through rings of shared buffers
-// guarded by mbarriers, so weight building, copies and MMAs overlap.
+// guarded by mbarriers, so weight building, copies and MMAs overlap.  The
+// rings normally fill the shared memory (one CTA per SM); with few slices per
+// weight matrix the builders bind, and 16-bit launches can size the rings for
+// half of it so that two CTAs share an SM (their accumulators then take at
+// most 256 TMEM columns each).
 // Every mbarrier wait is bounded by a clock budget; on timeout the kernel
 // records kErrTimeout, every role stops, the issued MMAs are drained (bounded)
 // and the tensor memory is freed.
