@@ -252,10 +252,12 @@ tcp_status tcp_batch_create(const tcp_batch_item* items, int32_t n_items, const 
   if (o.sino_dtype != TCP_F32 && o.sino_dtype != TCP_F16 && o.sino_dtype != TCP_BF16)
     return fail(TCP_ERR_DTYPE, "batch: sino dtype must be F32, F16 or BF16");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  TCP_CUDA_TRY(cudaGetDevice(&dev));
   auto* b = new tcp_batch();
   b->sdt = o.sino_dtype;
   b->vdt = items[0].vol.dtype;
-  TCP_CUDA_TRY(cudaGetDevice(&b->dev));
+  b->dev = dev;
   std::vector<int> order(n_items);
   for (int i = 0; i < n_items; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),

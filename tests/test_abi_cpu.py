@@ -391,3 +391,31 @@ def test_tensor_core_blocks_that_share_an_sm_fit_its_tensor_memory(lib):
         for combo in itertools.combinations_with_replacement(sorted(shapes), k):
             if sum(s + 1024 for s, _ in combo) <= 233472:
                 assert sum(a for _, a in combo) <= 512, combo
+
+
+def test_batch_argument_checks(lib):
+    # rejected on the host before any device work; *out stays NULL
+    out = ctypes.c_void_p(1)
+    item = _lib.BatchItem()
+    item.raw = _t(_lib.U16, (10, 2, 16), ptr=1 << 20)
+    item.vol = _t(_lib.F32, (2, 16, 16), ptr=1 << 21)
+    item.dark = item.flat = _t(_lib.F32, (2, 16), ptr=1 << 22)
+    th = (ctypes.c_double * 10)(*[0.1 * k for k in range(10)])
+    item.theta = ctypes.cast(th, ctypes.c_void_p)
+    item.center = 8.0
+    items = (_lib.BatchItem * 1)(item)
+    assert lib.tcp_batch_create(items, 1, None, None, None) == 1  # null output handle
+    assert lib.tcp_batch_create(None, 1, None, None, ctypes.byref(out)) == 1 and not out.value
+    out = ctypes.c_void_p(1)
+    assert lib.tcp_batch_create(items, 0, None, None, ctypes.byref(out)) == 1 and not out.value
+    opts = _lib.BatchOpts()
+    opts.sino_dtype = _lib.U16
+    out = ctypes.c_void_p(1)
+    assert lib.tcp_batch_create(items, 1, ctypes.byref(opts), None, ctypes.byref(out)) == 3 and not out.value
+    # host pointers (or no GPU at all): refused, nothing created
+    out = ctypes.c_void_p(1)
+    assert lib.tcp_batch_create(items, 1, None, None, ctypes.byref(out)) != 0 and not out.value
+    for fn in ("tcp_batch_run", "tcp_batch_capture", "tcp_batch_replay"):
+        assert getattr(lib, fn)(None, None) == 1
+    assert lib.tcp_batch_info(None, None, None, None, None) == 1
+    assert lib.tcp_batch_destroy(None) == 0
