@@ -22,8 +22,8 @@ class _Tcp:
 
 
 @pytest.mark.parametrize("path,kernel,bound", [
-    ("f32", 1, "alu"), ("f16", 1, "alu"), ("bf16", 1, "alu"), ("f32_cuda", 0, "alu"),
-    ("f32_frec", 0, "alu"), ("f16_frec", 0, "alu")])
+    ("f32", 1, "alu"), ("f16", 1, "alu"), ("bf16", 1, "alu"), ("f16", 3, "alu"), ("bf16", 3, "alu"),
+    ("f32_cuda", 0, "alu"), ("f32_frec", 0, "alu"), ("f16_frec", 0, "alu")])
 def test_roofline_object(monkeypatch, path, kernel, bound):
     monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: _Props())
     r = bench.bp_roofline(_Tcp(kernel), None, path, 256, 2048, 2048, 175.0)
@@ -43,7 +43,7 @@ def test_roofline_object(monkeypatch, path, kernel, bound):
         interps = 256 * 2048 * 2048 * 2048
         assert r["achieved"] == pytest.approx(interps / 0.175 / 1e9, rel=1e-12)
         assert r["frac"] == pytest.approx(interps / 0.175 / ceiling, rel=1e-12)
-        if kernel == 1:  # the dense MMA utilisation is a separately named diagnostic
+        if kernel in (1, 3):  # tensor cores: the dense MMA utilisation is a separately named diagnostic
             assert 0 < r["mma_frac_of_bf16_peak"] < 10
         else:
             assert 0 < r["frac_of_smem_roof"] < 10
