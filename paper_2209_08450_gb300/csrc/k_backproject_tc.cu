@@ -736,7 +736,8 @@ tcp_status launch_backproject_tc(const View3& sino, const TrigTable& trig, doubl
           : (S == 1 ? k_backproject_tc<__nv_bfloat16, 1, false> : k_backproject_tc<__nv_bfloat16, 2, false>);
   TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (blocks > 1)
-    TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
+    TCP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
   const int blocks_x = (a.nsub_x + 7) / 8, blocks_y = (a.nsub_y + 7) / 8;
   dim3 grid((unsigned)(blocks_x * blocks_y * 8 * 8), (unsigned)((nz + N - 1) / N));
   if (grid.y > 65535u) return fail(TCP_ERR_SHAPE, "backproject (tensor cores): too many slice blocks");
