@@ -419,3 +419,38 @@ def test_batch_argument_checks(lib):
         assert getattr(lib, fn)(None, None) == 1
     assert lib.tcp_batch_info(None, None, None, None, None) == 1
     assert lib.tcp_batch_destroy(None) == 0
+
+
+def test_plan_argument_checks(lib):
+    # the description and angles are checked on the host before any device
+    # work; *out stays NULL on every refusal
+    th = (ctypes.c_double * 8)(*[0.1 * k for k in range(8)])
+
+    def desc(**kw):
+        d = _lib.PlanDesc()
+        d.ntheta, d.nz, d.ndet, d.n, d.center, d.vol_dtype = 8, 4, 32, 32, 16.0, _lib.F32
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    def create(d, theta=th):
+        out = ctypes.c_void_p(1)
+        st = lib.tcp_plan_create(ctypes.byref(d) if d is not None else None, theta, ctypes.byref(out))
+        assert not out.value
+        return st
+
+    assert lib.tcp_plan_create(ctypes.byref(desc()), th, None) == 1  # null output handle
+    assert create(None) == 1
+    assert create(desc(ntheta=0)) == 2
+    assert create(desc(nz=-1)) == 2
+    assert create(desc(vol_dtype=_lib.U16)) == 3
+    assert create(desc(io=4)) == 1
+    assert create(desc(host_frames=-1)) == 1
+    assert create(desc(center=float("nan"))) == 1
+    assert create(desc(), None) == 1
+    bad = (ctypes.c_double * 8)(*([0.0] * 7 + [float("inf")]))
+    assert create(desc(), bad) == 1
+    assert lib.tcp_plan_destroy(None) == 0
+    assert lib.tcp_plan_info(None, None, None) == 1
+    cnt = ctypes.c_int64()
+    assert lib.tcp_plan_trace(None, None, 0, ctypes.byref(cnt)) == 1
