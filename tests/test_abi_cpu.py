@@ -475,3 +475,17 @@ def test_lprec_shape_dtype_and_alias_checks(lib):
     assert call(c=float("inf")) == 1
     assert call(th=None) == 1
     assert call(v=_t(_lib.F32, (2, n, n), ptr=(1 << 20) + 64)) == 10   # vol overlaps sino
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU or PyTorch fallback: without the built library the binding raises
+    import os
+    import subprocess
+    import sys
+    code = ("import paper_2209_08450_gb300._lib as L\n"
+            "try:\n    L.load(%r)\nexcept RuntimeError as e:\n    print('raised', 'not built' in str(e))\n"
+            % str(tmp_path / "libtcp.so"))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "raised True" in r.stdout

@@ -90,3 +90,31 @@ def test_torch_ellipsoid_generator_statistics():
     assert u.max() <= 2e4 + 1000 and u.min() >= 0
     assert abs(dark.numpy().view(np.uint16).mean() - 100) < 2
     assert 31.5 - 2 <= c <= 31.5 + 2
+
+
+def test_oracle_and_library_share_no_code():
+    # the FP64 oracle and the CUDA library are independent: no source of the
+    # package imports, loads or includes anything of the oracle, and the
+    # oracle neither imports the package nor includes its headers; the input
+    # generators (synth) hold none of the method's arithmetic and import neither
+    import glob
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def sources(d, exts):
+        return [p for e in exts for p in glob.glob(os.path.join(root, d, "**", "*" + e), recursive=True)]
+
+    pkg = sources("paper_2209_08450_gb300", (".py", ".cu", ".cuh", ".h")) + sources("include", (".h",))
+    for p in pkg:
+        text = open(p).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), p
+        assert "liboracle" not in text and "tcp_oracle" not in text, p
+    for p in sources("oracle", (".py", ".c", ".h")):
+        text = open(p).read()
+        assert not re.search(r"^\s*(import|from)\s+paper_2209_08450_gb300\b", text, re.M), p
+        assert not re.search(r'#include\s+"(tcp|tcp_internal)', text), p
+        assert "libtcp" not in text, p
+    for p in sources("synth", (".py",)):
+        text = open(p).read()
+        assert not re.search(r"^\s*(import|from)\s+(oracle|paper_2209_08450_gb300)\b", text, re.M), p
